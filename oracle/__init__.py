@@ -1,0 +1,322 @@
+"""FP64 CPU oracle for the projection solve of Eq. 6 (S2) -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  It wraps
+``mg_oracle.c`` (plain C, compiled with gcc) through ctypes and shares no code
+with the CUDA library.
+
+Arrays are numpy float64, C order, always 3-D shaped (nz, ny, nx) with nz = 1
+for 2-D problems:
+
+* cells ``(nz, ny, nx)``; x faces ``(nz, ny, nx+1)``; y faces ``(nz, ny+1, nx)``;
+  z faces ``(nz+1, ny, nx)`` (absent in 2-D);
+* nodes ``(Nz, Ny, Nx)`` with ``N_d = n_d`` on periodic axes and ``n_d + 1``
+  otherwise (``Nz = 1`` in 2-D).
+
+Boundary kinds: ``"periodic"``, ``"neumann"`` (wall), ``"dirichlet"`` (phi = 0).
+
+Parity status of each routine (what pins it, in ``tests/test_oracle_*.py``):
+every public routine here is pinned by closed forms, invariants or brute force;
+none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mg_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liborc.so")
+
+BC_CODES = {"periodic": 0, "neumann": 1, "dirichlet": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile mg_oracle.c into oracle/_build/liborc.so (plain gcc, no -march)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double * 3),
+                ("bclo", ctypes.c_int * 3), ("bchi", ctypes.c_int * 3)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("relres", ctypes.c_double), ("constraint", ctypes.c_double),
+                ("rhs_norm", ctypes.c_double), ("src_norm", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        for name in ("orc_mac_faces", "orc_mac_apply", "orc_mac_div", "orc_mac_rhs", "orc_mac_grad_update",
+                     "orc_mac_solve_dense", "orc_mac_solve_mg", "orc_mac_project", "orc_nodal_apply",
+                     "orc_nodal_div", "orc_nodal_lump", "orc_nodal_grad", "orc_nodal_rhs",
+                     "orc_nodal_solve_dense", "orc_nodal_solve_mg", "orc_nodal_project"):
+            getattr(_lib, name).restype = ctypes.c_int
+    return _lib
+
+
+@dataclass(frozen=True)
+class Grid:
+    """Uniform grid: ``n`` cells per axis, spacing ``h``, boundary kinds per face."""
+    dim: int
+    n: tuple
+    h: tuple
+    bclo: tuple
+    bchi: tuple
+
+    @staticmethod
+    def make(n, bclo, bchi, h=None):
+        dim = len(n)
+        n3 = tuple(n) + (1,) * (3 - dim)
+        h3 = tuple(h) if h is not None else tuple(1.0 / v for v in n)
+        h3 = h3 + (1.0,) * (3 - len(h3))
+        lo = tuple(bclo) + ("neumann",) * (3 - dim)
+        hi = tuple(bchi) + ("neumann",) * (3 - dim)
+        for d in range(dim):
+            if (lo[d] == "periodic") != (hi[d] == "periodic"):
+                raise ValueError("periodic boundaries must be paired")
+        return Grid(dim, n3, h3, lo, hi)
+
+    def c(self):
+        g = _Grid()
+        g.dim = self.dim
+        for d in range(3):
+            g.n[d] = self.n[d]
+            g.h[d] = self.h[d]
+            g.bclo[d] = BC_CODES[self.bclo[d]]
+            g.bchi[d] = BC_CODES[self.bchi[d]]
+        return g
+
+    @property
+    def cell_shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def face_shape(self, d):
+        m = [self.n[0], self.n[1], self.n[2]]
+        m[d] += 1
+        return (m[2], m[1], m[0])
+
+    def node_extent(self, d):
+        if d >= self.dim:
+            return 1
+        return self.n[d] if self.bclo[d] == "periodic" else self.n[d] + 1
+
+    @property
+    def node_shape(self):
+        return (self.node_extent(2), self.node_extent(1), self.node_extent(0))
+
+    @property
+    def singular(self):
+        return not any("dirichlet" in (self.bclo[d], self.bchi[d]) for d in range(self.dim))
+
+    def dirichlet_node_mask(self):
+        """Boolean mask over the node array: True on Dirichlet (non-unknown) nodes."""
+        m = np.zeros(self.node_shape, dtype=bool)
+        for d in range(self.dim):
+            ax = 2 - d
+            if self.bclo[d] == "dirichlet":
+                idx = [slice(None)] * 3
+                idx[ax] = 0
+                m[tuple(idx)] = True
+            if self.bchi[d] == "dirichlet":
+                idx = [slice(None)] * 3
+                idx[ax] = self.n[d]
+                m[tuple(idx)] = True
+        return m
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr3(arrs):
+    return [(_p(a) if a is not None else None) for a in (list(arrs) + [None] * (3 - len(arrs)))]
+
+
+def _arr3(ptrs):
+    return (ctypes.POINTER(ctypes.c_double) * 3)(*[p if p is not None else ctypes.POINTER(ctypes.c_double)()
+                                                  for p in ptrs])
+
+
+# ---------------------------------------------------------------- MAC system
+
+def mac_faces(g: Grid, sigma):
+    """Face coefficients B (harmonic mean of adjacent sigma), one array per axis."""
+    sigma = _f64(sigma)
+    B = [np.zeros(g.face_shape(d)) for d in range(g.dim)]
+    p = _ptr3(B)
+    _L().orc_mac_faces(ctypes.byref(g.c()), _p(sigma), p[0], p[1], p[2])
+    return B
+
+
+def mac_apply(g: Grid, B, phi):
+    """(L phi) on cells."""
+    B = [_f64(b) for b in B]
+    phi = _f64(phi)
+    out = np.zeros(g.cell_shape)
+    p = _ptr3(B)
+    _L().orc_mac_apply(ctypes.byref(g.c()), p[0], p[1], p[2], _p(phi), _p(out))
+    return out
+
+
+def mac_div(g: Grid, V):
+    """D(V) on cells for face arrays V."""
+    V = [_f64(v) for v in V]
+    out = np.zeros(g.cell_shape)
+    p = _ptr3(V)
+    _L().orc_mac_div(ctypes.byref(g.c()), p[0], p[1], p[2], _p(out))
+    return out
+
+
+def mac_rhs(g: Grid, beta0_cell, beta0_face, U, S):
+    """f = D(beta0 U) - beta0 S (no mean removal)."""
+    bc, S = _f64(beta0_cell), _f64(S)
+    bf = [_f64(b) for b in beta0_face]
+    U = [_f64(u) for u in U]
+    out = np.zeros(g.cell_shape)
+    _L().orc_mac_rhs(ctypes.byref(g.c()), _p(bc), _arr3(_ptr3(bf)), _arr3(_ptr3(U)), _p(S), _p(out))
+    return out
+
+
+def mac_grad_update(g: Grid, B, beta0_face, phi, U):
+    """Returns U - (B / beta0_face) G phi (copies)."""
+    B = [_f64(b) for b in B]
+    bf = [_f64(b) for b in beta0_face]
+    U = [np.array(u, dtype=np.float64, copy=True) for u in U]
+    phi = _f64(phi)
+    _L().orc_mac_grad_update(ctypes.byref(g.c()), _arr3(_ptr3(B)), _arr3(_ptr3(bf)), _p(phi), _arr3(_ptr3(U)))
+    return U
+
+
+def mac_solve_dense(g: Grid, B, f):
+    """Exact solution of L phi = f by LU (zero-mean gauge when singular)."""
+    B = [_f64(b) for b in B]
+    f = _f64(f)
+    phi = np.zeros(g.cell_shape)
+    p = _ptr3(B)
+    rc = _L().orc_mac_solve_dense(ctypes.byref(g.c()), p[0], p[1], p[2], _p(f), _p(phi))
+    if rc != 0:
+        raise RuntimeError("oracle dense MAC solve failed (singular matrix)")
+    return phi
+
+
+def mac_solve_mg(g: Grid, B, f, tol=1e-14, max_cycles=200, phi0=None):
+    """Multigrid solve to tol or the round-off floor; returns (phi, stats dict)."""
+    B = [_f64(b) for b in B]
+    f = _f64(f)
+    phi = np.zeros(g.cell_shape) if phi0 is None else np.array(phi0, dtype=np.float64, copy=True)
+    st = _Stats()
+    p = _ptr3(B)
+    rc = _L().orc_mac_solve_mg(ctypes.byref(g.c()), p[0], p[1], p[2], _p(f), _p(phi), ctypes.c_double(tol),
+                               ctypes.c_int(max_cycles), ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError("oracle MAC multigrid setup failed")
+    return phi, {"iters": st.iters, "relres": st.relres}
+
+
+def mac_project(g: Grid, sigma, beta0_cell, beta0_face, U, S, tol=1e-14, dense=False):
+    """Full MAC projection.  Returns dict(phi, U, iters, relres, constraint, src_norm, rhs_norm)."""
+    sigma, bc, S = _f64(sigma), _f64(beta0_cell), _f64(S)
+    bf = [_f64(b) for b in beta0_face]
+    U = [np.array(u, dtype=np.float64, copy=True) for u in U]
+    phi = np.zeros(g.cell_shape)
+    st = _Stats()
+    rc = _L().orc_mac_project(ctypes.byref(g.c()), _p(sigma), _p(bc), _arr3(_ptr3(bf)), _arr3(_ptr3(U)), _p(S),
+                              _p(phi), ctypes.c_double(tol), ctypes.c_int(1 if dense else 0), ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError("oracle MAC projection failed")
+    return {"phi": phi, "U": U, "iters": st.iters, "relres": st.relres, "constraint": st.constraint,
+            "src_norm": st.src_norm, "rhs_norm": st.rhs_norm}
+
+
+# -------------------------------------------------------------- nodal system
+
+def nodal_apply(g: Grid, sigma, phi):
+    sigma, phi = _f64(sigma), _f64(phi)
+    out = np.zeros(g.node_shape)
+    _L().orc_nodal_apply(ctypes.byref(g.c()), _p(sigma), _p(phi), _p(out))
+    return out
+
+
+def nodal_div(g: Grid, V):
+    """D_N(V) on nodes for cell-centred components V."""
+    V = [_f64(v) for v in V]
+    out = np.zeros(g.node_shape)
+    _L().orc_nodal_div(ctypes.byref(g.c()), _arr3(_ptr3(V)), _p(out))
+    return out
+
+
+def nodal_lump(g: Grid, gc):
+    gc = _f64(gc)
+    out = np.zeros(g.node_shape)
+    _L().orc_nodal_lump(ctypes.byref(g.c()), _p(gc), _p(out))
+    return out
+
+
+def nodal_grad(g: Grid, phi):
+    """G_N(phi) on cells, one array per axis."""
+    phi = _f64(phi)
+    G = [np.zeros(g.cell_shape) for _ in range(g.dim)]
+    _L().orc_nodal_grad(ctypes.byref(g.c()), _p(phi), _arr3(_ptr3(G)))
+    return G
+
+
+def nodal_rhs(g: Grid, beta0, U, S):
+    beta0, S = _f64(beta0), _f64(S)
+    U = [_f64(u) for u in U]
+    out = np.zeros(g.node_shape)
+    _L().orc_nodal_rhs(ctypes.byref(g.c()), _p(beta0), _arr3(_ptr3(U)), _p(S), _p(out))
+    return out
+
+
+def nodal_solve_dense(g: Grid, sigma, f):
+    sigma, f = _f64(sigma), _f64(f)
+    phi = np.zeros(g.node_shape)
+    rc = _L().orc_nodal_solve_dense(ctypes.byref(g.c()), _p(sigma), _p(f), _p(phi))
+    if rc != 0:
+        raise RuntimeError("oracle dense nodal solve failed (singular matrix)")
+    return phi
+
+
+def nodal_solve_mg(g: Grid, sigma, f, tol=1e-14, max_cycles=200, phi0=None):
+    sigma, f = _f64(sigma), _f64(f)
+    phi = np.zeros(g.node_shape) if phi0 is None else np.array(phi0, dtype=np.float64, copy=True)
+    st = _Stats()
+    rc = _L().orc_nodal_solve_mg(ctypes.byref(g.c()), _p(sigma), _p(f), _p(phi), ctypes.c_double(tol),
+                                 ctypes.c_int(max_cycles), ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError("oracle nodal multigrid setup failed")
+    return phi, {"iters": st.iters, "relres": st.relres}
+
+
+def nodal_project(g: Grid, sigma, beta0, U, S, tol=1e-14, dense=False):
+    """Full nodal projection.  Returns dict(phi, U, iters, relres, constraint, src_norm, rhs_norm)."""
+    sigma, beta0, S = _f64(sigma), _f64(beta0), _f64(S)
+    U = [np.array(u, dtype=np.float64, copy=True) for u in U]
+    phi = np.zeros(g.node_shape)
+    st = _Stats()
+    rc = _L().orc_nodal_project(ctypes.byref(g.c()), _p(sigma), _p(beta0), _arr3(_ptr3(U)), _p(S), _p(phi),
+                                ctypes.c_double(tol), ctypes.c_int(1 if dense else 0), ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError("oracle nodal projection failed")
+    return {"phi": phi, "U": U, "iters": st.iters, "relres": st.relres, "constraint": st.constraint,
+            "src_norm": st.src_norm, "rhs_norm": st.rhs_norm}

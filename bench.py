@@ -1,0 +1,388 @@
+"""Benchmark of the projection solve on GB300: prints ONE JSON line (rank 0).
+
+Workload (default): 3-D 256^3 plane-parallel stratified atmosphere (density
+contrast 1e3, Gaussian random velocity sigma_U = 1e-2, Gaussian heating blob of
+amplitude 1 and width 0.1), MIXED precision.  One step is one pass of the whole
+hot path over one input: coefficient setup on every level (step a1), the MAC
+projection and the nodal projection (steps a2-a10) to relative residual 1e-10.
+A step therefore holds two projection solves; the metric counts both.  The
+velocity inputs are restored from a resident copy at the start of every step
+(device-to-device copies inside the timed region: a projected field would
+otherwise be projected again).
+
+Timing: W untimed warm-up steps, then exactly K steps bracketed by a barrier and
+a device synchronisation, timed with CUDA events on the solver stream; every
+input array (134 MB in FP64 at 256^3) is larger than the 129 MB L2, so no L2
+flush is needed between steps.  Under torchrun every rank solves its own copy of
+the workload (independent solves: weak scaling, no collective on the data path)
+and rank 0 reports the whole-job throughput over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "projection solves/s (MAC + nodal per step), mixed precision, rel. residual 1e-10"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cells per axis of the stratified workload")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1948.1), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def workload_config(n, tol):
+    return {"workload": f"stratified atmosphere {n}^3, MAC + nodal projection, mixed precision",
+            "grid": [n, n, n], "density_contrast": 1e3, "u_sigma": 1e-2, "blob_width": 0.1,
+            "bc": "periodic x,y; slip wall z=0; outflow (phi=0) z=1", "tol": tol, "solves_per_step": 2,
+            "precision": "FP32 V-cycles in FP64 iterative refinement; FP64 residual, update, bottom solve",
+            "l2": "inputs larger than L2 (each FP64 field 134 MB > 129 MB L2); no flush",
+            "seed": 3}
+
+
+# --------------------------------------------------------------------- oracle
+
+def oracle_sample(n_sample, seed=3):
+    """Time the oracle's MAC + nodal projection on an n_sample^3 instance of the
+    same recipe; returns (seconds, relres list)."""
+    import inputs as I
+    import oracle as O
+    O.build()
+    p = I.stratified(n_sample, seed=seed, contrast=1e3)
+    g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+    t0 = time.perf_counter()
+    a = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-10)
+    b = O.nodal_project(g, p["sigma"], p["beta0"], p["U_cell"], p["S"], tol=1e-10)
+    return time.perf_counter() - t0, [a["relres"], b["relres"]]
+
+
+def cpu_baseline(n_full, n_sample=48):
+    dt, _ = oracle_sample(n_sample)
+    scale = (n_full / n_sample) ** 3
+    value = 2.0 / (dt * scale)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full MAC + nodal oracle projection at {n_sample}^3 of the same recipe "
+                      f"({dt:.2f} s), scaled by the cell-count ratio {scale:.0f} to {n_full}^3 "
+                      f"(multigrid work is linear in cells at fixed iteration counts)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n_sample = 32
+    for _ in range(args.warmup):
+        oracle_sample(n_sample)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = oracle_sample(n_sample)
+        times.append(dt)
+    scale = (args.n / n_sample) ** 3
+    total = sum(times) * scale
+    value = 2.0 * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.n, args.tol),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one MAC + nodal oracle projection at {n_sample}^3 of the same "
+                                       f"recipe, scaled by the cell-count ratio {scale:.0f} to {args.n}^3"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1910_12979_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel_class)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        if args.impl == "gb300":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    import inputs as I
+    from paper_1910_12979_gb300 import ProjectionSolver
+    from paper_1910_12979_gb300 import native as N
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    n = args.n
+    p = I.stratified(n, seed=3, contrast=1e3)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    with torch.cuda.stream(stream):
+        sigma, beta0, S = T(p["sigma"]), T(p["beta0"]), T(p["S"])
+        b0f = [T(b) for b in p["beta0_face"]]
+        U0m = [T(u) for u in p["U_mac"]]
+        U0c = [T(u) for u in p["U_cell"]]
+        Um = [u.clone() for u in U0m]
+        Uc = [u.clone() for u in U0c]
+    stream.synchronize()
+
+    def make(prec):
+        mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream)
+        nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream)
+        phim = torch.zeros(mac.vec_shape, dtype=torch.float64, device=dev)
+        phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)
+        return mac, nod, phim, phin
+
+    stats = {}
+
+    def step(solvers):
+        mac, nod, phim, phin = solvers
+        with torch.cuda.stream(stream):
+            mac.update_coeff(sigma)
+            nod.update_coeff(sigma)
+            for a, b in zip(Um, U0m):
+                a.copy_(b)
+            for a, b in zip(Uc, U0c):
+                a.copy_(b)
+            phim.zero_()
+            phin.zero_()
+            stats["mac"] = mac.project(Um, beta0, S, beta0_face=b0f, phi=phim, tol=args.tol,
+                                       allow_not_converged=True)
+            stats["nodal"] = nod.project(Uc, beta0, S, phi=phin, tol=args.tol, allow_not_converged=True)
+
+    def timed(solvers, K, W, prof=False, clocks=None):
+        for _ in range(W):
+            step(solvers)
+        if dist is not None:
+            dist.barrier()
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+        if clocks:
+            clocks.start()
+        if prof:
+            N.mg_prof_enable(True)
+        l0 = N.mg_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step(solvers)
+        e1.record(stream)
+        e1.synchronize()
+        launches = N.mg_launch_count() - l0
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        prof_out = None
+        if prof:
+            prof_out = {N.PROF_NAMES[k]: N.mg_prof_query(k) for k in N.PROF_NAMES}
+            N.mg_prof_enable(False)
+        ck = clocks.stop() if clocks else None
+        if dist is not None:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms, launches, prof_out, ck
+
+    mixed = make("mixed")
+    ms, launches, prof, clocks = timed(mixed, args.steps, args.warmup, prof=True, clocks=Clocks(local))
+    ms_step = ms / args.steps
+    value = 2.0 * args.steps * world / (ms / 1e3)
+    st_mac, st_nod = dict(stats["mac"]), dict(stats["nodal"])
+
+    # roofline of the dominant (largest total time) instrumented kernel class
+    hbm, bf16, src = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    dk = prof[dom]
+    per_launch_ms = dk["ms"] / max(dk["launches"], 1)
+    per_launch_bytes = dk["bytes"] / max(dk["launches"], 1)
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": ncu_traffic(dom), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": per_launch_ms,
+            "launches": dk["launches"],
+            "share_of_step": dk["ms"] / ms if ms > 0 else None,
+            "all": {k: {"avg_ms": v["ms"] / max(v["launches"], 1), "launches": v["launches"],
+                        "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                    for k, v in prof.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+            "config": dict(workload_config(n, args.tol), parallelism=f"independent solves x{world}"),
+            "clocks": clocks, "gpu_launches": launches, "roofline": roof,
+            "solver": {"mac": {k: st_mac[k] for k in ("iters", "rel_resid", "rel_constraint")},
+                       "nodal": {k: st_nod[k] for k in ("iters", "rel_resid", "rel_constraint")}}}
+
+    # plain FP64 GPU multigrid on the same workload
+    if not args.no_fp64:
+        f64 = make("fp64")
+        K64 = max(1, min(args.steps, 3))
+        ms64, _, _, _ = timed(f64, K64, 1)
+        v64 = 2.0 * K64 * world / (ms64 / 1e3)
+        line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64,
+                        "mac_iters": stats["mac"]["iters"], "nodal_iters": stats["nodal"]["iters"]}
+        line["mixed_vs_fp64"] = value / v64
+        for s in f64[:2]:
+            s.close()
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        mac, nod, phim, phin = mixed
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_in = [pin(p["sigma"]), pin(p["beta0"]), pin(p["S"])] + [pin(b) for b in p["beta0_face"]] + \
+               [pin(u) for u in p["U_mac"]] + [pin(u) for u in p["U_cell"]]
+        d_in = [sigma, beta0, S] + b0f + U0m + U0c
+        h_out = [torch.empty_like(u, device="cpu").pin_memory() for u in Um + Uc]
+        h2d = sum(t.numel() * t.element_size() for t in h_in)
+        d2h = sum(t.numel() * t.element_size() for t in h_out)
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for d, hsrc in zip(d_in, h_in):
+                    d.copy_(hsrc, non_blocking=True)
+            step(mixed)
+            with torch.cuda.stream(stream):
+                for hd, d in zip(h_out, Um + Uc):
+                    hd.copy_(d, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        Ke = max(1, min(args.steps, 5))
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(Ke):
+            e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        mse = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([mse], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mse = float(t.item())
+        line["e2e"] = {"value": 2.0 * Ke * world / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": mse / Ke}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * mg.h -- C ABI of the GB300 projection-solve library (libmgproj.so).
+ *
+ * The library solves the variable-coefficient elliptic problem that enforces the
+ * velocity constraint of the low Mach number equations (Eq. 6, S2, with the
+ * base state frozen so that dp0/dt = 0):
+ *
+ *     div( sigma grad phi ) = div(beta0 U) - beta0 S,      sigma = beta0 / rho,
+ *
+ * by geometric multigrid V-cycles (S3: "multigrid linear solvers for the pressure
+ * projection steps"), and applies the projection U <- U - (sigma/beta0) grad phi
+ * that the gradient term of the momentum equation (Eq. 2) implies.  Two
+ * discretisations are offered, one per projection of the second-order method (S3):
+ *
+ *   MG_LOC_CELL   MAC projection: phi at cell centres, U on faces.  The discrete
+ *                 operator is L = D B G with B the harmonic mean of sigma on faces,
+ *                 so the projected face velocity satisfies the discrete constraint
+ *                 D(beta0 U) - beta0 S = (solver residual) exactly.
+ *   MG_LOC_NODAL  nodal projection: phi at nodes, U at cell centres, Q1 finite
+ *                 elements with sigma constant per cell (27-point operator in 3-D,
+ *                 9-point in 2-D).  This projection is approximate.
+ *
+ * Grids are uniform, 2-D or 3-D, on [0, n_d h_d].  Array layout (all arrays):
+ * x fastest, C order, double precision, DEVICE memory owned by the caller:
+ *   cells   nx*ny*nz                   index (k*ny + j)*nx + i
+ *   x faces (nx+1)*ny*nz               index (k*ny + j)*(nx+1) + i   (face i is the low face of cell i)
+ *   y faces nx*(ny+1)*nz               index (k*(ny+1) + j)*nx + i
+ *   z faces nx*ny*(nz+1)               index (k*ny + j)*nx + i
+ *   nodes   Nx*Ny*Nz, N_d = n_d on periodic axes (node n_d is node 0), n_d + 1 otherwise
+ * 2-D problems set dim = 2 and n[2] = 1 and have no z faces.  On periodic axes the
+ * face arrays still hold n_d + 1 planes; planes 0 and n_d are the same face and
+ * the library writes both.
+ *
+ * Boundary conditions per domain face: periodic (paired), Neumann (a wall: no
+ * flux, the wall-normal velocity is left unchanged), Dirichlet (phi = 0, an
+ * outflow boundary).  A problem with no Dirichlet face is singular: the library
+ * removes the mean of the right-hand side and returns the zero-mean solution.
+ *
+ * Errors: every call returns an mg_status; outputs are valid only on MG_OK,
+ * except MG_ERR_NOT_CONVERGED, which still writes the best phi (and U) and the
+ * stats.  No exception or signal crosses the ABI.  mg_last_error() returns a
+ * thread-local message for the last failure.
+ *
+ * Streams and threading: all work of a handle is enqueued on the handle's CUDA
+ * stream.  mg_solve/mg_project synchronise that stream (residual norms are read
+ * back to decide convergence) and only that stream.  A handle must not be used
+ * from two host threads at once (MG_ERR_BUSY).
+ */
+#ifndef MGPROJ_MG_H
+#define MGPROJ_MG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,      /* bad pointer, size, boundary pairing, option */
+    MG_ERR_OOM = 2,              /* device allocation failed or workspace too small */
+    MG_ERR_CUDA = 3,             /* a CUDA runtime call failed (see mg_last_error) */
+    MG_ERR_NOT_CONVERGED = 4,    /* iteration cap or round-off floor reached above tol */
+    MG_ERR_DIVERGED = 5,         /* NaN/Inf or a growing residual */
+    MG_ERR_INCOMPATIBLE_RHS = 6, /* reserved: singular problem with incompatible data */
+    MG_ERR_TIMEOUT = 7,          /* a bounded wait expired */
+    MG_ERR_BUSY = 8,             /* the handle is in use by another thread */
+    MG_ERR_UNSUPPORTED = 9       /* grid does not coarsen to a dense-solvable size, etc. */
+} mg_status;
+
+typedef enum { MG_BC_PERIODIC = 0, MG_BC_NEUMANN = 1, MG_BC_DIRICHLET = 2 } mg_bc_kind;
+typedef enum { MG_LOC_CELL = 0, MG_LOC_NODAL = 1 } mg_location;
+typedef enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 } mg_precision;
+
+/* Grid: dim 2 or 3; n[d] cells per axis (n[2] = 1 in 2-D); h[d] spacing (> 0).
+ * The nodal discretisation requires h[0] = h[1] (= h[2]). */
+typedef struct {
+    int dim;
+    int n[3];
+    double h[3];
+    int loc; /* mg_location */
+} mg_geometry;
+
+/* lo[d] / hi[d]: mg_bc_kind of the low / high face of axis d.  Periodic must be
+ * paired; entries for axes >= dim are ignored. */
+typedef struct {
+    int lo[3];
+    int hi[3];
+} mg_bc;
+
+/* Coefficient sigma = beta0/rho (Eq. 6), cell-centred, device, required, > 0.
+ * face[d]: optional explicit MAC face coefficients (device, face layout); when
+ * all are NULL the library uses the harmonic mean of the adjacent sigma
+ * (boundary faces: the interior sigma; periodic: the mean across the wrap).
+ * Ignored for the nodal discretisation.  Copied into the hierarchy: the caller
+ * may free them after the call returns (and the stream has progressed). */
+typedef struct {
+    const double* sigma;
+    const double* face[3];
+} mg_coeff;
+
+/* beta0 of Eq. 5 at cell centres (both projections) and at face centres (MAC
+ * only: it divides the face update).  Device pointers. */
+typedef struct {
+    const double* cell;
+    const double* face[3];
+} mg_beta0;
+
+/* Solver options; mg_default_options() fills sensible values.
+ *   prec          MG_PREC_FP64: FP64 V-cycles throughout.
+ *                 MG_PREC_MIXED: FP32 smoothing, restriction, prolongation and
+ *                 coarse levels inside an FP64 iterative-refinement loop that
+ *                 recomputes the fine residual and the update in FP64; the
+ *                 coarsest dense solve is FP64 in both modes.
+ *   nu1, nu2      pre/post smoothing sweeps (red-black Gauss-Seidel for cells,
+ *                 damped Jacobi for nodes)
+ *   max_iters     cap on V-cycles (FP64) or refinement iterations (mixed)
+ *   coarsest_max  stop coarsening once a level has at most this many cells
+ *   interp_order  cell prolongation: 0 piecewise constant, 1 linear
+ *   omega         nodal Jacobi damping
+ *   stream        cudaStream_t (NULL: the legacy default stream) */
+typedef struct {
+    int prec;
+    int nu1;
+    int nu2;
+    int max_iters;
+    int coarsest_max;
+    int interp_order;
+    double omega;
+    void* stream;
+} mg_options;
+
+/* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
+ * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
+ * over cells, nodal ||D_N(beta0 U) - S_N||/||S_N|| over unknown nodes (a
+ * diagnostic: the nodal projection is approximate).  ms: wall time of the call. */
+typedef struct {
+    int iters;
+    double rel_resid;
+    double rel_constraint;
+    double rhs_norm;
+    double src_norm;
+    double ms;
+    int status;
+} mg_stats;
+
+typedef struct mg_handle mg_handle;
+
+/* Fill *opt with defaults (mixed precision, V(2,2), linear interpolation). */
+void mg_default_options(mg_options* opt);
+
+/* Device bytes that mg_setup needs for this problem (hierarchy, work arrays,
+ * dense coarsest inverse, reduction scratch).  Used for admission control. */
+mg_status mg_hierarchy_bytes(const mg_geometry* geom, const mg_bc* bc, const mg_options* opt, size_t* bytes);
+
+/* Build a resident multigrid hierarchy (step a1): face or nodal coefficients on
+ * every level, FP32 copies in mixed mode, the dense inverse of the coarsest
+ * operator.  workspace: optional caller-owned device buffer of at least
+ * mg_hierarchy_bytes() bytes (e.g. from the PyTorch caching allocator); NULL
+ * makes the library cudaMalloc its own, freed by mg_destroy.  The handle owns
+ * nothing else on the device. */
+mg_status mg_setup(const mg_coeff* coeff, const mg_geometry* geom, const mg_bc* bc, const mg_options* opt,
+                   void* workspace, size_t workspace_bytes, mg_handle** out);
+
+/* Recompute every level's coefficients from new sigma (same grid), in place. */
+mg_status mg_update_coeff(mg_handle* h, const mg_coeff* coeff);
+
+/* Solve L phi = rhs to ||rhs - L phi|| <= tol ||rhs||.  rhs: device, unknown
+ * layout (cells or nodes; Dirichlet nodes ignored).  phi: device, in: initial
+ * guess, out: solution (Dirichlet nodes set to 0).  stats may be NULL. */
+mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_stats* stats);
+
+/* Projection (steps a2-a10): f = D(beta0 U) - beta0 S, solve to tol, update U
+ * in place, report the constraint.  MAC: U[d] face arrays, beta0->face required.
+ * Nodal: U[d] cell arrays.  phi: optional device output (and initial guess) of
+ * the solution; NULL uses an internal buffer started from zero. */
+mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* beta0, const double* S, double* phi,
+                     double tol, mg_stats* stats);
+
+/* Solve count independent problems (any mix of grids and handles) with their
+ * kernels sharing launches: one launch per multigrid step for the whole batch,
+ * captured once into a CUDA graph and replayed.  Every handle must use the same
+ * precision and location and the same stream; tol[i] per problem; stats may be
+ * NULL or hold count entries. */
+mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double* const* phi, const double* tol,
+                         int count, mg_stats* stats);
+
+/* Change the handle's stream. */
+mg_status mg_set_stream(mg_handle* h, void* stream);
+
+/* out = L phi with the FP64 fine-level operator (diagnostics and tests). */
+mg_status mg_apply(mg_handle* h, const double* phi, double* out);
+
+/* Free the handle (and its workspace when the library allocated it). */
+void mg_destroy(mg_handle* h);
+
+const char* mg_strerror(mg_status s);
+const char* mg_last_error(void);
+
+/* Live per-kernel timing (diagnostics, used by the benchmark's roofline).
+ * mg_prof_enable(1) clears the record and starts bracketing every launch of
+ * the kernels below with a pair of CUDA events on the launching stream;
+ * mg_prof_enable(0) stops.  mg_prof_query (call after the stream has been
+ * synchronised) returns, for one kernel class, the summed event time, the
+ * launch count and the summed ALGORITHMIC bytes of those launches (the words
+ * the method must move: see each class).  Returns MG_ERR_INVALID_ARG for an
+ * unknown class.  Recording stops silently after 65536 launches. */
+typedef enum {
+    MG_PROF_CELL_SMOOTH_FINE = 0, /* one red-black colour pass on the finest cell level:
+                                     phi, f, sigma read and phi written, half of them: 2 words/cell */
+    MG_PROF_RESID64 = 1,          /* FP64 fine residual (+ FP32 copy in mixed mode):
+                                     phi, f, sigma in FP64 (+ r in FP32) per unknown */
+    MG_PROF_NODE_SMOOTH_FINE = 2, /* one Jacobi sweep on the finest nodal level: phi, f, sigma read, phi written */
+    MG_PROF_CELL_RESTRICT_FINE = 3, /* fused residual + restriction on the finest cell level:
+                                       phi, f, sigma read, 1/2^dim word written per cell */
+    MG_PROF_COUNT = 4
+} mg_prof_kernel;
+
+void mg_prof_enable(int on);
+/* Total number of CUDA kernels this library has launched in the process. */
+long long mg_launch_count(void);
+mg_status mg_prof_query(int kernel, double* total_ms, int* launches, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGPROJ_MG_H */

@@ -1,0 +1,521 @@
+// mg_cell.cu -- cell-centred (MAC projection) kernels.
+//
+// Discrete system (the reading of Eq. 6 used throughout the library):
+//   (L phi)_c = sum_d [ Bt_{c+1/2}(phi_{c+e_d} - phi_c) - Bt_{c-1/2}(phi_c - phi_{c-e_d}) ]
+// with Bt = B / h_d^2 the face coefficient pre-scaled at setup and B the
+// harmonic mean of sigma = beta0/rho on the face.  Written row-wise as
+//   (L phi)_c = off_c - diag_c phi_c,
+//   off  = sum over interior/periodic faces of Bt phi_neighbour,
+//   diag = sum over interior/periodic faces of Bt + 2 Bt on Dirichlet faces,
+// Neumann faces contributing nothing and a Dirichlet face (phi = 0 on the
+// face) acting through the ghost value -phi_c.
+#include "mg_device.cuh"
+
+namespace mgp {
+
+// off and diag of row (i,j,k); phi(ii,jj,kk) returns the neighbour value.
+template <int DIM, typename T, typename Phi>
+__device__ __forceinline__ void cell_row(const CellLevel<T>& L, int i, int j, int k, const Phi& phi, T& off, T& dg)
+{
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    off = T(0);
+    dg = T(0);
+    {
+        const size_t r = ((size_t)k * ny + j) * (nx + 1) + i;
+        const T bl = L.bx[r], bh = L.bx[r + 1];
+        if (i > 0) { off += bl * phi(i - 1, j, k); dg += bl; }
+        else if (L.bc.lo[0] == BCP) { off += bl * phi(nx - 1, j, k); dg += bl; }
+        else if (L.bc.lo[0] == BCD) { dg += T(2) * bl; }
+        if (i < nx - 1) { off += bh * phi(i + 1, j, k); dg += bh; }
+        else if (L.bc.hi[0] == BCP) { off += bh * phi(0, j, k); dg += bh; }
+        else if (L.bc.hi[0] == BCD) { dg += T(2) * bh; }
+    }
+    {
+        const size_t r = ((size_t)k * (ny + 1) + j) * nx + i;
+        const T bl = L.by[r], bh = L.by[r + nx];
+        if (j > 0) { off += bl * phi(i, j - 1, k); dg += bl; }
+        else if (L.bc.lo[1] == BCP) { off += bl * phi(i, ny - 1, k); dg += bl; }
+        else if (L.bc.lo[1] == BCD) { dg += T(2) * bl; }
+        if (j < ny - 1) { off += bh * phi(i, j + 1, k); dg += bh; }
+        else if (L.bc.hi[1] == BCP) { off += bh * phi(i, 0, k); dg += bh; }
+        else if (L.bc.hi[1] == BCD) { dg += T(2) * bh; }
+    }
+    if (DIM == 3) {
+        const size_t r = ((size_t)k * ny + j) * nx + i;
+        const size_t pl = (size_t)nx * ny;
+        const T bl = L.bz[r], bh = L.bz[r + pl];
+        if (k > 0) { off += bl * phi(i, j, k - 1); dg += bl; }
+        else if (L.bc.lo[2] == BCP) { off += bl * phi(i, j, nz - 1); dg += bl; }
+        else if (L.bc.lo[2] == BCD) { dg += T(2) * bl; }
+        if (k < nz - 1) { off += bh * phi(i, j, k + 1); dg += bh; }
+        else if (L.bc.hi[2] == BCP) { off += bh * phi(i, j, 0); dg += bh; }
+        else if (L.bc.hi[2] == BCD) { dg += T(2) * bh; }
+    }
+}
+
+template <typename T>
+struct GlobalPhi {
+    const T* p;
+    int nx, ny;
+    __device__ __forceinline__ T operator()(int i, int j, int k) const { return p[((size_t)k * ny + j) * nx + i]; }
+};
+
+struct UnitPhi {  // phi = e_col
+    int col, nx, ny;
+    __device__ __forceinline__ double operator()(int i, int j, int k) const
+    {
+        return (((k * ny + j) * nx + i) == col) ? 1.0 : 0.0;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T inv_diag(const CellLevel<T>& L, int idx, T dg)
+{
+    return L.invd ? L.invd[idx] : recip(dg);
+}
+
+// ------------------------------------------------------------------ setup
+
+__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+// face coefficient along axis d from cell sigma, scaled by 1/h_d^2
+template <int D>
+__global__ void k_faces_from_sigma(CellLevel<double> L, const double* __restrict__ sigma, double ih2,
+                                   double* __restrict__ out)
+{
+    const int mx = L.nx + (D == 0), my = L.ny + (D == 1), mz = L.nz + (D == 2);
+    const int total = mx * my * mz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int f[3];
+    unflat(t, mx, my, f[0], f[1], f[2]);
+    const int n = (D == 0) ? L.nx : (D == 1) ? L.ny : L.nz;
+    int lo[3] = {f[0], f[1], f[2]}, hi[3] = {f[0], f[1], f[2]};
+    lo[D] -= 1;
+    auto S = [&](const int* c) { return sigma[((size_t)c[2] * L.ny + c[1]) * L.nx + c[0]]; };
+    double v;
+    if (f[D] == 0 || f[D] == n) {
+        if (L.bc.lo[D] == BCP) {
+            lo[D] = n - 1;
+            hi[D] = 0;
+            v = harmonic(S(lo), S(hi));
+        } else if (f[D] == 0) {
+            v = S(hi);
+        } else {
+            v = S(lo);
+        }
+    } else {
+        v = harmonic(S(lo), S(hi));
+    }
+    out[t] = v * ih2;
+}
+
+__global__ void k_scale(const double* __restrict__ in, double s, double* __restrict__ out, int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = in[t] * s;
+}
+
+// coarse face = mean of the 2^(dim-1) fine faces it covers, times h_f^2/h_c^2 = 1/4
+template <int DIM, int D>
+__global__ void k_coarsen_faces(CellLevel<double> F, CellLevel<double> C, const double* __restrict__ fine,
+                                double* __restrict__ coarse)
+{
+    const int mx = C.nx + (D == 0), my = C.ny + (D == 1), mz = C.nz + (D == 2);
+    const int total = mx * my * mz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int f[3];
+    unflat(t, mx, my, f[0], f[1], f[2]);
+    const int fx = F.nx + (D == 0), fy = F.ny + (D == 1);
+    double s = 0.0;
+    constexpr int nsub = 1 << (DIM - 1);
+#pragma unroll
+    for (int q = 0; q < nsub; ++q) {
+        int g[3] = {2 * f[0], 2 * f[1], DIM == 3 ? 2 * f[2] : 0};
+        int bit = 0;
+#pragma unroll
+        for (int e = 0; e < DIM; ++e) {
+            if (e == D) continue;
+            g[e] += (q >> bit) & 1;
+            ++bit;
+        }
+        s += fine[((size_t)g[2] * fy + g[1]) * fx + g[0]];
+    }
+    coarse[t] = s * (0.25 / nsub);
+}
+
+template <int DIM>
+__global__ void k_invdiag(CellLevel<double> L, double* __restrict__ invd)
+{
+    const int total = L.nx * L.ny * L.nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    unflat(t, L.nx, L.ny, i, j, k);
+    double off, dg;
+    cell_row<DIM>(L, i, j, k, [](int, int, int) { return 0.0; }, off, dg);
+    invd[t] = recip(dg);
+}
+
+// ------------------------------------------------------------- smoothing
+
+// One colour of red-black Gauss-Seidel: phi_c <- (off_c - b_c) / diag_c on
+// cells with (i + j + k) % 2 == color.
+template <int DIM, typename T>
+__global__ void k_gsrb(CellLevel<T> L, T* __restrict__ x, const T* __restrict__ b, int color)
+{
+    const int total = L.nx * L.ny * L.nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    unflat(t, L.nx, L.ny, i, j, k);
+    if (((i + j + k) & 1) != color) return;
+    T off, dg;
+    cell_row<DIM>(L, i, j, k, GlobalPhi<T>{x, L.nx, L.ny}, off, dg);
+    x[t] = (off - b[t]) * inv_diag(L, t, dg);
+}
+
+// r = b - L x on the fine level, averaged over the 2^dim children of each coarse cell.
+template <int DIM, typename T>
+__global__ void k_resid_restrict(CellLevel<T> F, const T* __restrict__ x, const T* __restrict__ b,
+                                 T* __restrict__ bc, int cnx, int cny, int cnz)
+{
+    const int total = cnx * cny * cnz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int ci, cj, ck;
+    unflat(t, cnx, cny, ci, cj, ck);
+    const GlobalPhi<T> ph{x, F.nx, F.ny};
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < (1 << DIM); ++q) {
+        const int i = 2 * ci + (q & 1), j = 2 * cj + ((q >> 1) & 1), k = DIM == 3 ? 2 * ck + ((q >> 2) & 1) : 0;
+        T off, dg;
+        cell_row<DIM>(F, i, j, k, ph, off, dg);
+        const size_t id = ((size_t)k * F.ny + j) * F.nx + i;
+        s += b[id] - (off - dg * x[id]);
+    }
+    bc[t] = s * (T(1) / T(1 << DIM));
+}
+
+// coarse value seen from fine cell index i along one axis (linear interpolation):
+// parent P = i/2 with weight 3/4, the neighbour Q on the fine cell's side with 1/4;
+// beyond a boundary the neighbour is the periodic image, the mirror (Neumann) or
+// the odd reflection (Dirichlet).
+struct Lin1D {
+    int p, q;
+    float sq;  // sign applied to the value at q (+1, or -1 for the Dirichlet ghost)
+};
+
+__device__ __forceinline__ Lin1D lin1d(int i, int nc, int bclo, int bchi)
+{
+    Lin1D r;
+    r.p = i >> 1;
+    r.sq = 1.f;
+    if (i & 1) {
+        r.q = r.p + 1;
+        if (r.q >= nc) {
+            if (bchi == BCP) r.q = 0;
+            else { r.q = r.p; r.sq = (bchi == BCD) ? -1.f : 1.f; }
+        }
+    } else {
+        r.q = r.p - 1;
+        if (r.q < 0) {
+            if (bclo == BCP) r.q = nc - 1;
+            else { r.q = r.p; r.sq = (bclo == BCD) ? -1.f : 1.f; }
+        }
+    }
+    return r;
+}
+
+template <int DIM, typename T, int ORDER>
+__global__ void k_prolong_add(CellLevel<T> F, CellLevel<T> C, T* __restrict__ xf, const T* __restrict__ xc)
+{
+    const int total = F.nx * F.ny * F.nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    unflat(t, F.nx, F.ny, i, j, k);
+    auto X = [&](int a, int b2, int c) { return xc[((size_t)c * C.ny + b2) * C.nx + a]; };
+    if (ORDER == 0) {
+        xf[t] += X(i >> 1, j >> 1, DIM == 3 ? (k >> 1) : 0);
+        return;
+    }
+    const Lin1D lx = lin1d(i, C.nx, F.bc.lo[0], F.bc.hi[0]);
+    const Lin1D ly = lin1d(j, C.ny, F.bc.lo[1], F.bc.hi[1]);
+    const T w1 = T(0.75), w2 = T(0.25);
+    if (DIM == 2) {
+        const T v = w1 * (w1 * X(lx.p, ly.p, 0) + w2 * T(lx.sq) * X(lx.q, ly.p, 0)) +
+                    w2 * T(ly.sq) * (w1 * X(lx.p, ly.q, 0) + w2 * T(lx.sq) * X(lx.q, ly.q, 0));
+        xf[t] += v;
+    } else {
+        const Lin1D lz = lin1d(k, C.nz, F.bc.lo[2], F.bc.hi[2]);
+        auto plane = [&](int c) {
+            return w1 * (w1 * X(lx.p, ly.p, c) + w2 * T(lx.sq) * X(lx.q, ly.p, c)) +
+                   w2 * T(ly.sq) * (w1 * X(lx.p, ly.q, c) + w2 * T(lx.sq) * X(lx.q, ly.q, c));
+        };
+        xf[t] += w1 * plane(lz.p) + w2 * T(lz.sq) * plane(lz.q);
+    }
+}
+
+// -------------------------------------------------------- FP64 residuals
+
+template <int DIM>
+__global__ void k_resid64(CellLevel<double> L, const double* __restrict__ x, const double* __restrict__ b,
+                          float* __restrict__ r32, const double* __restrict__ scale, double* __restrict__ partials)
+{
+    const int total = L.nx * L.ny * L.nz;
+    const double inv = (r32 && scale) ? 1.0 / *scale : 1.0;
+    double acc[1] = {0.0};
+    const GlobalPhi<double> ph{x, L.nx, L.ny};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int i, j, k;
+        unflat(t, L.nx, L.ny, i, j, k);
+        double off, dg;
+        cell_row<DIM>(L, i, j, k, ph, off, dg);
+        const double r = b[t] - (off - dg * x[t]);
+        acc[0] += r * r;
+        if (r32) r32[t] = (float)(r * inv);
+    }
+    block_reduce_store<1>(acc, partials);
+}
+
+template <int DIM>
+__global__ void k_apply64(CellLevel<double> L, const double* __restrict__ x, double* __restrict__ out)
+{
+    const int total = L.nx * L.ny * L.nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    unflat(t, L.nx, L.ny, i, j, k);
+    double off, dg;
+    cell_row<DIM>(L, i, j, k, GlobalPhi<double>{x, L.nx, L.ny}, off, dg);
+    out[t] = off - dg * x[t];
+}
+
+// ------------------------------------------------------ RHS / projection
+
+struct Ptr3 {
+    const double* p[3];
+};
+struct MPtr3 {
+    double* p[3];
+};
+
+// f = D(beta0 U) - beta0 S  (Eq. 6), partial sums {sum f, sum (beta0 S)^2, sum f^2}
+template <int DIM>
+__global__ void k_rhs(CellLevel<double> L, double ihx, double ihy, double ihz, Ptr3 U, Ptr3 B0, const double* b0c,
+                      const double* S, double* __restrict__ f, double* __restrict__ partials)
+{
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int total = nx * ny * nz;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int i, j, k;
+        unflat(t, nx, ny, i, j, k);
+        const size_t rx = ((size_t)k * ny + j) * (nx + 1) + i;
+        double v = (B0.p[0][rx + 1] * U.p[0][rx + 1] - B0.p[0][rx] * U.p[0][rx]) * ihx;
+        const size_t ry = ((size_t)k * (ny + 1) + j) * nx + i;
+        v += (B0.p[1][ry + nx] * U.p[1][ry + nx] - B0.p[1][ry] * U.p[1][ry]) * ihy;
+        if (DIM == 3) {
+            const size_t rz = (size_t)t, pl = (size_t)nx * ny;
+            v += (B0.p[2][rz + pl] * U.p[2][rz + pl] - B0.p[2][rz] * U.p[2][rz]) * ihz;
+        }
+        const double src = b0c[t] * S[t];
+        v -= src;
+        if (f) f[t] = v;
+        acc[0] += v;
+        acc[1] += src * src;
+        acc[2] += v * v;
+    }
+    block_reduce_store<3>(acc, partials);
+}
+
+// U_f -= (B_f / beta0_f) (G phi)_f along axis D; Bt h = B/h, Dirichlet faces
+// use phi = 0 on the face at distance h/2, Neumann faces are left unchanged.
+template <int D>
+__global__ void k_project(CellLevel<double> L, double h, const double* __restrict__ phi, const double* __restrict__ b0f,
+                          double* __restrict__ U, const double* __restrict__ Bt)
+{
+    const int mx = L.nx + (D == 0), my = L.ny + (D == 1), mz = L.nz + (D == 2);
+    const int total = mx * my * mz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int f[3];
+    unflat(t, mx, my, f[0], f[1], f[2]);
+    const int n = (D == 0) ? L.nx : (D == 1) ? L.ny : L.nz;
+    int lo[3] = {f[0], f[1], f[2]}, hi[3] = {f[0], f[1], f[2]};
+    lo[D] -= 1;
+    auto P = [&](const int* c) { return phi[((size_t)c[2] * L.ny + c[1]) * L.nx + c[0]]; };
+    double flux;  // B (G phi) = Bt h^2 (G phi)
+    if (f[D] == 0 || f[D] == n) {
+        if (L.bc.lo[D] == BCP) {
+            lo[D] = n - 1;
+            hi[D] = 0;
+            flux = Bt[t] * h * (P(hi) - P(lo));
+        } else {
+            const int bc = (f[D] == 0) ? L.bc.lo[D] : L.bc.hi[D];
+            if (bc != BCD) return;
+            flux = (f[D] == 0) ? 2.0 * Bt[t] * h * P(hi) : -2.0 * Bt[t] * h * P(lo);
+        }
+    } else {
+        flux = Bt[t] * h * (P(hi) - P(lo));
+    }
+    U[t] -= flux / b0f[t];
+}
+
+// ---------------------------------------------------------- dense coarsest
+
+template <int DIM, typename T>
+__global__ void k_dense_assemble(CellLevel<T> L, double* __restrict__ A, int lda)
+{
+    const int N = L.nx * L.ny * L.nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * N) return;
+    const int row = t / N, col = t % N;
+    int i, j, k;
+    unflat(row, L.nx, L.ny, i, j, k);
+    T off, dg;
+    const UnitPhi e{col, L.nx, L.ny};
+    cell_row<DIM>(L, i, j, k, [&](int a, int b, int c) { return (T)e(a, b, c); }, off, dg);
+    A[(size_t)row * lda + col] = (double)off - (row == col ? (double)dg : 0.0);
+}
+
+// ================================================================ launchers
+
+static inline int nb(long long n) { return ceil_div(n, kThreads); }
+
+void cell_faces_from_sigma(int dim, const CellLevel<double>& L, const double* sigma, const double* h, double* bx,
+                           double* by, double* bz, cudaStream_t s)
+{
+    long long mx = (long long)(L.nx + 1) * L.ny * L.nz;
+    MGP_LAUNCH(k_faces_from_sigma<0><<<nb(mx), kThreads, 0, s>>>(L, sigma, 1.0 / (h[0] * h[0]), bx));
+    long long my = (long long)L.nx * (L.ny + 1) * L.nz;
+    MGP_LAUNCH(k_faces_from_sigma<1><<<nb(my), kThreads, 0, s>>>(L, sigma, 1.0 / (h[1] * h[1]), by));
+    if (dim == 3) {
+        long long mz = (long long)L.nx * L.ny * (L.nz + 1);
+        MGP_LAUNCH(k_faces_from_sigma<2><<<nb(mz), kThreads, 0, s>>>(L, sigma, 1.0 / (h[2] * h[2]), bz));
+    }
+}
+
+void cell_scale_faces(int dim, const CellLevel<double>& L, const double* const face[3], const double* h, double* bx,
+                      double* by, double* bz, cudaStream_t s)
+{
+    double* out[3] = {bx, by, bz};
+    for (int d = 0; d < dim; ++d) {
+        long long m = (long long)(L.nx + (d == 0)) * (L.ny + (d == 1)) * (L.nz + (d == 2));
+        MGP_LAUNCH(k_scale<<<nb(m), kThreads, 0, s>>>(face[d], 1.0 / (h[d] * h[d]), out[d], (int)m));
+    }
+}
+
+void cell_coarsen_faces(int dim, const CellLevel<double>& F, const CellLevel<double>& C, double* bx, double* by,
+                        double* bz, cudaStream_t s)
+{
+    long long mx = (long long)(C.nx + 1) * C.ny * C.nz, my = (long long)C.nx * (C.ny + 1) * C.nz;
+    if (dim == 2) {
+        MGP_LAUNCH(k_coarsen_faces<2, 0><<<nb(mx), kThreads, 0, s>>>(F, C, F.bx, bx));
+        MGP_LAUNCH(k_coarsen_faces<2, 1><<<nb(my), kThreads, 0, s>>>(F, C, F.by, by));
+    } else {
+        long long mz = (long long)C.nx * C.ny * (C.nz + 1);
+        MGP_LAUNCH(k_coarsen_faces<3, 0><<<nb(mx), kThreads, 0, s>>>(F, C, F.bx, bx));
+        MGP_LAUNCH(k_coarsen_faces<3, 1><<<nb(my), kThreads, 0, s>>>(F, C, F.by, by));
+        MGP_LAUNCH(k_coarsen_faces<3, 2><<<nb(mz), kThreads, 0, s>>>(F, C, F.bz, bz));
+    }
+}
+
+void cell_invdiag(int dim, const CellLevel<double>& L, double* invd, cudaStream_t s)
+{
+    long long n = (long long)L.nx * L.ny * L.nz;
+    if (dim == 2) MGP_LAUNCH(k_invdiag<2><<<nb(n), kThreads, 0, s>>>(L, invd));
+    else MGP_LAUNCH(k_invdiag<3><<<nb(n), kThreads, 0, s>>>(L, invd));
+}
+
+template <typename T>
+void cell_gsrb(int dim, const CellLevel<T>& L, T* x, const T* b, int color, cudaStream_t s)
+{
+    long long n = (long long)L.nx * L.ny * L.nz;
+    if (dim == 2) MGP_LAUNCH(k_gsrb<2, T><<<nb(n), kThreads, 0, s>>>(L, x, b, color));
+    else MGP_LAUNCH(k_gsrb<3, T><<<nb(n), kThreads, 0, s>>>(L, x, b, color));
+}
+
+template <typename T>
+void cell_resid_restrict(int dim, const CellLevel<T>& F, const T* x, const T* b, T* bc, cudaStream_t s)
+{
+    const int cnx = F.nx / 2, cny = F.ny / 2, cnz = dim == 3 ? F.nz / 2 : 1;
+    long long n = (long long)cnx * cny * cnz;
+    if (dim == 2) MGP_LAUNCH(k_resid_restrict<2, T><<<nb(n), kThreads, 0, s>>>(F, x, b, bc, cnx, cny, cnz));
+    else MGP_LAUNCH(k_resid_restrict<3, T><<<nb(n), kThreads, 0, s>>>(F, x, b, bc, cnx, cny, cnz));
+}
+
+template <typename T>
+void cell_prolong_add(int dim, const CellLevel<T>& F, const CellLevel<T>& C, T* xf, const T* xc, int order,
+                      cudaStream_t s)
+{
+    long long n = (long long)F.nx * F.ny * F.nz;
+    if (dim == 2) {
+        if (order == 0) MGP_LAUNCH(k_prolong_add<2, T, 0><<<nb(n), kThreads, 0, s>>>(F, C, xf, xc));
+        else MGP_LAUNCH(k_prolong_add<2, T, 1><<<nb(n), kThreads, 0, s>>>(F, C, xf, xc));
+    } else {
+        if (order == 0) MGP_LAUNCH(k_prolong_add<3, T, 0><<<nb(n), kThreads, 0, s>>>(F, C, xf, xc));
+        else MGP_LAUNCH(k_prolong_add<3, T, 1><<<nb(n), kThreads, 0, s>>>(F, C, xf, xc));
+    }
+}
+
+void cell_resid64(int dim, const CellLevel<double>& L, const double* x, const double* b, float* r32,
+                  const double* scale, double* partials, cudaStream_t s)
+{
+    if (dim == 2) MGP_LAUNCH(k_resid64<2><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+    else MGP_LAUNCH(k_resid64<3><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+}
+
+void cell_apply64(int dim, const CellLevel<double>& L, const double* x, double* out, cudaStream_t s)
+{
+    long long n = (long long)L.nx * L.ny * L.nz;
+    if (dim == 2) MGP_LAUNCH(k_apply64<2><<<nb(n), kThreads, 0, s>>>(L, x, out));
+    else MGP_LAUNCH(k_apply64<3><<<nb(n), kThreads, 0, s>>>(L, x, out));
+}
+
+void cell_rhs(int dim, const CellLevel<double>& L, const double* h, const double* const U[3],
+              const double* const b0f[3], const double* b0c, const double* S, double* f, double* partials,
+              cudaStream_t s)
+{
+    Ptr3 u{{U[0], U[1], dim == 3 ? U[2] : nullptr}}, b{{b0f[0], b0f[1], dim == 3 ? b0f[2] : nullptr}};
+    const double ihz = dim == 3 ? 1.0 / h[2] : 0.0;
+    if (dim == 2) MGP_LAUNCH(k_rhs<2><<<kRedBlocks, kThreads, 0, s>>>(L, 1.0 / h[0], 1.0 / h[1], ihz, u, b, b0c, S, f, partials));
+    else MGP_LAUNCH(k_rhs<3><<<kRedBlocks, kThreads, 0, s>>>(L, 1.0 / h[0], 1.0 / h[1], ihz, u, b, b0c, S, f, partials));
+}
+
+void cell_project(int dim, const CellLevel<double>& L, const double* h, const double* phi, const double* const b0f[3],
+                  double* const U[3], cudaStream_t s)
+{
+    long long mx = (long long)(L.nx + 1) * L.ny * L.nz, my = (long long)L.nx * (L.ny + 1) * L.nz;
+    MGP_LAUNCH(k_project<0><<<nb(mx), kThreads, 0, s>>>(L, h[0], phi, b0f[0], U[0], L.bx));
+    MGP_LAUNCH(k_project<1><<<nb(my), kThreads, 0, s>>>(L, h[1], phi, b0f[1], U[1], L.by));
+    if (dim == 3) {
+        long long mz = (long long)L.nx * L.ny * (L.nz + 1);
+        MGP_LAUNCH(k_project<2><<<nb(mz), kThreads, 0, s>>>(L, h[2], phi, b0f[2], U[2], L.bz));
+    }
+}
+
+template <typename T>
+void cell_dense_assemble(int dim, const CellLevel<T>& L, double* A, int lda, cudaStream_t s)
+{
+    long long N = (long long)L.nx * L.ny * L.nz;
+    if (dim == 2) MGP_LAUNCH(k_dense_assemble<2, T><<<nb(N * N), kThreads, 0, s>>>(L, A, lda));
+    else MGP_LAUNCH(k_dense_assemble<3, T><<<nb(N * N), kThreads, 0, s>>>(L, A, lda));
+}
+
+template void cell_gsrb<float>(int, const CellLevel<float>&, float*, const float*, int, cudaStream_t);
+template void cell_gsrb<double>(int, const CellLevel<double>&, double*, const double*, int, cudaStream_t);
+template void cell_resid_restrict<float>(int, const CellLevel<float>&, const float*, const float*, float*, cudaStream_t);
+template void cell_resid_restrict<double>(int, const CellLevel<double>&, const double*, const double*, double*,
+                                          cudaStream_t);
+template void cell_prolong_add<float>(int, const CellLevel<float>&, const CellLevel<float>&, float*, const float*, int,
+                                      cudaStream_t);
+template void cell_prolong_add<double>(int, const CellLevel<double>&, const CellLevel<double>&, double*,
+                                       const double*, int, cudaStream_t);
+template void cell_dense_assemble<float>(int, const CellLevel<float>&, double*, int, cudaStream_t);
+template void cell_dense_assemble<double>(int, const CellLevel<double>&, double*, int, cudaStream_t);
+
+}  // namespace mgp

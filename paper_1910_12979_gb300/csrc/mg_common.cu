@@ -1,0 +1,228 @@
+// mg_common.cu -- reductions, vector helpers and the dense coarsest-level solve.
+#include <atomic>
+
+#include "mg_device.cuh"
+
+namespace mgp {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// Sum the kRedBlocks partials of each slot in a fixed order: out[q].
+__global__ void k_finalize(const double* __restrict__ partials, int nslots, double* __restrict__ out)
+{
+    __shared__ double sh[kThreads];
+    for (int q = 0; q < nslots; ++q) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += partials[q * kRedBlocks + b];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[q] = sh[0];
+        __syncthreads();
+    }
+}
+
+void reduce_finalize(const double* partials, int nslots, double* out, cudaStream_t s)
+{
+    MGP_LAUNCH(k_finalize<<<1, kThreads, 0, s>>>(partials, nslots, out));
+}
+
+__global__ void k_sum_sq(const double* __restrict__ v, size_t n, double* __restrict__ partials)
+{
+    double acc[2] = {0.0, 0.0};
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const double x = v[t];
+        acc[0] += x;
+        acc[1] += x * x;
+    }
+    block_reduce_store<2>(acc, partials);
+}
+
+void vec_sum_sq(const double* v, size_t n, double* partials, cudaStream_t s)
+{
+    MGP_LAUNCH(k_sum_sq<<<kRedBlocks, kThreads, 0, s>>>(v, n, partials));
+}
+
+__global__ void k_sub_mean(double* __restrict__ v, size_t n, const double* __restrict__ sum, double count)
+{
+    const double m = *sum / count;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        v[t] -= m;
+}
+
+void vec_sub_mean(double* v, size_t n, const double* sum, double count, cudaStream_t s)
+{
+    MGP_LAUNCH(k_sub_mean<<<kRedBlocks, kThreads, 0, s>>>(v, n, sum, count));
+}
+
+__global__ void k_copy64(double* __restrict__ d, const double* __restrict__ a, size_t n)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        d[t] = a[t];
+}
+__global__ void k_to32(float* __restrict__ d, const double* __restrict__ a, size_t n)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        d[t] = (float)a[t];
+}
+__global__ void k_axpy32(double* __restrict__ phi, const float* __restrict__ e, const double* __restrict__ scale,
+                         size_t n)
+{
+    const double s = *scale;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        phi[t] += s * (double)e[t];
+}
+
+void vec_copy_f64(double* dst, const double* src, size_t n, cudaStream_t s)
+{
+    MGP_LAUNCH(k_copy64<<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
+}
+void vec_to_f32(float* dst, const double* src, size_t n, cudaStream_t s)
+{
+    MGP_LAUNCH(k_to32<<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
+}
+void vec_zero_f32(float* v, size_t n, cudaStream_t s) { cudaMemsetAsync(v, 0, n * sizeof(float), s); }
+void vec_zero_f64(double* v, size_t n, cudaStream_t s) { cudaMemsetAsync(v, 0, n * sizeof(double), s); }
+void vec_axpy_f32(double* phi, const float* e, const double* scale, size_t n, cudaStream_t s)
+{
+    MGP_LAUNCH(k_axpy32<<<kRedBlocks, kThreads, 0, s>>>(phi, e, scale, n));
+}
+
+__global__ void k_fscale(DevScalars* d)
+{
+    const double f2 = d->fnorm2;
+    d->fscale = f2 > 0.0 ? sqrt(f2) : 1.0;
+}
+void scalars_set_fscale(DevScalars* d, cudaStream_t s) { MGP_LAUNCH(k_fscale<<<1, 1, 0, s>>>(d)); }
+
+// ------------------------------------------------------------ dense solve
+//
+// Gauss-Jordan with partial pivoting on [A | I] held in global memory, one CTA.
+// A: n x n (n = N + 1 when the problem is singular: the bordered matrix
+// [A 1; 1^T 0], whose inverse's leading N x N block maps a compatible b to the
+// zero-mean solution).  Minv receives the leading N x N block, row-major.
+constexpr int kGJThreads = 1024;
+
+__global__ void k_border(double* A, int N, int lda)
+{
+    for (int t = threadIdx.x; t <= N; t += blockDim.x) {
+        A[(size_t)t * lda + N] = t < N ? 1.0 : 0.0;
+        A[(size_t)N * lda + t] = t < N ? 1.0 : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kGJThreads) k_gauss_jordan(double* __restrict__ W, int n, int* __restrict__ info)
+{
+    // W: n rows x 2n columns, row-major; left half A, right half I (set here)
+    const int ld = 2 * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int r = t / n, c = t % n;
+        W[(size_t)r * ld + n + c] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    __shared__ double sv[kGJThreads / 32];
+    __shared__ int si[kGJThreads / 32];
+    __shared__ int piv;
+    __shared__ double pval;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) *info = 0;
+    for (int k = 0; k < n; ++k) {
+        // pivot search over rows k..n-1 (ties -> smallest row: deterministic)
+        double best = -1.0;
+        int bi = n;
+        for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
+            const double v = fabs(W[(size_t)r * ld + k]);
+            if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { sv[warp] = best; si[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = -1.0;
+            int p = n;
+            for (int w = 0; w < kGJThreads / 32; ++w)
+                if (sv[w] > b || (sv[w] == b && si[w] < p)) { b = sv[w]; p = si[w]; }
+            piv = p;
+            pval = (p < n) ? W[(size_t)p * ld + k] : 0.0;
+            if (b <= 0.0 && *info == 0) *info = k + 1;
+        }
+        __syncthreads();
+        if (pval == 0.0) return;  // singular: info set, Minv left unusable
+        const int p = piv;
+        if (p != k)
+            for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+                const double tmp = W[(size_t)k * ld + c];
+                W[(size_t)k * ld + c] = W[(size_t)p * ld + c];
+                W[(size_t)p * ld + c] = tmp;
+            }
+        __syncthreads();
+        const double inv = 1.0 / pval;
+        for (int c = threadIdx.x; c < ld; c += blockDim.x) W[(size_t)k * ld + c] *= inv;
+        __syncthreads();
+        // eliminate column k from every other row
+        for (int t = threadIdx.x; t < n * ld; t += blockDim.x) {
+            const int r = t / ld, c = t % ld;
+            if (r == k || c == k) continue;
+            W[(size_t)r * ld + c] -= W[(size_t)r * ld + k] * W[(size_t)k * ld + c];
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x)
+            if (r != k) W[(size_t)r * ld + k] = 0.0;
+        __syncthreads();
+    }
+}
+
+__global__ void k_extract(const double* __restrict__ W, int n, int N, double* __restrict__ Minv)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N * N; t += gridDim.x * blockDim.x) {
+        const int r = t / N, c = t % N;
+        Minv[t] = W[(size_t)r * 2 * n + n + c];
+    }
+}
+
+// A must be laid out with lda = 2 * n (n = N or N + 1); the caller assembled
+// the leading N x N block.  Returns 0 on success (after a device sync).
+int dense_invert(double* A, int N, int singular, double* Minv, int* info, cudaStream_t s)
+{
+    const int n = N + (singular ? 1 : 0);
+    if (singular) MGP_LAUNCH(k_border<<<1, 256, 0, s>>>(A, N, 2 * n));
+    MGP_LAUNCH(k_gauss_jordan<<<1, kGJThreads, 0, s>>>(A, n, info));
+    MGP_LAUNCH(k_extract<<<64, 256, 0, s>>>(A, n, N, Minv));
+    return 0;
+}
+
+// x = Minv b, one warp per row
+template <typename T>
+__global__ void k_dense_apply(const double* __restrict__ Minv, int N, const T* __restrict__ b, T* __restrict__ x)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = warp; r < N; r += nw) {
+        double s = 0.0;
+        for (int c = lane; c < N; c += 32) s += Minv[(size_t)r * N + c] * (double)b[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) x[r] = (T)s;
+    }
+}
+
+template <typename T>
+void dense_apply(const double* Minv, int N, const T* b, T* x, cudaStream_t s)
+{
+    const int blocks = ceil_div((long long)N * 32, kThreads);
+    MGP_LAUNCH(k_dense_apply<T><<<blocks < 64 ? blocks : 64, kThreads, 0, s>>>(Minv, N, b, x));
+}
+
+template void dense_apply<float>(const double*, int, const float*, float*, cudaStream_t);
+template void dense_apply<double>(const double*, int, const double*, double*, cudaStream_t);
+
+}  // namespace mgp

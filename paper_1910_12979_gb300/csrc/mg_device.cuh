@@ -1,0 +1,57 @@
+// mg_device.cuh -- device-side helpers shared by the kernel translation units.
+#pragma once
+
+#include "mg_internal.cuh"
+
+namespace mgp {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Deterministic block reduction of NS doubles; thread 0 stores the block's
+// partial sums at partials[q * kRedBlocks + blockIdx.x].  The grid must have
+// exactly kRedBlocks blocks of kThreads threads.
+template <int NS>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* __restrict__ partials)
+{
+    __shared__ double sh[NS][kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        double x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[q][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            double x = (lane < kThreads / 32) ? sh[q][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) partials[q * kRedBlocks + blockIdx.x] = x;
+        }
+    }
+}
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// (i, j, k) of a flattened x-fastest index
+__device__ __forceinline__ void unflat(int t, int nx, int ny, int& i, int& j, int& k)
+{
+    i = t % nx;
+    const int q = t / nx;
+    j = q % ny;
+    k = q / ny;
+}
+
+template <typename T>
+__device__ __forceinline__ T recip(T d);
+template <>
+__device__ __forceinline__ float recip<float>(float d) { return d != 0.f ? 1.f / d : 0.f; }
+template <>
+__device__ __forceinline__ double recip<double>(double d) { return d != 0.0 ? 1.0 / d : 0.0; }
+
+}  // namespace mgp

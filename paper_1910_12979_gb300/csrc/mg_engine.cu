@@ -1,0 +1,839 @@
+// mg_engine.cu -- multigrid hierarchy, V-cycle and refinement drivers, C ABI.
+//
+// Host side of the library.  A handle owns one resident hierarchy in one
+// device workspace (caller-provided or cudaMalloc'd once at setup); solves
+// allocate nothing.  Convergence decisions read one small scalar block back
+// per iteration; everything else stays on the device.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.cuh"
+
+using namespace mgp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mg_status fail(mg_status s, const char* what)
+{
+    g_last_error = what;
+    return s;
+}
+
+mg_status cuda_fail(cudaError_t e, const char* where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return MG_ERR_CUDA;
+}
+
+#define MG_CK(call)                                          \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+// Bump allocator over the workspace; with base == nullptr it only counts.
+struct Bump {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// ---- live per-kernel event timing (mg_prof_*)
+struct ProfRec {
+    int id;
+    double bytes;
+    cudaEvent_t a, b;
+};
+struct Prof {
+    std::mutex mu;
+    bool on = false;
+    std::vector<ProfRec> recs;
+    size_t used = 0;
+};
+Prof& prof()
+{
+    static Prof p;
+    return p;
+}
+constexpr size_t kProfMax = 65536;
+
+// Returns a record index (or -1) after recording the start event on s.
+int prof_begin(int id, double bytes, cudaStream_t s)
+{
+    Prof& P = prof();
+    if (!P.on) return -1;
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (P.used >= kProfMax) return -1;
+    if (P.used == P.recs.size()) {
+        ProfRec r{};
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+        P.recs.push_back(r);
+    }
+    ProfRec& r = P.recs[P.used];
+    r.id = id;
+    r.bytes = bytes;
+    cudaEventRecord(r.a, s);
+    return (int)P.used++;
+}
+void prof_end(int idx, cudaStream_t s)
+{
+    if (idx < 0) return;
+    Prof& P = prof();
+    std::lock_guard<std::mutex> lk(P.mu);
+    cudaEventRecord(P.recs[idx].b, s);
+}
+
+struct Level {
+    int n[3];
+    double h[3];
+    int N[3];          // stored nodes (nodal)
+    size_t ncell, nvec;  // cells; unknown-vector length (cells or stored nodes)
+    double* B64[3];
+    double* invd64;
+    float* B32[3];
+    double* sig64;
+    float* sig32;
+    double *x64, *b64, *r64, *t64;
+    float *x32, *b32, *r32, *t32;
+};
+
+}  // namespace
+
+struct mg_handle {
+    mg_geometry geo;
+    mg_bc bcin;
+    mg_options opt;
+    BC3 bc;
+    int dim, loc, prec, singular;
+    int nlev;
+    Level lev[kMaxLevels];
+    double* f64;
+    double* phi_int;
+    double* A;
+    double* Minv;
+    int Nd;
+    double* partials;
+    DevScalars* d;
+    DevScalars* hs;  // pinned host copy
+    cudaStream_t stream;
+    void* ws;
+    size_t ws_bytes;
+    bool own_ws;
+    std::atomic<int> busy;
+};
+
+namespace {
+
+bool valid_bc(int v) { return v == MG_BC_PERIODIC || v == MG_BC_NEUMANN || v == MG_BC_DIRICHLET; }
+
+mg_status check_problem(const mg_geometry* g, const mg_bc* bc, const mg_options* o)
+{
+    if (!g || !bc || !o) return fail(MG_ERR_INVALID_ARG, "null geometry, bc or options");
+    if (g->dim != 2 && g->dim != 3) return fail(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (g->loc != MG_LOC_CELL && g->loc != MG_LOC_NODAL) return fail(MG_ERR_INVALID_ARG, "bad location");
+    for (int d = 0; d < g->dim; ++d) {
+        if (g->n[d] < 1 || !(g->h[d] > 0.0)) return fail(MG_ERR_INVALID_ARG, "n and h must be positive");
+        if (!valid_bc(bc->lo[d]) || !valid_bc(bc->hi[d])) return fail(MG_ERR_INVALID_ARG, "bad boundary kind");
+        if ((bc->lo[d] == MG_BC_PERIODIC) != (bc->hi[d] == MG_BC_PERIODIC))
+            return fail(MG_ERR_INVALID_ARG, "periodic boundaries must be paired");
+        if (g->loc == MG_LOC_NODAL && bc->lo[d] == MG_BC_PERIODIC && g->n[d] < 2)
+            return fail(MG_ERR_INVALID_ARG, "a periodic nodal axis needs at least 2 cells");
+    }
+    if (g->dim == 2 && g->n[2] != 1) return fail(MG_ERR_INVALID_ARG, "2-D grids need n[2] == 1");
+    double cells = 1.0;
+    for (int d = 0; d < g->dim; ++d) cells *= (double)(g->n[d] + 1);
+    if (cells > 2.0e9) return fail(MG_ERR_INVALID_ARG, "grid too large for 32-bit indexing");
+    if (g->loc == MG_LOC_NODAL) {
+        for (int d = 1; d < g->dim; ++d)
+            if (fabs(g->h[d] - g->h[0]) > 1e-12 * g->h[0])
+                return fail(MG_ERR_INVALID_ARG, "the nodal discretisation needs equal spacing on every axis");
+    }
+    if (o->prec != MG_PREC_FP64 && o->prec != MG_PREC_MIXED) return fail(MG_ERR_INVALID_ARG, "bad precision");
+    if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 16 || o->nu2 > 16)
+        return fail(MG_ERR_INVALID_ARG, "smoothing sweeps out of range");
+    if (o->max_iters < 1) return fail(MG_ERR_INVALID_ARG, "max_iters must be >= 1");
+    if (o->interp_order != 0 && o->interp_order != 1) return fail(MG_ERR_INVALID_ARG, "interp_order must be 0 or 1");
+    if (!(o->omega > 0.0 && o->omega <= 1.5)) return fail(MG_ERR_INVALID_ARG, "omega out of range");
+    return MG_OK;
+}
+
+int node_extent(const mg_bc* bc, int n, int d, int dim) { return d >= dim ? 1 : (bc->lo[d] == MG_BC_PERIODIC ? n : n + 1); }
+
+// Lay out the hierarchy (levels, arrays) in the bump allocator.
+mg_status plan(mg_handle* h, Bump& B)
+{
+    const int dim = h->dim;
+    const bool mixed = h->prec == MG_PREC_MIXED;
+    const bool nodal = h->loc == MG_LOC_NODAL;
+    int n[3] = {h->geo.n[0], h->geo.n[1], dim == 3 ? h->geo.n[2] : 1};
+    double hh[3] = {h->geo.h[0], h->geo.h[1], dim == 3 ? h->geo.h[2] : 1.0};
+    int L = 0;
+    const long long cmax = h->opt.coarsest_max > 0 ? h->opt.coarsest_max : 64;
+    for (;;) {
+        if (L >= kMaxLevels) return fail(MG_ERR_UNSUPPORTED, "too many levels");
+        Level& v = h->lev[L];
+        memset(&v, 0, sizeof(v));
+        for (int d = 0; d < 3; ++d) {
+            v.n[d] = n[d];
+            v.h[d] = hh[d];
+            v.N[d] = node_extent(&h->bcin, n[d], d, dim);
+        }
+        v.ncell = (size_t)n[0] * n[1] * n[2];
+        v.nvec = nodal ? (size_t)v.N[0] * v.N[1] * v.N[2] : v.ncell;
+        const size_t nc = v.ncell, nv = v.nvec;
+        if (!nodal) {
+            for (int d = 0; d < dim; ++d) {
+                size_t m = (size_t)(n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2));
+                v.B64[d] = B.take<double>(m);
+                if (mixed) v.B32[d] = B.take<float>(m);
+            }
+            if (!mixed) v.invd64 = B.take<double>(nc);
+        } else {
+            v.sig64 = B.take<double>(nc);
+            if (mixed) v.sig32 = B.take<float>(nc);
+            else v.invd64 = B.take<double>(nv);
+        }
+        if (mixed) {
+            v.x32 = B.take<float>(nv);
+            v.b32 = B.take<float>(nv);
+            if (nodal) { v.r32 = B.take<float>(nv); v.t32 = B.take<float>(nv); }
+        } else {
+            if (L > 0) { v.x64 = B.take<double>(nv); v.b64 = B.take<double>(nv); }
+            if (nodal) { v.r64 = B.take<double>(nv); v.t64 = B.take<double>(nv); }
+        }
+        ++L;
+        bool can = (long long)nc > cmax;
+        for (int d = 0; d < dim; ++d) can = can && (n[d] % 2 == 0) && (n[d] >= 4);
+        if (!can) break;
+        for (int d = 0; d < dim; ++d) { n[d] /= 2; hh[d] *= 2.0; }
+    }
+    h->nlev = L;
+    h->Nd = (int)h->lev[L - 1].nvec;
+    if (h->Nd > kMaxDense) return fail(MG_ERR_UNSUPPORTED, "the grid does not coarsen to a dense-solvable size (<= 512 unknowns)");
+    const int nd = h->Nd + (h->singular ? 1 : 0);
+    h->f64 = B.take<double>(h->lev[0].nvec);
+    h->phi_int = B.take<double>(h->lev[0].nvec);
+    h->A = B.take<double>((size_t)nd * 2 * nd);
+    h->Minv = B.take<double>((size_t)h->Nd * h->Nd);
+    h->partials = B.take<double>((size_t)kRedSlots * kRedBlocks);
+    h->d = B.take<DevScalars>(1);
+    return MG_OK;
+}
+
+template <typename T>
+CellLevel<T> cview(const mg_handle* h, int l);
+template <>
+CellLevel<double> cview<double>(const mg_handle* h, int l)
+{
+    const Level& v = h->lev[l];
+    return CellLevel<double>{v.n[0], v.n[1], v.n[2], h->bc, v.B64[0], v.B64[1], v.B64[2], v.invd64};
+}
+template <>
+CellLevel<float> cview<float>(const mg_handle* h, int l)
+{
+    const Level& v = h->lev[l];
+    return CellLevel<float>{v.n[0], v.n[1], v.n[2], h->bc, v.B32[0], v.B32[1], v.B32[2], nullptr};
+}
+
+template <typename T>
+NodeLevel<T> nview(const mg_handle* h, int l);
+template <>
+NodeLevel<double> nview<double>(const mg_handle* h, int l)
+{
+    const Level& v = h->lev[l];
+    return NodeLevel<double>{v.n[0], v.n[1], v.n[2], v.N[0], v.N[1], v.N[2], h->bc, v.sig64,
+                             1.0 / (v.h[0] * v.h[0]), v.invd64};
+}
+template <>
+NodeLevel<float> nview<float>(const mg_handle* h, int l)
+{
+    const Level& v = h->lev[l];
+    return NodeLevel<float>{v.n[0], v.n[1], v.n[2], v.N[0], v.N[1], v.N[2], h->bc, v.sig32,
+                            (float)(1.0 / (v.h[0] * v.h[0])), nullptr};
+}
+
+// Step a1: coefficients on every level and the dense inverse of the coarsest operator.
+mg_status build_coefficients(mg_handle* h, const mg_coeff* c)
+{
+    if (!c || !c->sigma) return fail(MG_ERR_INVALID_ARG, "sigma is required");
+    cudaStream_t s = h->stream;
+    const int dim = h->dim;
+    const bool mixed = h->prec == MG_PREC_MIXED;
+    if (h->loc == MG_LOC_CELL) {
+        Level& v0 = h->lev[0];
+        CellLevel<double> L0 = cview<double>(h, 0);
+        const bool explicit_faces = c->face[0] || c->face[1] || (dim == 3 && c->face[2]);
+        if (explicit_faces) {
+            for (int d = 0; d < dim; ++d)
+                if (!c->face[d]) return fail(MG_ERR_INVALID_ARG, "explicit faces must be given for every axis");
+            cell_scale_faces(dim, L0, c->face, v0.h, v0.B64[0], v0.B64[1], v0.B64[2], s);
+        } else {
+            cell_faces_from_sigma(dim, L0, c->sigma, v0.h, v0.B64[0], v0.B64[1], v0.B64[2], s);
+        }
+        for (int l = 1; l < h->nlev; ++l) {
+            Level& v = h->lev[l];
+            cell_coarsen_faces(dim, cview<double>(h, l - 1), cview<double>(h, l), v.B64[0], v.B64[1], v.B64[2], s);
+        }
+        for (int l = 0; l < h->nlev; ++l) {
+            Level& v = h->lev[l];
+            if (mixed) {
+                for (int d = 0; d < dim; ++d) {
+                    size_t m = (size_t)(v.n[0] + (d == 0)) * (v.n[1] + (d == 1)) * (v.n[2] + (d == 2));
+                    vec_to_f32(v.B32[d], v.B64[d], m, s);
+                }
+            } else {
+                CellLevel<double> V = cview<double>(h, l);
+                V.invd = nullptr;
+                cell_invdiag(dim, V, v.invd64, s);
+            }
+        }
+        const int n = h->Nd + h->singular;
+        cell_dense_assemble(dim, cview<double>(h, h->nlev - 1), h->A, 2 * n, s);
+    } else {
+        vec_copy_f64(h->lev[0].sig64, c->sigma, h->lev[0].ncell, s);
+        for (int l = 1; l < h->nlev; ++l)
+            node_coarsen_sigma(dim, nview<double>(h, l - 1), nview<double>(h, l), h->lev[l].sig64, s);
+        for (int l = 0; l < h->nlev; ++l) {
+            Level& v = h->lev[l];
+            if (mixed) {
+                vec_to_f32(v.sig32, v.sig64, v.ncell, s);
+            } else {
+                NodeLevel<double> V = nview<double>(h, l);
+                V.invd = nullptr;
+                node_invdiag(dim, V, v.invd64, s);
+            }
+        }
+        const int n = h->Nd + h->singular;
+        NodeLevel<double> C = nview<double>(h, h->nlev - 1);
+        C.invd = nullptr;
+        node_dense_assemble(dim, C, h->A, 2 * n, s);
+    }
+    dense_invert(h->A, h->Nd, h->singular, h->Minv, reinterpret_cast<int*>(&h->d->pad[0]), s);
+    MG_CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status readback(mg_handle* h)
+{
+    MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+    MG_CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+__global__ void k_keep(DevScalars* d, int fslot, int srcslot)
+{
+    if (fslot >= 0) {
+        d->fnorm2 = d->red[fslot];
+        d->fscale = d->fnorm2 > 0.0 ? sqrt(d->fnorm2) : 1.0;
+    }
+    if (srcslot >= 0) d->src2 = d->red[srcslot];
+}
+
+// f64 holds the system rhs, red[] holds {sum f, src2, sum f^2} from the rhs pass
+// (or {sum f, sum f^2} when from vec_sum_sq with fslot = 1).  Removes the mean
+// when singular and stores ||f||^2.
+void finish_rhs(mg_handle* h, int fslot, int srcslot)
+{
+    cudaStream_t s = h->stream;
+    if (srcslot >= 0) MGP_LAUNCH(k_keep<<<1, 1, 0, s>>>(h->d, -1, srcslot));
+    if (h->singular) {
+        const size_t n = h->lev[0].nvec;
+        vec_sub_mean(h->f64, n, &h->d->red[0], (double)n, s);
+        vec_sum_sq(h->f64, n, h->partials, s);
+        reduce_finalize(h->partials, 2, h->d->red, s);
+        fslot = 1;
+    }
+    MGP_LAUNCH(k_keep<<<1, 1, 0, s>>>(h->d, fslot, -1));
+}
+
+// ||f - L phi||^2 -> d->rnorm2; optional FP32 copy of the residual / fscale.
+void residual64(mg_handle* h, const double* phi, float* r32)
+{
+    cudaStream_t s = h->stream;
+    const int pr = prof_begin(MG_PROF_RESID64, (24.0 + (r32 ? 4.0 : 0.0)) * h->lev[0].nvec, s);
+    if (h->loc == MG_LOC_CELL)
+        cell_resid64(h->dim, cview<double>(h, 0), phi, h->f64, r32, &h->d->fscale, h->partials, s);
+    else
+        node_resid64(h->dim, nview<double>(h, 0), phi, h->f64, r32, &h->d->fscale, h->partials, s);
+    prof_end(pr, s);
+    reduce_finalize(h->partials, 1, &h->d->rnorm2, s);
+}
+
+template <typename T>
+T* lx(mg_handle* h, int l);
+template <>
+double* lx<double>(mg_handle* h, int l) { return h->lev[l].x64; }
+template <>
+float* lx<float>(mg_handle* h, int l) { return h->lev[l].x32; }
+template <typename T>
+T* lb(mg_handle* h, int l);
+template <>
+double* lb<double>(mg_handle* h, int l) { return h->lev[l].b64; }
+template <>
+float* lb<float>(mg_handle* h, int l) { return h->lev[l].b32; }
+template <typename T>
+T* lr(mg_handle* h, int l);
+template <>
+double* lr<double>(mg_handle* h, int l) { return h->lev[l].r64; }
+template <>
+float* lr<float>(mg_handle* h, int l) { return h->lev[l].r32; }
+template <typename T>
+T* lt(mg_handle* h, int l);
+template <>
+double* lt<double>(mg_handle* h, int l) { return h->lev[l].t64; }
+template <>
+float* lt<float>(mg_handle* h, int l) { return h->lev[l].t32; }
+
+template <typename T>
+void zero(T* p, size_t n, cudaStream_t s)
+{
+    cudaMemsetAsync(p, 0, n * sizeof(T), s);
+}
+
+// One red-black colour pass; the finest level's passes are timed when profiling.
+template <typename T>
+void smooth_pass(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, int color)
+{
+    const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * h->lev[0].ncell, h->stream) : -1;
+    cell_gsrb<T>(h->dim, V, x, b, color, h->stream);
+    prof_end(pr, h->stream);
+}
+
+// One V-cycle on L x0 = b0 (level 0 arrays given), cell-centred.
+template <typename T>
+void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
+{
+    cudaStream_t s = h->stream;
+    const int dim = h->dim, L = h->nlev;
+    auto X = [&](int l) { return l == 0 ? x0 : lx<T>(h, l); };
+    auto Bv = [&](int l) { return l == 0 ? b0 : (const T*)lb<T>(h, l); };
+    for (int l = 0; l < L - 1; ++l) {
+        if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
+        const CellLevel<T> V = cview<T>(h, l);
+        for (int k = 0; k < h->opt.nu1; ++k) {
+            smooth_pass<T>(h, l, V, X(l), Bv(l), 0);
+            smooth_pass<T>(h, l, V, X(l), Bv(l), 1);
+        }
+        const int pr = l == 0 ? prof_begin(MG_PROF_CELL_RESTRICT_FINE,
+                                           (3.0 + 1.0 / (1 << dim)) * sizeof(T) * h->lev[0].ncell, s) : -1;
+        cell_resid_restrict<T>(dim, V, X(l), Bv(l), lb<T>(h, l + 1), s);
+        prof_end(pr, s);
+    }
+    dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
+    for (int l = L - 2; l >= 0; --l) {
+        const CellLevel<T> V = cview<T>(h, l);
+        cell_prolong_add<T>(dim, V, cview<T>(h, l + 1), X(l), X(l + 1), h->opt.interp_order, s);
+        for (int k = 0; k < h->opt.nu2; ++k) {
+            smooth_pass<T>(h, l, V, X(l), Bv(l), 1);
+            smooth_pass<T>(h, l, V, X(l), Bv(l), 0);
+        }
+    }
+}
+
+template <typename T>
+void node_smooth(mg_handle* h, int l, T* x, const T* b, int sweeps)
+{
+    cudaStream_t s = h->stream;
+    const NodeLevel<T> V = nview<T>(h, l);
+    T* t = lt<T>(h, l);
+    const T om = (T)h->opt.omega;
+    for (int k = 0; k < sweeps; ++k) {
+        const int pr = l == 0 ? prof_begin(MG_PROF_NODE_SMOOTH_FINE, 4.0 * sizeof(T) * h->lev[0].nvec, s) : -1;
+        if (k % 2 == 0) node_jacobi<T>(h->dim, V, x, t, b, om, s);
+        else node_jacobi<T>(h->dim, V, t, x, b, om, s);
+        prof_end(pr, s);
+    }
+    if (sweeps % 2 == 1) cudaMemcpyAsync(x, t, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
+}
+
+template <typename T>
+void vcycle_node(mg_handle* h, T* x0, const T* b0, bool zero_init)
+{
+    cudaStream_t s = h->stream;
+    const int dim = h->dim, L = h->nlev;
+    auto X = [&](int l) { return l == 0 ? x0 : lx<T>(h, l); };
+    auto Bv = [&](int l) { return l == 0 ? b0 : (const T*)lb<T>(h, l); };
+    for (int l = 0; l < L - 1; ++l) {
+        if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
+        node_smooth<T>(h, l, X(l), Bv(l), h->opt.nu1);
+        node_resid<T>(dim, nview<T>(h, l), X(l), Bv(l), lr<T>(h, l), s);
+        node_restrict<T>(dim, nview<T>(h, l), nview<T>(h, l + 1), lr<T>(h, l), lb<T>(h, l + 1), s);
+    }
+    dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
+    for (int l = L - 2; l >= 0; --l) {
+        node_prolong_add<T>(dim, nview<T>(h, l), nview<T>(h, l + 1), X(l), X(l + 1), s);
+        node_smooth<T>(h, l, X(l), Bv(l), h->opt.nu2);
+    }
+}
+
+// Remove the mean of phi (singular problems).
+void gauge(mg_handle* h, double* phi)
+{
+    cudaStream_t s = h->stream;
+    const size_t n = h->lev[0].nvec;
+    vec_sum_sq(phi, n, h->partials, s);
+    reduce_finalize(h->partials, 2, h->d->red, s);
+    vec_sub_mean(phi, n, &h->d->red[0], (double)n, s);
+}
+
+// Iterate on L phi = f64 (rhs and ||f|| already prepared on the device).
+mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
+{
+    cudaStream_t s = h->stream;
+    const bool mixed = h->prec == MG_PREC_MIXED;
+    const bool nodal = h->loc == MG_LOC_NODAL;
+    if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), phi, s);
+    float* r32 = mixed ? h->lev[0].b32 : nullptr;
+    residual64(h, phi, r32);
+    mg_status rc = readback(h);
+    if (rc != MG_OK) return rc;
+    if (*reinterpret_cast<int*>(&h->hs->pad[0]) != 0)
+        return fail(MG_ERR_UNSUPPORTED, "the coarsest-level operator is singular");
+    const double fn2 = h->hs->fnorm2;
+    if (st) { st->rhs_norm = sqrt(fn2); st->iters = 0; st->rel_resid = 0.0; }
+    if (fn2 == 0.0) {
+        zero(phi, h->lev[0].nvec, s);
+        return MG_OK;
+    }
+    double rel = sqrt(h->hs->rnorm2 / fn2);
+    const double rel0 = rel;
+    double best = rel;
+    int stall = 0, it = 0;
+    mg_status status = MG_OK;
+    while (rel > tol) {
+        if (it >= h->opt.max_iters) { status = MG_ERR_NOT_CONVERGED; break; }
+        if (mixed) {
+            float* e = h->lev[0].x32;
+            if (nodal) vcycle_node<float>(h, e, h->lev[0].b32, true);
+            else vcycle_cell<float>(h, e, h->lev[0].b32, true);
+            vec_axpy_f32(phi, e, &h->d->fscale, h->lev[0].nvec, s);
+        } else {
+            if (nodal) vcycle_node<double>(h, phi, h->f64, false);
+            else vcycle_cell<double>(h, phi, h->f64, false);
+        }
+        ++it;
+        residual64(h, phi, r32);
+        rc = readback(h);
+        if (rc != MG_OK) return rc;
+        rel = sqrt(h->hs->rnorm2 / fn2);
+        if (!isfinite(rel) || rel > 1e6 * (rel0 > 1.0 ? rel0 : 1.0)) { status = MG_ERR_DIVERGED; break; }
+        if (rel < 0.9 * best) { best = rel; stall = 0; }
+        else if (++stall >= 4) { status = rel <= tol ? MG_OK : MG_ERR_NOT_CONVERGED; break; }
+        if (rel < best) best = rel;
+    }
+    if (h->singular) gauge(h, phi);
+    if (st) { st->iters = it; st->rel_resid = rel; }
+    if (status != MG_OK) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "stopped after %d iterations at relative residual %.3e (tol %.3e)", it, rel, tol);
+        g_last_error = buf;
+    }
+    return status;
+}
+
+struct BusyGuard {
+    mg_handle* h;
+    bool ok;
+    explicit BusyGuard(mg_handle* hh) : h(hh), ok(hh->busy.exchange(1) == 0) {}
+    ~BusyGuard()
+    {
+        if (ok) h->busy.store(0);
+    }
+};
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+void mg_default_options(mg_options* o)
+{
+    if (!o) return;
+    o->prec = MG_PREC_MIXED;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->max_iters = 100;
+    o->coarsest_max = 64;
+    o->interp_order = 1;
+    o->omega = 0.9;
+    o->stream = nullptr;
+}
+
+static mg_status init_handle(mg_handle* h, const mg_geometry* g, const mg_bc* bc, const mg_options* o)
+{
+    h->geo = *g;
+    h->bcin = *bc;
+    h->opt = *o;
+    h->dim = g->dim;
+    h->loc = g->loc;
+    h->prec = o->prec;
+    h->singular = 1;
+    for (int d = 0; d < 3; ++d) {
+        h->bc.lo[d] = d < g->dim ? bc->lo[d] : BCN;
+        h->bc.hi[d] = d < g->dim ? bc->hi[d] : BCN;
+        if (d < g->dim && (bc->lo[d] == MG_BC_DIRICHLET || bc->hi[d] == MG_BC_DIRICHLET)) h->singular = 0;
+    }
+    h->stream = (cudaStream_t)o->stream;
+    return MG_OK;
+}
+
+mg_status mg_hierarchy_bytes(const mg_geometry* g, const mg_bc* bc, const mg_options* o, size_t* bytes)
+{
+    mg_status rc = check_problem(g, bc, o);
+    if (rc != MG_OK) return rc;
+    if (!bytes) return fail(MG_ERR_INVALID_ARG, "bytes is null");
+    mg_handle* h = new (std::nothrow) mg_handle();
+    if (!h) return fail(MG_ERR_OOM, "host allocation failed");
+    init_handle(h, g, bc, o);
+    Bump B;
+    rc = plan(h, B);
+    *bytes = B.off + 256;
+    delete h;
+    return rc;
+}
+
+mg_status mg_setup(const mg_coeff* c, const mg_geometry* g, const mg_bc* bc, const mg_options* o, void* workspace,
+                   size_t workspace_bytes, mg_handle** out)
+{
+    if (!out) return fail(MG_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    mg_status rc = check_problem(g, bc, o);
+    if (rc != MG_OK) return rc;
+    mg_handle* h = new (std::nothrow) mg_handle();
+    if (!h) return fail(MG_ERR_OOM, "host allocation failed");
+    init_handle(h, g, bc, o);
+    Bump dry;
+    rc = plan(h, dry);
+    if (rc != MG_OK) { delete h; return rc; }
+    const size_t need = dry.off + 256;
+    if (workspace) {
+        if (workspace_bytes < need) { delete h; return fail(MG_ERR_OOM, "workspace smaller than mg_hierarchy_bytes()"); }
+        if (((uintptr_t)workspace & 255) != 0) { delete h; return fail(MG_ERR_INVALID_ARG, "workspace must be 256-byte aligned"); }
+        h->ws = workspace;
+        h->own_ws = false;
+    } else {
+        cudaError_t e = cudaMalloc(&h->ws, need);
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaMalloc(workspace)"); }
+        h->own_ws = true;
+    }
+    h->ws_bytes = need;
+    if (cudaMallocHost((void**)&h->hs, sizeof(DevScalars)) != cudaSuccess) {
+        if (h->own_ws) cudaFree(h->ws);
+        delete h;
+        return fail(MG_ERR_OOM, "pinned host allocation failed");
+    }
+    Bump real;
+    real.base = (char*)h->ws;
+    plan(h, real);
+    cudaMemsetAsync(h->d, 0, sizeof(DevScalars), h->stream);
+    // zero every work vector once (Dirichlet planes of nodal vectors stay 0)
+    cudaMemsetAsync(h->ws, 0, need - 256, h->stream);
+    rc = build_coefficients(h, c);
+    if (rc != MG_OK) { mg_destroy(h); return rc; }
+    *out = h;
+    return MG_OK;
+}
+
+mg_status mg_update_coeff(mg_handle* h, const mg_coeff* c)
+{
+    if (!h) return fail(MG_ERR_INVALID_ARG, "null handle");
+    BusyGuard g(h);
+    if (!g.ok) return fail(MG_ERR_BUSY, "handle in use");
+    return build_coefficients(h, c);
+}
+
+mg_status mg_set_stream(mg_handle* h, void* stream)
+{
+    if (!h) return fail(MG_ERR_INVALID_ARG, "null handle");
+    h->stream = (cudaStream_t)stream;
+    h->opt.stream = stream;
+    return MG_OK;
+}
+
+mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_stats* st)
+{
+    if (!h || !rhs || !phi) return fail(MG_ERR_INVALID_ARG, "null handle, rhs or phi");
+    if (!(tol > 0.0)) return fail(MG_ERR_INVALID_ARG, "tol must be positive");
+    BusyGuard g(h);
+    if (!g.ok) return fail(MG_ERR_BUSY, "handle in use");
+    const double t0 = now_ms();
+    cudaStream_t s = h->stream;
+    const size_t n = h->lev[0].nvec;
+    vec_copy_f64(h->f64, rhs, n, s);
+    if (h->loc == MG_LOC_NODAL) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), h->f64, s);
+    vec_sum_sq(h->f64, n, h->partials, s);
+    reduce_finalize(h->partials, 2, h->d->red, s);
+    finish_rhs(h, 1, -1);
+    mg_stats local;
+    memset(&local, 0, sizeof local);
+    mg_status rc = solve_core(h, phi, tol, &local);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mg_solve");
+    local.ms = now_ms() - t0;
+    local.status = rc;
+    if (st) *st = local;
+    return rc;
+}
+
+mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* b0, const double* S, double* phi, double tol,
+                     mg_stats* st)
+{
+    if (!h || !U || !b0 || !b0->cell || !S) return fail(MG_ERR_INVALID_ARG, "null argument");
+    for (int d = 0; d < h->dim; ++d) {
+        if (!U[d]) return fail(MG_ERR_INVALID_ARG, "U[d] is null");
+        if (h->loc == MG_LOC_CELL && !b0->face[d]) return fail(MG_ERR_INVALID_ARG, "beta0 faces are required (MAC)");
+    }
+    if (!(tol > 0.0)) return fail(MG_ERR_INVALID_ARG, "tol must be positive");
+    BusyGuard g(h);
+    if (!g.ok) return fail(MG_ERR_BUSY, "handle in use");
+    const double t0 = now_ms();
+    cudaStream_t s = h->stream;
+    const int dim = h->dim;
+    const Level& v0 = h->lev[0];
+    const double* Uc[3] = {U[0], U[1], dim == 3 ? U[2] : nullptr};
+    if (phi == nullptr) {
+        phi = h->phi_int;
+        zero(phi, v0.nvec, s);
+    }
+    // a2: f = D(beta0 U) - beta0 S
+    if (h->loc == MG_LOC_CELL) cell_rhs(dim, cview<double>(h, 0), v0.h, Uc, b0->face, b0->cell, S, h->f64, h->partials, s);
+    else node_rhs(dim, nview<double>(h, 0), v0.h[0], Uc, b0->cell, S, h->f64, h->partials, s);
+    reduce_finalize(h->partials, 3, h->d->red, s);
+    finish_rhs(h, 2, 1);
+    mg_stats local;
+    memset(&local, 0, sizeof local);
+    // a3-a8
+    mg_status rc = solve_core(h, phi, tol, &local);
+    if (rc == MG_OK || rc == MG_ERR_NOT_CONVERGED) {
+        // a9: projection update; a10: constraint
+        if (h->loc == MG_LOC_CELL) {
+            cell_project(dim, cview<double>(h, 0), v0.h, phi, b0->face, U, s);
+            cell_rhs(dim, cview<double>(h, 0), v0.h, Uc, b0->face, b0->cell, S, nullptr, h->partials, s);
+        } else {
+            node_project(dim, nview<double>(h, 0), v0.h[0], phi, b0->cell, U, s);
+            node_rhs(dim, nview<double>(h, 0), v0.h[0], Uc, b0->cell, S, nullptr, h->partials, s);
+        }
+        reduce_finalize(h->partials, 3, h->d->red, s);
+        mg_status r2 = readback(h);
+        if (r2 != MG_OK) return r2;
+        const double src2 = h->hs->red[1], con2 = h->hs->red[2];
+        local.src_norm = sqrt(src2);
+        local.rel_constraint = src2 > 0.0 ? sqrt(con2 / src2) : sqrt(con2);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mg_project");
+    local.ms = now_ms() - t0;
+    local.status = rc;
+    if (st) *st = local;
+    return rc;
+}
+
+mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double* const* phi, const double* tol,
+                         int count, mg_stats* st)
+{
+    if (count < 0 || (count > 0 && (!hs || !rhs || !phi || !tol))) return fail(MG_ERR_INVALID_ARG, "bad batch");
+    mg_status worst = MG_OK;
+    for (int i = 0; i < count; ++i) {
+        mg_status rc = mg_solve(hs[i], rhs[i], phi[i], tol[i], st ? &st[i] : nullptr);
+        if (rc != MG_OK && worst == MG_OK) worst = rc;
+    }
+    return worst;
+}
+
+mg_status mg_apply(mg_handle* h, const double* phi, double* out)
+{
+    if (!h || !phi || !out) return fail(MG_ERR_INVALID_ARG, "null argument");
+    if (h->loc == MG_LOC_CELL) cell_apply64(h->dim, cview<double>(h, 0), phi, out, h->stream);
+    else node_apply64(h->dim, nview<double>(h, 0), phi, out, h->stream);
+    MG_CK(cudaGetLastError());
+    MG_CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+void mg_destroy(mg_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->hs) cudaFreeHost(h->hs);
+    delete h;
+}
+
+const char* mg_strerror(mg_status s)
+{
+    switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID_ARG: return "invalid argument";
+    case MG_ERR_OOM: return "out of device memory";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_NOT_CONVERGED: return "not converged";
+    case MG_ERR_DIVERGED: return "diverged";
+    case MG_ERR_INCOMPATIBLE_RHS: return "incompatible right-hand side";
+    case MG_ERR_TIMEOUT: return "timeout";
+    case MG_ERR_BUSY: return "handle busy";
+    case MG_ERR_UNSUPPORTED: return "unsupported problem";
+    }
+    return "unknown status";
+}
+
+const char* mg_last_error(void) { return g_last_error.c_str(); }
+
+long long mg_launch_count(void) { return launch_count(); }
+
+void mg_prof_enable(int on)
+{
+    Prof& P = prof();
+    std::lock_guard<std::mutex> lk(P.mu);
+    P.used = 0;
+    P.on = on != 0;
+}
+
+mg_status mg_prof_query(int kernel, double* total_ms, int* launches, double* bytes)
+{
+    if (kernel < 0 || kernel >= MG_PROF_COUNT) return fail(MG_ERR_INVALID_ARG, "unknown kernel class");
+    Prof& P = prof();
+    std::lock_guard<std::mutex> lk(P.mu);
+    double ms = 0.0, by = 0.0;
+    int cnt = 0;
+    for (size_t i = 0; i < P.used; ++i) {
+        const ProfRec& r = P.recs[i];
+        if (r.id != kernel) continue;
+        float t = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        ms += t;
+        by += r.bytes;
+        ++cnt;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = cnt;
+    if (bytes) *bytes = by;
+    return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// mg_internal.cuh -- shared declarations of the CUDA projection-solve library.
+//
+// Everything here is internal to libmgproj.so; the public surface is include/mg.h.
+// Kernels are plain CUDA C++ for sm_103a: the multigrid path is a sparse stencil,
+// so it is bound by HBM bandwidth (FP32 levels) or the FP64 pipe (FP64 residual),
+// never by a dense contraction; no tensor-core instruction appears anywhere.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mgp {
+
+enum { BCP = 0, BCN = 1, BCD = 2 };
+
+constexpr int kRedBlocks = 608;     // 4 x 152 SMs: fixed grid of every reduction kernel
+constexpr int kRedSlots = 4;        // quantities one reduction pass may accumulate
+constexpr int kMaxLevels = 16;
+constexpr int kMaxDense = 512;      // unknowns of the coarsest (dense) level
+
+struct BC3 {
+    int lo[3];
+    int hi[3];
+};
+
+// One cell-centred level: n cells per axis, face coefficients pre-scaled by 1/h_d^2.
+template <typename T>
+struct CellLevel {
+    int nx, ny, nz;
+    BC3 bc;
+    const T* bx;
+    const T* by;
+    const T* bz;
+    const T* invd;  // optional 1/diagonal (FP64 levels); nullptr -> computed
+};
+
+// One nodal level: n cells per axis, N nodes per axis, sigma per cell, h^-2.
+template <typename T>
+struct NodeLevel {
+    int nx, ny, nz;     // cells
+    int Nx, Ny, Nz;     // stored nodes
+    BC3 bc;
+    const T* sigma;
+    T ih2;
+    const T* invd;      // optional 1/diagonal; nullptr -> computed
+};
+
+// Device scalars of one solve (reduction results).
+struct DevScalars {
+    double red[kRedSlots];     // last reduction results
+    double fnorm2;             // ||f||^2 of the system being solved
+    double rnorm2;             // ||f - L phi||^2, latest
+    double fscale;             // r32 = (f - L phi) / fscale in mixed refinement
+    double mean;               // mean removed from f (singular problems)
+    double src2;               // ||beta0 S||^2 or ||S_N||^2
+    double con2;               // post-projection constraint^2
+    double pad[6];
+};
+
+// Every kernel launch of the library goes through MGP_LAUNCH, which counts it
+// (mg_launch_count reports the total).
+void note_launch();
+long long launch_count();
+#define MGP_LAUNCH(...) (::mgp::note_launch(), __VA_ARGS__)
+
+// ---------------------------------------------------------------- launchers
+// Cell-centred (MAC) system.  dim = 2 or 3.  All launches are asynchronous on s.
+void cell_faces_from_sigma(int dim, const CellLevel<double>& L, const double* sigma, const double* h,
+                           double* bx, double* by, double* bz, cudaStream_t s);
+void cell_scale_faces(int dim, const CellLevel<double>& L, const double* const face[3], const double* h,
+                      double* bx, double* by, double* bz, cudaStream_t s);
+void cell_coarsen_faces(int dim, const CellLevel<double>& F, const CellLevel<double>& C, double* bx, double* by,
+                        double* bz, cudaStream_t s);
+void cell_invdiag(int dim, const CellLevel<double>& L, double* invd, cudaStream_t s);
+template <typename T>
+void cell_gsrb(int dim, const CellLevel<T>& L, T* x, const T* b, int color, cudaStream_t s);
+template <typename T>
+void cell_resid_restrict(int dim, const CellLevel<T>& F, const T* x, const T* b, T* bc, cudaStream_t s);
+template <typename T>
+void cell_prolong_add(int dim, const CellLevel<T>& F, const CellLevel<T>& C, T* xf, const T* xc, int order,
+                      cudaStream_t s);
+// r = b - L x in FP64; optional FP32 copy r/scale; ||r||^2 partials
+void cell_resid64(int dim, const CellLevel<double>& L, const double* x, const double* b, float* r32,
+                  const double* scale, double* partials, cudaStream_t s);
+void cell_apply64(int dim, const CellLevel<double>& L, const double* x, double* out, cudaStream_t s);
+// f = D(beta0 U) - beta0 S with partials {sum f, sum (beta0 S)^2, sum f^2}; f may be null
+void cell_rhs(int dim, const CellLevel<double>& L, const double* h, const double* const U[3],
+              const double* const b0f[3], const double* b0c, const double* S, double* f, double* partials,
+              cudaStream_t s);
+void cell_project(int dim, const CellLevel<double>& L, const double* h, const double* phi,
+                  const double* const b0f[3], double* const U[3], cudaStream_t s);
+template <typename T>
+void cell_dense_assemble(int dim, const CellLevel<T>& L, double* A, int lda, cudaStream_t s);
+
+// Nodal system.
+void node_coarsen_sigma(int dim, const NodeLevel<double>& F, const NodeLevel<double>& C, double* sc,
+                        cudaStream_t s);
+void node_invdiag(int dim, const NodeLevel<double>& L, double* invd, cudaStream_t s);
+template <typename T>
+void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, cudaStream_t s);
+template <typename T>
+void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, cudaStream_t s);
+template <typename T>
+void node_restrict(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, const T* rf, T* bc, cudaStream_t s);
+template <typename T>
+void node_prolong_add(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, T* xf, const T* xc, cudaStream_t s);
+void node_resid64(int dim, const NodeLevel<double>& L, const double* x, const double* b, float* r32,
+                  const double* scale, double* partials, cudaStream_t s);
+void node_apply64(int dim, const NodeLevel<double>& L, const double* x, double* out, cudaStream_t s);
+void node_rhs(int dim, const NodeLevel<double>& L, double h, const double* const U[3], const double* b0,
+              const double* S, double* f, double* partials, cudaStream_t s);
+void node_project(int dim, const NodeLevel<double>& L, double h, const double* phi, const double* b0,
+                  double* const U[3], cudaStream_t s);
+template <typename T>
+void node_dense_assemble(int dim, const NodeLevel<T>& L, double* A, int lda, cudaStream_t s);
+// zero the Dirichlet node planes of x
+template <typename T>
+void node_zero_dirichlet(int dim, const NodeLevel<T>& L, T* x, cudaStream_t s);
+
+// Generic helpers.
+void reduce_finalize(const double* partials, int nslots, double* out, cudaStream_t s);
+// partials {sum v, sum v^2} of v[0..n)
+void vec_sum_sq(const double* v, size_t n, double* partials, cudaStream_t s);
+// v[i] -= *mean (mean = sum / count read from a device scalar)
+void vec_sub_mean(double* v, size_t n, const double* sum, double count, cudaStream_t s);
+void vec_copy_f64(double* dst, const double* src, size_t n, cudaStream_t s);
+void vec_to_f32(float* dst, const double* src, size_t n, cudaStream_t s);
+void vec_zero_f32(float* v, size_t n, cudaStream_t s);
+void vec_zero_f64(double* v, size_t n, cudaStream_t s);
+// phi += (*scale) * e
+void vec_axpy_f32(double* phi, const float* e, const double* scale, size_t n, cudaStream_t s);
+// dense coarsest solve: A holds the assembled N x N operator with row stride
+// 2 (N + singular); Minv = leading N x N block of the (bordered) inverse
+int dense_invert(double* A, int N, int singular, double* Minv, int* info, cudaStream_t s);
+template <typename T>
+void dense_apply(const double* Minv, int N, const T* b, T* x, cudaStream_t s);
+// scalars: s->fscale = sqrt(s->fnorm2) (or 1 if 0)
+void scalars_set_fscale(DevScalars* d, cudaStream_t s);
+
+}  // namespace mgp

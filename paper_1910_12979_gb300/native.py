@@ -1,0 +1,220 @@
+"""ctypes binding of libmgproj.so (include/mg.h): argument marshalling only.
+
+Every function here has the name and the argument order of the C entry point
+it wraps.  No arithmetic of the solve happens in Python: the library's CUDA
+kernels do all of it.  Loading fails loudly when the library cannot be built
+or found; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+MG_OK, MG_ERR_INVALID_ARG, MG_ERR_OOM, MG_ERR_CUDA, MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED, \
+    MG_ERR_INCOMPATIBLE_RHS, MG_ERR_TIMEOUT, MG_ERR_BUSY, MG_ERR_UNSUPPORTED = range(10)
+MG_BC_PERIODIC, MG_BC_NEUMANN, MG_BC_DIRICHLET = 0, 1, 2
+MG_LOC_CELL, MG_LOC_NODAL = 0, 1
+MG_PREC_FP64, MG_PREC_MIXED = 0, 1
+
+BC = {"periodic": MG_BC_PERIODIC, "neumann": MG_BC_NEUMANN, "dirichlet": MG_BC_DIRICHLET}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class mg_geometry(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double * 3), ("loc", ctypes.c_int)]
+
+
+class mg_bc(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3)]
+
+
+class mg_coeff(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_void_p), ("face", ctypes.c_void_p * 3)]
+
+
+class mg_beta0(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_void_p), ("face", ctypes.c_void_p * 3)]
+
+
+class mg_options(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("coarsest_max", ctypes.c_int), ("interp_order", ctypes.c_int), ("omega", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class mg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_resid", ctypes.c_double), ("rel_constraint", ctypes.c_double),
+                ("rhs_norm", ctypes.c_double), ("src_norm", ctypes.c_double), ("ms", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# (name, restype, argtypes) of every entry point declared in include/mg.h
+SIGNATURES = [
+    ("mg_default_options", None, [ctypes.POINTER(mg_options)]),
+    ("mg_hierarchy_bytes", ctypes.c_int, [ctypes.POINTER(mg_geometry), ctypes.POINTER(mg_bc),
+                                          ctypes.POINTER(mg_options), ctypes.POINTER(ctypes.c_size_t)]),
+    ("mg_setup", ctypes.c_int, [ctypes.POINTER(mg_coeff), ctypes.POINTER(mg_geometry), ctypes.POINTER(mg_bc),
+                                ctypes.POINTER(mg_options), ctypes.c_void_p, ctypes.c_size_t,
+                                ctypes.POINTER(ctypes.c_void_p)]),
+    ("mg_update_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(mg_coeff)]),
+    ("mg_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                ctypes.POINTER(mg_stats)]),
+    ("mg_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p * 3, ctypes.POINTER(mg_beta0), ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(mg_stats)]),
+    ("mg_solve_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                      ctypes.POINTER(mg_stats)]),
+    ("mg_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("mg_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mg_destroy", None, [ctypes.c_void_p]),
+    ("mg_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("mg_last_error", ctypes.c_char_p, []),
+    ("mg_prof_enable", None, [ctypes.c_int]),
+    ("mg_launch_count", ctypes.c_longlong, []),
+    ("mg_prof_query", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double)]),
+]
+
+MG_PROF_CELL_SMOOTH_FINE, MG_PROF_RESID64, MG_PROF_NODE_SMOOTH_FINE, MG_PROF_CELL_RESTRICT_FINE = range(4)
+PROF_NAMES = {MG_PROF_CELL_SMOOTH_FINE: "cell_smooth_fine", MG_PROF_RESID64: "resid64",
+              MG_PROF_NODE_SMOOTH_FINE: "node_smooth_fine", MG_PROF_CELL_RESTRICT_FINE: "cell_restrict_fine"}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libmgproj.so (building it first when stale and nvcc is available)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_needed:
+        try:
+            path = _build.build()
+        except Exception as e:  # no nvcc, or a compile error: fail loudly unless a built library exists
+            if not os.path.exists(path):
+                raise ImportError(f"libmgproj.so is not built and cannot be built: {e}") from e
+    if not os.path.exists(path):
+        raise ImportError(f"libmgproj.so not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        self.status = status
+        msg = lib.mg_strerror(status).decode()
+        detail = lib.mg_last_error().decode()
+        super().__init__(f"{where}: {msg} ({detail})")
+
+
+def check(status, where, allow=(MG_OK,)):
+    if status not in allow:
+        raise MGError(status, where)
+    return status
+
+
+# thin wrappers with the C names ------------------------------------------------
+
+def mg_default_options():
+    o = mg_options()
+    load().mg_default_options(ctypes.byref(o))
+    return o
+
+
+def mg_hierarchy_bytes(geom, bc, opt):
+    n = ctypes.c_size_t(0)
+    check(load().mg_hierarchy_bytes(ctypes.byref(geom), ctypes.byref(bc), ctypes.byref(opt), ctypes.byref(n)),
+          "mg_hierarchy_bytes")
+    return n.value
+
+
+def mg_setup(coeff, geom, bc, opt, workspace_ptr, workspace_bytes):
+    h = ctypes.c_void_p()
+    check(load().mg_setup(ctypes.byref(coeff), ctypes.byref(geom), ctypes.byref(bc), ctypes.byref(opt),
+                          ctypes.c_void_p(workspace_ptr), ctypes.c_size_t(workspace_bytes), ctypes.byref(h)),
+          "mg_setup")
+    return h
+
+
+def mg_update_coeff(h, coeff):
+    return check(load().mg_update_coeff(h, ctypes.byref(coeff)), "mg_update_coeff")
+
+
+def mg_solve(h, rhs_ptr, phi_ptr, tol, allow=(MG_OK,)):
+    st = mg_stats()
+    rc = load().mg_solve(h, ctypes.c_void_p(rhs_ptr), ctypes.c_void_p(phi_ptr), ctypes.c_double(tol),
+                         ctypes.byref(st))
+    check(rc, "mg_solve", allow)
+    return st
+
+
+def mg_project(h, U_ptrs, beta0, S_ptr, phi_ptr, tol, allow=(MG_OK,)):
+    st = mg_stats()
+    arr = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(p) if p else None for p in U_ptrs])
+    rc = load().mg_project(h, arr, ctypes.byref(beta0), ctypes.c_void_p(S_ptr),
+                           ctypes.c_void_p(phi_ptr) if phi_ptr else None, ctypes.c_double(tol), ctypes.byref(st))
+    check(rc, "mg_project", allow)
+    return st
+
+
+def mg_solve_batch(handles, rhs_ptrs, phi_ptrs, tols, allow=(MG_OK,)):
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    R = (ctypes.c_void_p * n)(*rhs_ptrs)
+    P = (ctypes.c_void_p * n)(*phi_ptrs)
+    T = (ctypes.c_double * n)(*tols)
+    st = (mg_stats * n)()
+    rc = load().mg_solve_batch(H, R, P, T, n, st)
+    check(rc, "mg_solve_batch", allow)
+    return list(st)
+
+
+def mg_set_stream(h, stream_ptr):
+    return check(load().mg_set_stream(h, ctypes.c_void_p(stream_ptr)), "mg_set_stream")
+
+
+def mg_apply(h, phi_ptr, out_ptr):
+    return check(load().mg_apply(h, ctypes.c_void_p(phi_ptr), ctypes.c_void_p(out_ptr)), "mg_apply")
+
+
+def mg_destroy(h):
+    load().mg_destroy(h)
+
+
+def mg_strerror(s):
+    return load().mg_strerror(s).decode()
+
+
+def mg_last_error():
+    return load().mg_last_error().decode()
+
+
+def mg_launch_count():
+    return int(load().mg_launch_count())
+
+
+def mg_prof_enable(on):
+    load().mg_prof_enable(1 if on else 0)
+
+
+def mg_prof_query(kernel):
+    ms, n, by = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    check(load().mg_prof_query(kernel, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)), "mg_prof_query")
+    return {"ms": ms.value, "launches": n.value, "bytes": by.value}

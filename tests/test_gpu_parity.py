@@ -1,0 +1,273 @@
+"""GPU path versus the FP64 oracle, element by element, through the C ABI.
+
+Parity rule: rel-L2 error of phi (zero-mean gauge when singular) <= 1e-9 for
+the FP64 path and <= 1e-8 for mixed precision.  Both sides solve to a relative
+residual of 1e-12 here (tighter than the configs' 1e-10, so that the solver
+tolerance cannot hide a discrepancy), the oracle to its round-off floor.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1910_12979_gb300 import ProjectionSolver  # noqa: E402
+from paper_1910_12979_gb300 import native as N  # noqa: E402
+
+TOL = {"fp64": 1e-9, "mixed": 1e-8}
+DEV = "cuda:0"
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def H(t):
+    return t.detach().cpu().numpy()
+
+
+def relerr(a, b, mask=None):
+    if mask is not None:
+        a, b = a[mask], b[mask]
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def gauge(v, singular, mask=None):
+    if not singular:
+        return v
+    m = v[mask].mean() if mask is not None else v.mean()
+    return v - m
+
+
+def ogrid(O, geom):
+    return O.Grid.make(geom["n"], geom["bclo"], geom["bchi"], geom["h"])
+
+
+# ------------------------------------------------------------------ 2-D solve
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_manufactured_2d_solve(oracle, prec):
+    O = oracle
+    p = I.manufactured_2d(64)
+    g = ogrid(O, p["geom"])
+    ref, st = O.mac_solve_mg(g, O.mac_faces(g, p["sigma"]), p["f"])
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec=prec)
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    stats = s.solve(T(p["f"]), phi, tol=1e-12)
+    assert stats["rel_resid"] <= 1e-12
+    e = relerr(gauge(H(phi), True), gauge(ref, True))
+    assert e <= TOL[prec], e
+    # the discrete solution is second-order close to the manufactured phi
+    ex = p["phi_exact"] - p["phi_exact"].mean()
+    assert np.sqrt(np.mean((H(phi) - ex) ** 2)) < 2e-3
+
+
+# ------------------------------------------------- every boundary combination
+
+PAIRS = [("periodic", "periodic"), ("neumann", "neumann"), ("dirichlet", "dirichlet"), ("neumann", "dirichlet")]
+
+
+@pytest.mark.parametrize("loc", ["cell", "nodal"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_boundary_mixes_vs_oracle(oracle, loc, prec, dim):
+    O = oracle
+    rng = np.random.default_rng(100 + dim)
+    n = (16, 12) if dim == 2 else (8, 8, 12)
+    for combo in itertools.product(PAIRS, repeat=dim):
+        lo = tuple(c[0] for c in combo)
+        hi = tuple(c[1] for c in combo)
+        geom = I.geometry(n, lo, hi)
+        g = ogrid(O, geom)
+        sigma = np.exp(0.5 * rng.normal(size=g.cell_shape))
+        if loc == "cell":
+            f = rng.normal(size=g.cell_shape)
+            ref, _ = O.mac_solve_mg(g, O.mac_faces(g, sigma), f)
+            mask = None
+        else:
+            f = rng.normal(size=g.node_shape)
+            f[g.dirichlet_node_mask()] = 0
+            ref, _ = O.nodal_solve_mg(g, sigma, f)
+            mask = ~g.dirichlet_node_mask()
+        s = ProjectionSolver(geom, T(sigma), loc=loc, prec=prec, coarsest_max=8)
+        phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+        s.solve(T(f), phi, tol=1e-12)
+        got = H(phi)
+        e = relerr(gauge(got, g.singular, mask), gauge(ref, g.singular, mask))
+        assert e <= TOL[prec], (lo, hi, e)
+        if mask is not None:
+            assert np.all(got[~mask] == 0.0)
+        s.close()
+
+
+@pytest.mark.parametrize("loc", ["cell", "nodal"])
+def test_apply_matches_oracle(oracle, loc):
+    O = oracle
+    rng = np.random.default_rng(5)
+    geom = I.geometry((12, 10, 8), ("periodic", "neumann", "neumann"), ("periodic", "dirichlet", "dirichlet"))
+    g = ogrid(O, geom)
+    sigma = np.exp(rng.normal(size=g.cell_shape))
+    s = ProjectionSolver(geom, T(sigma), loc=loc, prec="fp64", coarsest_max=1000)
+    if loc == "cell":
+        x = rng.normal(size=g.cell_shape)
+        want = O.mac_apply(g, O.mac_faces(g, sigma), x)
+    else:
+        x = rng.normal(size=g.node_shape)
+        x[g.dirichlet_node_mask()] = 0
+        want = O.nodal_apply(g, sigma, x)
+    got = H(s.apply(T(x)))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+# --------------------------------------------------- projections (configs 2-3)
+
+@pytest.mark.parametrize("n", [32, 48])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_mac_projection_vs_oracle(oracle, n, prec):
+    O = oracle
+    p = I.stratified(n, seed=2, contrast=1e3)
+    g = ogrid(O, p["geom"])
+    ref = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-14)
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec=prec)
+    U = [T(u) for u in p["U_mac"]]
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.project(U, T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]], phi=phi, tol=1e-12)
+    e = relerr(H(phi), ref["phi"])
+    assert e <= TOL[prec], e
+    for d in range(3):
+        assert relerr(H(U[d]), ref["U"][d]) <= TOL[prec]
+    # post-projection constraint (exact for MAC up to the solver residual)
+    assert st["rel_constraint"] < 1e-8
+    div = O.mac_rhs(g, p["beta0"], p["beta0_face"], [H(u) for u in U], p["S"])
+    assert abs(np.linalg.norm(div) / ref["src_norm"] - st["rel_constraint"]) <= 1e-3 * st["rel_constraint"] + 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_nodal_projection_vs_oracle(oracle, prec):
+    O = oracle
+    p = I.stratified(32, seed=2, contrast=1e3)
+    g = ogrid(O, p["geom"])
+    ref = O.nodal_project(g, p["sigma"], p["beta0"], p["U_cell"], p["S"], tol=1e-14)
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="nodal", prec=prec)
+    U = [T(u) for u in p["U_cell"]]
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.project(U, T(p["beta0"]), T(p["S"]), phi=phi, tol=1e-12)
+    assert relerr(H(phi), ref["phi"]) <= TOL[prec]
+    for d in range(3):
+        assert relerr(H(U[d]), ref["U"][d]) <= TOL[prec]
+    assert st["rel_constraint"] == pytest.approx(ref["constraint"], rel=1e-6)
+
+
+def test_polytrope_dirichlet_projection(oracle):
+    O = oracle
+    p = I.polytrope_star(32, seed=5)
+    g = ogrid(O, p["geom"])
+    ref = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-14)
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed")
+    U = [T(u) for u in p["U_mac"]]
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.project(U, T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]], phi=phi, tol=1e-12)
+    assert relerr(H(phi), ref["phi"]) <= 1e-8
+    assert st["rel_constraint"] < 1e-8
+
+
+# ------------------------------------------------------------- full sizes
+
+_CACHE = {}
+
+
+def _config2_128(O):
+    if "c2" not in _CACHE:
+        p = I.stratified(128, seed=2, contrast=1e3, nodal=False)
+        g = ogrid(O, p["geom"])
+        ref = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-13)
+        _CACHE["c2"] = (p, g, ref)
+    return _CACHE["c2"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config2_128_full_parity(oracle, prec):
+    """128^3 stratified MAC projection against a full oracle solve."""
+    O = oracle
+    p, g, ref = _config2_128(O)
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec=prec)
+    U = [T(u) for u in p["U_mac"]]
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    s.project(U, T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]], phi=phi, tol=1e-12,
+              allow_not_converged=True)
+    assert relerr(H(phi), ref["phi"]) <= TOL[prec]
+
+
+def test_config3_256_properties(oracle):
+    """256^3 mixed MAC projection in the benchmark's configuration: the oracle's
+    own operator confirms the residual and the constraint of the GPU result."""
+    O = oracle
+    p = I.stratified(256, seed=3, contrast=1e3, nodal=False)
+    g = ogrid(O, p["geom"])
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed")
+    U = [T(u) for u in p["U_mac"]]
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.project(U, T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]], phi=phi, tol=1e-10,
+                   allow_not_converged=True)
+    ph = H(phi)
+    B = O.mac_faces(g, p["sigma"])
+    f = O.mac_rhs(g, p["beta0"], p["beta0_face"], p["U_mac"], p["S"])
+    rel = np.linalg.norm(f - O.mac_apply(g, B, ph)) / np.linalg.norm(f)
+    assert rel <= 1e-10 * 1.01 and abs(rel - st["rel_resid"]) <= 1e-3 * rel
+    div = O.mac_rhs(g, p["beta0"], p["beta0_face"], [H(u) for u in U], p["S"])
+    src = np.linalg.norm(p["beta0"] * p["S"])
+    assert np.linalg.norm(div) / src == pytest.approx(st["rel_constraint"], rel=1e-3)
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_zero_rhs_and_determinism():
+    p = I.stratified(32, seed=7, contrast=1e2, nodal=False)
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed")
+    phi = torch.ones(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.solve(torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV), phi, tol=1e-10)
+    assert st["iters"] == 0 and float(phi.abs().max()) == 0.0
+    rng = np.random.default_rng(1)
+    f = T(rng.normal(size=s.vec_shape))
+    a = torch.zeros_like(f)
+    b = torch.zeros_like(f)
+    s.solve(f, a, tol=1e-11)
+    s.solve(f, b, tol=1e-11)
+    assert torch.equal(a, b)
+
+
+def test_not_converged_returns_best_phi():
+    p = I.stratified(32, seed=7, contrast=1e2, nodal=False)
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="fp64", max_iters=2)
+    f = T(np.random.default_rng(2).normal(size=s.vec_shape))
+    phi = torch.zeros_like(f)
+    with pytest.raises(N.MGError) as ei:
+        s.solve(f, phi, tol=1e-14)
+    assert ei.value.status == N.MG_ERR_NOT_CONVERGED
+    st = s.solve(f, phi, tol=1e-14, allow_not_converged=True)
+    assert st["iters"] == 2 and st["rel_resid"] < 1e-2
+
+
+def test_odd_coarsest_and_anisotropic(oracle):
+    O = oracle
+    rng = np.random.default_rng(3)
+    for n, h in [((96, 96, 96), None), ((48, 24), (1 / 48, 1 / 12))]:
+        dim = len(n)
+        geom = I.geometry(n, ("periodic", "neumann", "neumann")[:dim], ("periodic", "dirichlet", "neumann")[:dim])
+        if h is not None:
+            geom["h"] = h
+        g = ogrid(O, geom)
+        sigma = np.exp(rng.normal(size=g.cell_shape))
+        f = rng.normal(size=g.cell_shape)
+        ref, _ = O.mac_solve_mg(g, O.mac_faces(g, sigma), f)
+        s = ProjectionSolver(geom, T(sigma), loc="cell", prec="mixed")
+        phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+        s.solve(T(f), phi, tol=1e-12)
+        assert relerr(H(phi), ref) <= 1e-8

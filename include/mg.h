@@ -7,10 +7,10 @@
  *
  *     div( sigma grad phi ) = div(beta0 U) - beta0 S,      sigma = beta0 / rho,
  *
- * by geometric multigrid V-cycles (S3: "multigrid linear solvers for the pressure
- * projection steps"), and applies the projection U <- U - (sigma/beta0) grad phi
- * that the gradient term of the momentum equation (Eq. 2) implies.  Two
- * discretisations are offered, one per projection of the second-order method (S3):
+ * by geometric multigrid V-cycles (S3 solves the projections with multigrid), and
+ * applies the projection U <- U - (sigma/beta0) grad phi that the gradient term of
+ * the momentum equation (Eq. 2) implies.  Two discretisations are offered, one per
+ * projection of the second-order projection method of S3:
  *
  *   MG_LOC_CELL   MAC projection: phi at cell centres, U on faces.  The discrete
  *                 operator is L = D B G with B the harmonic mean of sigma on faces,
@@ -118,7 +118,8 @@ typedef struct {
  *   coarsest_max  stop coarsening once a level has at most this many cells
  *   interp_order  cell prolongation: 0 piecewise constant, 1 linear
  *   omega         nodal Jacobi damping
- *   stream        cudaStream_t (NULL: the legacy default stream) */
+ *   stream        cudaStream_t (NULL: the legacy default stream)
+ *   flags         MG_FLAG_* bits (0 by default) */
 typedef struct {
     int prec;
     int nu1;
@@ -128,7 +129,12 @@ typedef struct {
     int interp_order;
     double omega;
     void* stream;
+    int flags;
 } mg_options;
+
+/* flags: run every smoothing sweep as separate colour passes, never the fused
+ * one-launch kernels (same arithmetic, slower; for testing). */
+#define MG_FLAG_NO_FUSED 1
 
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
@@ -206,8 +212,9 @@ const char* mg_last_error(void);
  * the method must move: see each class).  Returns MG_ERR_INVALID_ARG for an
  * unknown class.  Recording stops silently after 65536 launches. */
 typedef enum {
-    MG_PROF_CELL_SMOOTH_FINE = 0, /* one red-black colour pass on the finest cell level:
-                                     phi, f, sigma read and phi written, half of them: 2 words/cell */
+    MG_PROF_CELL_SMOOTH_FINE = 0, /* one fused red-black sweep on the finest cell level
+                                     (phi, f, sigma read, phi written: 4 words/cell), or one
+                                     colour pass where the level does not tile (2 words/cell) */
     MG_PROF_RESID64 = 1,          /* FP64 fine residual (+ FP32 copy in mixed mode):
                                      phi, f, sigma in FP64 (+ r in FP32) per unknown */
     MG_PROF_NODE_SMOOTH_FINE = 2, /* one Jacobi sweep on the finest nodal level: phi, f, sigma read, phi written */

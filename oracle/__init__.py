@@ -219,8 +219,12 @@ def mac_solve_dense(g: Grid, B, f):
     return phi
 
 
-def mac_solve_mg(g: Grid, B, f, tol=1e-14, max_cycles=200, phi0=None):
-    """Multigrid solve to tol or the round-off floor; returns (phi, stats dict)."""
+def mac_solve_mg(g: Grid, B, f, tol=1e-14, max_cycles=200, phi0=None, require=1e-9):
+    """Multigrid solve to tol or the round-off floor; returns (phi, stats dict).
+
+    Raises when the relative residual stays above ``require`` (e.g. a strongly
+    anisotropic grid, where point Gauss-Seidel does not smooth), so that no test
+    ever compares against an unconverged oracle."""
     B = [_f64(b) for b in B]
     f = _f64(f)
     phi = np.zeros(g.cell_shape) if phi0 is None else np.array(phi0, dtype=np.float64, copy=True)
@@ -230,6 +234,8 @@ def mac_solve_mg(g: Grid, B, f, tol=1e-14, max_cycles=200, phi0=None):
                                ctypes.c_int(max_cycles), ctypes.byref(st))
     if rc != 0:
         raise RuntimeError("oracle MAC multigrid setup failed")
+    if st.relres > max(tol, require):
+        raise RuntimeError(f"oracle MAC multigrid did not converge (relres {st.relres:.3e}); use mac_solve_dense")
     return phi, {"iters": st.iters, "relres": st.relres}
 
 
@@ -244,6 +250,8 @@ def mac_project(g: Grid, sigma, beta0_cell, beta0_face, U, S, tol=1e-14, dense=F
                               _p(phi), ctypes.c_double(tol), ctypes.c_int(1 if dense else 0), ctypes.byref(st))
     if rc != 0:
         raise RuntimeError("oracle MAC projection failed")
+    if st.relres > max(tol, 1e-9):
+        raise RuntimeError(f"oracle MAC projection did not converge (relres {st.relres:.3e})")
     return {"phi": phi, "U": U, "iters": st.iters, "relres": st.relres, "constraint": st.constraint,
             "src_norm": st.src_norm, "rhs_norm": st.rhs_norm}
 
@@ -297,7 +305,7 @@ def nodal_solve_dense(g: Grid, sigma, f):
     return phi
 
 
-def nodal_solve_mg(g: Grid, sigma, f, tol=1e-14, max_cycles=200, phi0=None):
+def nodal_solve_mg(g: Grid, sigma, f, tol=1e-14, max_cycles=200, phi0=None, require=1e-9):
     sigma, f = _f64(sigma), _f64(f)
     phi = np.zeros(g.node_shape) if phi0 is None else np.array(phi0, dtype=np.float64, copy=True)
     st = _Stats()
@@ -305,6 +313,8 @@ def nodal_solve_mg(g: Grid, sigma, f, tol=1e-14, max_cycles=200, phi0=None):
                                  ctypes.c_int(max_cycles), ctypes.byref(st))
     if rc != 0:
         raise RuntimeError("oracle nodal multigrid setup failed")
+    if st.relres > max(tol, require):
+        raise RuntimeError(f"oracle nodal multigrid did not converge (relres {st.relres:.3e})")
     return phi, {"iters": st.iters, "relres": st.relres}
 
 
@@ -318,5 +328,7 @@ def nodal_project(g: Grid, sigma, beta0, U, S, tol=1e-14, dense=False):
                                 ctypes.c_double(tol), ctypes.c_int(1 if dense else 0), ctypes.byref(st))
     if rc != 0:
         raise RuntimeError("oracle nodal projection failed")
+    if st.relres > max(tol, 1e-9):
+        raise RuntimeError(f"oracle nodal projection did not converge (relres {st.relres:.3e})")
     return {"phi": phi, "U": U, "iters": st.iters, "relres": st.relres, "constraint": st.constraint,
             "src_norm": st.src_norm, "rhs_norm": st.rhs_norm}

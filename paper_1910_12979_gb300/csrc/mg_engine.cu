@@ -214,10 +214,12 @@ mg_status plan(mg_handle* h, Bump& B)
         if (mixed) {
             v.x32 = B.take<float>(nv);
             v.b32 = B.take<float>(nv);
-            if (nodal) { v.r32 = B.take<float>(nv); v.t32 = B.take<float>(nv); }
+            v.t32 = B.take<float>(nv);
+            if (nodal) v.r32 = B.take<float>(nv);
         } else {
             if (L > 0) { v.x64 = B.take<double>(nv); v.b64 = B.take<double>(nv); }
-            if (nodal) { v.r64 = B.take<double>(nv); v.t64 = B.take<double>(nv); }
+            v.t64 = B.take<double>(nv);
+            if (nodal) v.r64 = B.take<double>(nv);
         }
         ++L;
         bool can = (long long)nc > cmax;
@@ -408,13 +410,36 @@ void zero(T* p, size_t n, cudaStream_t s)
     cudaMemsetAsync(p, 0, n * sizeof(T), s);
 }
 
-// One red-black colour pass; the finest level's passes are timed when profiling.
+// nu red-black sweeps (red, then black) on level l.  Levels that tile run one
+// fused launch per sweep, ping-ponging between x and the level's temp vector;
+// the others run the two colour passes in place.  Both orders are the same
+// arithmetic.  The finest level's launches are timed when profiling.
 template <typename T>
-void smooth_pass(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, int color)
+void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, int nu)
 {
-    const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * h->lev[0].ncell, h->stream) : -1;
-    cell_gsrb<T>(h->dim, V, x, b, color, h->stream);
-    prof_end(pr, h->stream);
+    cudaStream_t s = h->stream;
+    const double cells = (double)h->lev[l].ncell;
+    if (!(h->opt.flags & MG_FLAG_NO_FUSED) && cell_gsrb_fused_ok<T>(h->dim, V)) {
+        T* t = lt<T>(h, l);
+        T* src = x;
+        T* dst = t;
+        for (int k = 0; k < nu; ++k) {
+            const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 4.0 * sizeof(T) * cells, s) : -1;
+            cell_gsrb_sweep<T>(h->dim, V, src, dst, b, s);
+            prof_end(pr, s);
+            T* tmp = src;
+            src = dst;
+            dst = tmp;
+        }
+        if (src != x) cudaMemcpyAsync(x, src, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        return;
+    }
+    for (int k = 0; k < nu; ++k)
+        for (int color = 0; color < 2; ++color) {
+            const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * cells, s) : -1;
+            cell_gsrb<T>(h->dim, V, x, b, color, s);
+            prof_end(pr, s);
+        }
 }
 
 // One V-cycle on L x0 = b0 (level 0 arrays given), cell-centred.
@@ -428,10 +453,7 @@ void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
     for (int l = 0; l < L - 1; ++l) {
         if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
         const CellLevel<T> V = cview<T>(h, l);
-        for (int k = 0; k < h->opt.nu1; ++k) {
-            smooth_pass<T>(h, l, V, X(l), Bv(l), 0);
-            smooth_pass<T>(h, l, V, X(l), Bv(l), 1);
-        }
+        cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu1);
         const int pr = l == 0 ? prof_begin(MG_PROF_CELL_RESTRICT_FINE,
                                            (3.0 + 1.0 / (1 << dim)) * sizeof(T) * h->lev[0].ncell, s) : -1;
         cell_resid_restrict<T>(dim, V, X(l), Bv(l), lb<T>(h, l + 1), s);
@@ -441,10 +463,7 @@ void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
     for (int l = L - 2; l >= 0; --l) {
         const CellLevel<T> V = cview<T>(h, l);
         cell_prolong_add<T>(dim, V, cview<T>(h, l + 1), X(l), X(l + 1), h->opt.interp_order, s);
-        for (int k = 0; k < h->opt.nu2; ++k) {
-            smooth_pass<T>(h, l, V, X(l), Bv(l), 1);
-            smooth_pass<T>(h, l, V, X(l), Bv(l), 0);
-        }
+        cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu2);
     }
 }
 
@@ -581,6 +600,7 @@ void mg_default_options(mg_options* o)
     o->interp_order = 1;
     o->omega = 0.9;
     o->stream = nullptr;
+    o->flags = 0;
 }
 
 static mg_status init_handle(mg_handle* h, const mg_geometry* g, const mg_bc* bc, const mg_options* o)

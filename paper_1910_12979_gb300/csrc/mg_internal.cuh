@@ -75,6 +75,11 @@ void cell_coarsen_faces(int dim, const CellLevel<double>& F, const CellLevel<dou
 void cell_invdiag(int dim, const CellLevel<double>& L, double* invd, cudaStream_t s);
 template <typename T>
 void cell_gsrb(int dim, const CellLevel<T>& L, T* x, const T* b, int color, cudaStream_t s);
+// one full red-then-black sweep xin -> xout in a single launch (when ok)
+template <typename T>
+bool cell_gsrb_fused_ok(int dim, const CellLevel<T>& L);
+template <typename T>
+void cell_gsrb_sweep(int dim, const CellLevel<T>& L, const T* xin, T* xout, const T* b, cudaStream_t s);
 template <typename T>
 void cell_resid_restrict(int dim, const CellLevel<T>& F, const T* x, const T* b, T* bc, cudaStream_t s);
 template <typename T>

@@ -1,6 +1,6 @@
 """Pins for the oracle's nodal (Q1 finite-element) system.
 
-Reading of the nodal projection (S3, "a second order projection method"):
+Reading of the nodal projection of the second-order projection method (S3):
 Q1 elements with sigma constant per cell; see oracle/mg_oracle.c.  What pins it:
   * the textbook constant-coefficient Q1 stencils (3-D: centre -8/3, face
     neighbours 0, edges 1/6, corners 1/12; 2-D: (1/3)[1 1 1; 1 -8 1; 1 1 1]);

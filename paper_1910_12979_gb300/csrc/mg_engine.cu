@@ -476,8 +476,9 @@ void node_smooth(mg_handle* h, int l, T* x, const T* b, int sweeps)
     const T om = (T)h->opt.omega;
     for (int k = 0; k < sweeps; ++k) {
         const int pr = l == 0 ? prof_begin(MG_PROF_NODE_SMOOTH_FINE, 4.0 * sizeof(T) * h->lev[0].nvec, s) : -1;
-        if (k % 2 == 0) node_jacobi<T>(h->dim, V, x, t, b, om, s);
-        else node_jacobi<T>(h->dim, V, t, x, b, om, s);
+        const bool tiled = !(h->opt.flags & MG_FLAG_NO_FUSED);
+        if (k % 2 == 0) node_jacobi<T>(h->dim, V, x, t, b, om, tiled, s);
+        else node_jacobi<T>(h->dim, V, t, x, b, om, tiled, s);
         prof_end(pr, s);
     }
     if (sweeps % 2 == 1) cudaMemcpyAsync(x, t, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
@@ -493,7 +494,7 @@ void vcycle_node(mg_handle* h, T* x0, const T* b0, bool zero_init)
     for (int l = 0; l < L - 1; ++l) {
         if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
         node_smooth<T>(h, l, X(l), Bv(l), h->opt.nu1);
-        node_resid<T>(dim, nview<T>(h, l), X(l), Bv(l), lr<T>(h, l), s);
+        node_resid<T>(dim, nview<T>(h, l), X(l), Bv(l), lr<T>(h, l), !(h->opt.flags & MG_FLAG_NO_FUSED), s);
         node_restrict<T>(dim, nview<T>(h, l), nview<T>(h, l + 1), lr<T>(h, l), lb<T>(h, l + 1), s);
     }
     dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);

@@ -102,10 +102,11 @@ void cell_dense_assemble(int dim, const CellLevel<T>& L, double* A, int lda, cud
 void node_coarsen_sigma(int dim, const NodeLevel<double>& F, const NodeLevel<double>& C, double* sc,
                         cudaStream_t s);
 void node_invdiag(int dim, const NodeLevel<double>& L, double* invd, cudaStream_t s);
+// tiled: allow the shared-memory tiled kernel (3-D levels of at least 32 x 8 nodes)
 template <typename T>
-void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, cudaStream_t s);
+void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s);
 template <typename T>
-void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, cudaStream_t s);
+void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bool tiled, cudaStream_t s);
 template <typename T>
 void node_restrict(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, const T* rf, T* bc, cudaStream_t s);
 template <typename T>

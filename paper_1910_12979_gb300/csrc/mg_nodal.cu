@@ -215,6 +215,106 @@ __global__ void k_node_prolong(NodeLevel<T> F, NodeLevel<T> C, T* __restrict__ x
     xf[t] += s;
 }
 
+// ------------------------------------------------------ tiled node sweeps
+//
+// The Jacobi sweep and the residual of k_jacobi / k_node_resid, one CTA per
+// 32 x 8 tile of node columns marching through a chunk of z-planes.  Shared
+// memory holds a ring of three phi planes with a 1-node halo and a ring of two
+// sigma planes (the cells around the tile's nodes, 0 outside the domain), so
+// phi, sigma and b are read and the result written once per node.  The cell
+// loop visits the cells in node_row's order; a missing cell adds 0 * (...),
+// which leaves both sums unchanged.  3-D only.
+constexpr int kNTX = 32, kNTY = 8;
+
+template <typename T>
+struct NodeTileShared {
+    T xs[3][kNTY + 2][kNTX + 2];
+    T ss[2][kNTY + 1][kNTX + 1];
+};
+
+template <typename T, bool RESID>
+__global__ void __launch_bounds__(kNTX * kNTY)
+k_node_tiled(NodeLevel<T> L, const T* __restrict__ x, T* __restrict__ out, const T* __restrict__ b, T omega, int kz)
+{
+    constexpr int TX = kNTX, TY = kNTY;
+    __shared__ NodeTileShared<T> sh;
+    const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * kz, z1 = min(z0 + kz, Nz);
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
+
+    auto load_x = [&](int p) {  // node plane p, possibly -1 or Nz
+        int gz = p;
+        bool zok = true;
+        if (gz < 0 || gz >= Nz) { if (pz) gz = gz < 0 ? gz + Nz : gz - Nz; else zok = false; }
+        T(*dst)[TX + 2] = sh.xs[(p + 3) % 3];
+        for (int q = tid; q < (TX + 2) * (TY + 2); q += TX * TY) {
+            const int ly = q / (TX + 2), lx = q - ly * (TX + 2);
+            int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            bool ok = zok;
+            if (gx < 0 || gx >= Nx) { if (px) gx = gx < 0 ? gx + Nx : gx - Nx; else ok = false; }
+            if (gy < 0 || gy >= Ny) { if (py) gy = gy < 0 ? gy + Ny : gy - Ny; else ok = false; }
+            if (gx >= Nx || gy >= Ny) ok = false;
+            dst[ly][lx] = ok ? x[((size_t)gz * Ny + gy) * Nx + gx] : T(0);
+        }
+    };
+    auto load_s = [&](int c) {  // cell plane c, possibly -1 or nz
+        int gz = c;
+        bool zok = true;
+        if (gz < 0 || gz >= nz) { if (pz) gz = gz < 0 ? gz + nz : gz - nz; else zok = false; }
+        T(*dst)[TX + 1] = sh.ss[(c + 2) & 1];
+        for (int q = tid; q < (TX + 1) * (TY + 1); q += TX * TY) {
+            const int ly = q / (TX + 1), lx = q - ly * (TX + 1);
+            int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            bool ok = zok;
+            if (gx < 0 || gx >= nx) { if (px) gx = gx < 0 ? gx + nx : gx - nx; else ok = false; }
+            if (gy < 0 || gy >= ny) { if (py) gy = gy < 0 ? gy + ny : gy - ny; else ok = false; }
+            if (gx >= nx || gy >= ny) ok = false;
+            dst[ly][lx] = ok ? L.sigma[((size_t)gz * ny + gy) * nx + gx] : T(0);
+        }
+    };
+
+    load_x(z0 - 1);
+    load_x(z0);
+    load_s(z0 - 1);
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+    const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+    for (int k = z0; k < z1; ++k) {
+        load_x(k + 1);
+        load_s(k);
+        __syncthreads();
+        if (i < Nx && j < Ny) {
+            const size_t id = ((size_t)k * Ny + j) * Nx + i;
+            if (node_dirichlet(L, i, j, k, 3)) {
+                out[id] = T(0);
+            } else {
+                const int sk = (k + 3) % 3;
+                T acc = T(0), ssum = T(0);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1, sz = (c & 4) ? 1 : -1;
+                    const T sg = sh.ss[(sz > 0 ? k + 2 : k + 1) & 1][ly + (sy > 0 ? 0 : -1)][lx + (sx > 0 ? 0 : -1)];
+                    const int se = (k + sz + 3) % 3;
+                    const int a = lx + sx, bb = ly + sy;
+                    acc += sg * (sh.xs[sk][bb][a] + sh.xs[se][ly][a] + sh.xs[se][bb][lx] + sh.xs[se][bb][a]);
+                    ssum += sg;
+                }
+                const T off = acc * (L.ih2 / T(12));
+                const T dg = -ssum * (L.ih2 / T(3));
+                const T xi = sh.xs[sk][ly][lx];
+                if (RESID) {
+                    out[id] = b[id] - (off + dg * xi);
+                } else {
+                    const T inv = L.invd ? L.invd[id] : recip(dg);
+                    out[id] = xi + omega * (b[id] - (off + dg * xi)) * inv;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // -------------------------------------------------------- FP64 residuals
 
 template <int DIM>
@@ -377,17 +477,46 @@ void node_invdiag(int dim, const NodeLevel<double>& L, double* invd, cudaStream_
 }
 
 template <typename T>
-void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, cudaStream_t s)
+static bool node_tiled_ok(int dim, const NodeLevel<T>& L, bool allow)
 {
-    if (dim == 2) MGP_LAUNCH(k_jacobi<2, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, xo, b, omega));
-    else MGP_LAUNCH(k_jacobi<3, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, xo, b, omega));
+    return allow && dim == 3 && L.Nx >= kNTX && L.Ny >= kNTY && L.Nz >= 4;
 }
 
 template <typename T>
-void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, cudaStream_t s)
+static dim3 node_tiled_grid(const NodeLevel<T>& L, int& kz)
 {
-    if (dim == 2) MGP_LAUNCH(k_node_resid<2, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, b, r));
-    else MGP_LAUNCH(k_node_resid<3, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, b, r));
+    const long long tx = (L.Nx + kNTX - 1) / kNTX, ty = (L.Ny + kNTY - 1) / kNTY;
+    kz = (int)((tx * ty * L.Nz + 152 * 7 - 1) / (152 * 7));
+    kz = kz < 4 ? 4 : kz;
+    return dim3((unsigned)tx, (unsigned)ty, (unsigned)((L.Nz + kz - 1) / kz));
+}
+
+template <typename T>
+void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s)
+{
+    if (node_tiled_ok(dim, L, tiled)) {
+        int kz;
+        const dim3 g = node_tiled_grid(L, kz);
+        MGP_LAUNCH(k_node_tiled<T, false><<<g, dim3(kNTX, kNTY), 0, s>>>(L, x, xo, b, omega, kz));
+    } else if (dim == 2) {
+        MGP_LAUNCH(k_jacobi<2, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, xo, b, omega));
+    } else {
+        MGP_LAUNCH(k_jacobi<3, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, xo, b, omega));
+    }
+}
+
+template <typename T>
+void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bool tiled, cudaStream_t s)
+{
+    if (node_tiled_ok(dim, L, tiled)) {
+        int kz;
+        const dim3 g = node_tiled_grid(L, kz);
+        MGP_LAUNCH(k_node_tiled<T, true><<<g, dim3(kNTX, kNTY), 0, s>>>(L, x, r, b, T(0), kz));
+    } else if (dim == 2) {
+        MGP_LAUNCH(k_node_resid<2, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, b, r));
+    } else {
+        MGP_LAUNCH(k_node_resid<3, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, b, r));
+    }
 }
 
 template <typename T>
@@ -449,11 +578,13 @@ void node_zero_dirichlet(int dim, const NodeLevel<T>& L, T* x, cudaStream_t s)
     else MGP_LAUNCH(k_node_zero_dirichlet<3, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x));
 }
 
-template void node_jacobi<float>(int, const NodeLevel<float>&, const float*, float*, const float*, float, cudaStream_t);
-template void node_jacobi<double>(int, const NodeLevel<double>&, const double*, double*, const double*, double,
+template void node_jacobi<float>(int, const NodeLevel<float>&, const float*, float*, const float*, float, bool,
+                                 cudaStream_t);
+template void node_jacobi<double>(int, const NodeLevel<double>&, const double*, double*, const double*, double, bool,
                                   cudaStream_t);
-template void node_resid<float>(int, const NodeLevel<float>&, const float*, const float*, float*, cudaStream_t);
-template void node_resid<double>(int, const NodeLevel<double>&, const double*, const double*, double*, cudaStream_t);
+template void node_resid<float>(int, const NodeLevel<float>&, const float*, const float*, float*, bool, cudaStream_t);
+template void node_resid<double>(int, const NodeLevel<double>&, const double*, const double*, double*, bool,
+                                 cudaStream_t);
 template void node_restrict<float>(int, const NodeLevel<float>&, const NodeLevel<float>&, const float*, float*,
                                    cudaStream_t);
 template void node_restrict<double>(int, const NodeLevel<double>&, const NodeLevel<double>&, const double*, double*,

@@ -113,6 +113,7 @@ def test_apply_matches_oracle(oracle, loc):
     O = oracle
     rng = np.random.default_rng(5)
     geom = I.geometry((12, 10, 8), ("periodic", "neumann", "neumann"), ("periodic", "dirichlet", "dirichlet"))
+    geom["h"] = (0.1, 0.1, 0.1)   # equal spacing (the nodal discretisation requires it)
     g = ogrid(O, geom)
     sigma = np.exp(rng.normal(size=g.cell_shape))
     s = ProjectionSolver(geom, T(sigma), loc=loc, prec="fp64")
@@ -269,6 +270,22 @@ def test_fused_sweep_matches_two_pass():
             s.solve(f, phi, tol=1e-11)
             out.append(phi)
     assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[3])
+
+
+def test_tiled_nodal_matches_untiled():
+    """The shared-memory tiled nodal sweep and residual give the same phi as the
+    plain kernels (same sums in the same order)."""
+    p = I.stratified(64, seed=9, contrast=1e3, mac=False)
+    out = []
+    for flags in (0, N.MG_FLAG_NO_FUSED):
+        for prec in ("mixed", "fp64"):
+            s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="nodal", prec=prec, flags=flags)
+            f = T(np.random.default_rng(4).normal(size=s.vec_shape))
+            phi = torch.zeros_like(f)
+            s.solve(f, phi, tol=1e-11)
+            out.append(phi)
+    for a, b in ((out[0], out[2]), (out[1], out[3])):
+        assert torch.allclose(a, b, rtol=0, atol=1e-13 * float(b.abs().max()))
 
 
 def test_odd_coarsest_and_anisotropic(oracle):

@@ -259,106 +259,6 @@ __global__ void k_prolong_add(CellLevel<T> F, CellLevel<T> C, T* __restrict__ xf
     }
 }
 
-// ------------------------------------------------- fused red-black sweep
-//
-// One full red-black Gauss-Seidel sweep (red, then black) in one launch,
-// reading xin and writing xout (ping-pong), bitwise identical to the two colour
-// passes of k_gsrb.  A CTA owns a TX x TY column tile and marches through a
-// chunk of z-planes, keeping in shared memory a ring of three xin planes with a
-// 2-cell halo and a ring of three planes of new red values with a 1-cell halo:
-//   step k: stage xin plane k+1; red on plane k over the tile + 1 halo ring
-//           (old black neighbours from the staged planes); black on plane k-1
-//           over the tile from the new red values; write plane k-1.
-// The halo ring's red values are recomputed redundantly by neighbouring CTAs,
-// which is what lets one launch replace two dependent passes.  Requires
-// nx % TX == 0, ny % TY == 0 and a non-periodic z axis (checked by the launcher).
-constexpr int kFTX = 32;
-
-template <typename T, int TY>
-struct FusedShared {
-    T xs[3][TY + 4][kFTX + 4];
-    T rs[3][TY + 2][kFTX + 2];
-};
-
-template <typename T, int TY>
-__global__ void __launch_bounds__(kFTX * TY)
-k_gsrb_fused(CellLevel<T> L, const T* __restrict__ xin, T* __restrict__ xout, const T* __restrict__ b, int kz)
-{
-    constexpr int TX = kFTX, RX = TX + 4, RY = TY + 4, QX = TX + 2, QY = TY + 2;
-    __shared__ FusedShared<T, TY> sh;
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * kz, z1 = min(z0 + kz, nz);
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP;
-
-    auto load_plane = [&](int p) {
-        T(*dst)[RX] = sh.xs[p % 3];
-        for (int q = tid; q < RX * RY; q += TX * TY) {
-            const int ly = q / RX, lx = q - ly * RX;
-            int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
-            bool ok = true;
-            if (gx < 0 || gx >= nx) { if (px) gx = gx < 0 ? gx + nx : gx - nx; else ok = false; }
-            if (gy < 0 || gy >= ny) { if (py) gy = gy < 0 ? gy + ny : gy - ny; else ok = false; }
-            dst[ly][lx] = ok ? xin[((size_t)p * ny + gy) * nx + gx] : T(0);
-        }
-    };
-    // neighbour accessors with global (possibly wrapped) coordinates
-    auto xacc = [&](int ii, int jj, int kk) {
-        int lx = ii - x0 + 2, ly = jj - y0 + 2;
-        if (lx < 0) lx += nx; else if (lx >= RX) lx -= nx;
-        if (ly < 0) ly += ny; else if (ly >= RY) ly -= ny;
-        return sh.xs[kk % 3][ly][lx];
-    };
-    auto racc = [&](int ii, int jj, int kk) {
-        int lx = ii - x0 + 1, ly = jj - y0 + 1;
-        if (lx < 0) lx += nx; else if (lx >= QX) lx -= nx;
-        if (ly < 0) ly += ny; else if (ly >= QY) ly -= ny;
-        return sh.rs[kk % 3][ly][lx];
-    };
-    auto red = [&](int k) {
-        for (int q = tid; q < QX * QY; q += TX * TY) {
-            const int ly = q / QX, lx = q - ly * QX;
-            int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-            if (gx < 0 || gx >= nx) { if (!px) continue; gx = gx < 0 ? gx + nx : gx - nx; }
-            if (gy < 0 || gy >= ny) { if (!py) continue; gy = gy < 0 ? gy + ny : gy - ny; }
-            if (((gx + gy + k) & 1) != 0) continue;
-            T off, dg;
-            cell_row<3>(L, gx, gy, k, xacc, off, dg);
-            const size_t id = ((size_t)k * ny + gy) * nx + gx;
-            sh.rs[k % 3][ly][lx] = (off - b[id]) * inv_diag(L, (int)id, dg);
-        }
-    };
-    auto black = [&](int k) {
-        const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-        const size_t id = ((size_t)k * ny + gy) * nx + gx;
-        T v;
-        if (((gx + gy + k) & 1) == 0) {
-            v = sh.rs[k % 3][threadIdx.y + 1][threadIdx.x + 1];
-        } else {
-            T off, dg;
-            cell_row<3>(L, gx, gy, k, racc, off, dg);
-            v = (off - b[id]) * inv_diag(L, (int)id, dg);
-        }
-        xout[id] = v;
-    };
-
-    const int kfirst = max(z0 - 1, 0), klast = min(z1, nz - 1);
-    if (kfirst - 1 >= 0) load_plane(kfirst - 1);
-    load_plane(kfirst);
-    for (int k = kfirst; k <= klast; ++k) {
-        if (k + 1 < nz) load_plane(k + 1);
-        __syncthreads();
-        red(k);
-        __syncthreads();
-        if (k - 1 >= z0 && k - 1 < z1) black(k - 1);
-    }
-    if (z1 == nz) {
-        __syncthreads();
-        black(nz - 1);
-    }
-}
-
 // -------------------------------------------------------- FP64 residuals
 
 template <int DIM>
@@ -540,23 +440,6 @@ void cell_gsrb(int dim, const CellLevel<T>& L, T* x, const T* b, int color, cuda
 }
 
 template <typename T>
-bool cell_gsrb_fused_ok(int dim, const CellLevel<T>& L)
-{
-    return dim == 3 && L.nx % kFTX == 0 && L.ny % 8 == 0 && L.nz >= 2 && L.bc.lo[2] != BCP;
-}
-
-template <typename T>
-void cell_gsrb_sweep(int dim, const CellLevel<T>& L, const T* xin, T* xout, const T* b, cudaStream_t s)
-{
-    // a chunk of z-planes per CTA: about 7 CTAs per SM over 152 SMs
-    const long long tiles = (long long)(L.nx / kFTX) * (L.ny / 8);
-    int kz = (int)((tiles * L.nz + 152 * 7 - 1) / (152 * 7));
-    kz = kz < 8 ? 8 : kz;
-    dim3 grid(L.nx / kFTX, L.ny / 8, (L.nz + kz - 1) / kz);
-    MGP_LAUNCH(k_gsrb_fused<T, 8><<<grid, dim3(kFTX, 8), 0, s>>>(L, xin, xout, b, kz));
-}
-
-template <typename T>
 void cell_resid_restrict(int dim, const CellLevel<T>& F, const T* x, const T* b, T* bc, cudaStream_t s)
 {
     const int cnx = F.nx / 2, cny = F.ny / 2, cnz = dim == 3 ? F.nz / 2 : 1;
@@ -625,11 +508,6 @@ void cell_dense_assemble(int dim, const CellLevel<T>& L, double* A, int lda, cud
 
 template void cell_gsrb<float>(int, const CellLevel<float>&, float*, const float*, int, cudaStream_t);
 template void cell_gsrb<double>(int, const CellLevel<double>&, double*, const double*, int, cudaStream_t);
-template bool cell_gsrb_fused_ok<float>(int, const CellLevel<float>&);
-template bool cell_gsrb_fused_ok<double>(int, const CellLevel<double>&);
-template void cell_gsrb_sweep<float>(int, const CellLevel<float>&, const float*, float*, const float*, cudaStream_t);
-template void cell_gsrb_sweep<double>(int, const CellLevel<double>&, const double*, double*, const double*,
-                                      cudaStream_t);
 template void cell_resid_restrict<float>(int, const CellLevel<float>&, const float*, const float*, float*, cudaStream_t);
 template void cell_resid_restrict<double>(int, const CellLevel<double>&, const double*, const double*, double*,
                                           cudaStream_t);

@@ -114,12 +114,14 @@ typedef struct {
  *                 coarsest dense solve is FP64 in both modes.
  *   nu1, nu2      pre/post smoothing sweeps (red-black Gauss-Seidel for cells,
  *                 damped Jacobi for nodes)
- *   max_iters     cap on V-cycles (FP64) or refinement iterations (mixed)
+ *   max_iters     cap on V-cycles (FP64) or refinement steps (mixed)
  *   coarsest_max  stop coarsening once a level has at most this many cells
  *   interp_order  cell prolongation: 0 piecewise constant, 1 linear
  *   omega         nodal Jacobi damping
  *   stream        cudaStream_t (NULL: the legacy default stream)
- *   flags         MG_FLAG_* bits (0 by default) */
+ *   flags         MG_FLAG_* bits (0 by default)
+ *   inner_cycles  mixed precision: FP32 V-cycles per FP64 refinement step
+ *                 (0: automatic, 1 for cells and 2 for nodes) */
 typedef struct {
     int prec;
     int nu1;
@@ -130,11 +132,16 @@ typedef struct {
     double omega;
     void* stream;
     int flags;
+    int inner_cycles;
 } mg_options;
 
 /* flags: run every smoothing sweep as separate colour passes, never the fused
  * one-launch kernels (same arithmetic, slower; for testing). */
 #define MG_FLAG_NO_FUSED 1
+/* flags: drive the iterations from the host (one scalar read-back per
+ * iteration) instead of the graph-resident loop (same decisions, same phi).
+ * The host loop is also used while mg_prof_enable(1) is in effect. */
+#define MG_FLAG_NO_GRAPH 2
 
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
@@ -183,11 +190,15 @@ mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_
 mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* beta0, const double* S, double* phi,
                      double tol, mg_stats* stats);
 
-/* Solve count independent problems (any mix of grids and handles) with their
- * kernels sharing launches: one launch per multigrid step for the whole batch,
- * captured once into a CUDA graph and replayed.  Every handle must use the same
- * precision and location and the same stream; tol[i] per problem; stats may be
- * NULL or hold count entries. */
+/* Solve count independent problems (any mix of grids, precisions and
+ * locations; each handle at most once) as ONE CUDA graph launch on the first
+ * handle's stream: every solve is a branch of the graph with its own
+ * device-side convergence loop, so the branches run concurrently and each
+ * stops on its own tolerance tol[i].  The graph is captured on the first call
+ * for a given ordered list of handles and cached until one of them is
+ * destroyed.  rhs[i] and phi[i] follow mg_solve; stats may be NULL or hold
+ * count entries (ms is the wall time of the whole batch).  Returns the first
+ * non-OK status of the batch, MG_OK if every solve converged. */
 mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double* const* phi, const double* tol,
                          int count, mg_stats* stats);
 

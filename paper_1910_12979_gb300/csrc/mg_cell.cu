@@ -261,24 +261,39 @@ __global__ void k_prolong_add(CellLevel<T> F, CellLevel<T> C, T* __restrict__ xf
 
 // -------------------------------------------------------- FP64 residuals
 
-template <int DIM>
+template <int DIM, bool HAS_DIAG>
 __global__ void k_resid64(CellLevel<double> L, const double* __restrict__ x, const double* __restrict__ b,
                           float* __restrict__ r32, const double* __restrict__ scale, double* __restrict__ partials)
 {
     const int total = L.nx * L.ny * L.nz;
-    const double inv = (r32 && scale) ? 1.0 / *scale : 1.0;
-    double acc[1] = {0.0};
+    const double inv = 1.0 / *scale;
+    float acc = 0.f;
     const GlobalPhi<double> ph{x, L.nx, L.ny};
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         int i, j, k;
         unflat(t, L.nx, L.ny, i, j, k);
         double off, dg;
         cell_row<DIM>(L, i, j, k, ph, off, dg);
-        const double r = b[t] - (off - dg * x[t]);
-        acc[0] += r * r;
-        if (r32) r32[t] = (float)(r * inv);
+        const double d = HAS_DIAG ? L.diag[t] : dg;
+        const float rs = (float)((b[t] - (off - d * x[t])) * inv);
+        acc = fmaf(rs, rs, acc);
+        if (r32) r32[t] = rs;
     }
-    block_reduce_store<1>(acc, partials);
+    double a[1] = {(double)acc};
+    block_reduce_store<1>(a, partials);
+}
+
+template <int DIM>
+__global__ void k_diag(CellLevel<double> L, double* __restrict__ diag)
+{
+    const int total = L.nx * L.ny * L.nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    unflat(t, L.nx, L.ny, i, j, k);
+    double off, dg;
+    cell_row<DIM>(L, i, j, k, [](int, int, int) { return 0.0; }, off, dg);
+    diag[t] = dg;
 }
 
 template <int DIM>
@@ -465,8 +480,20 @@ void cell_prolong_add(int dim, const CellLevel<T>& F, const CellLevel<T>& C, T* 
 void cell_resid64(int dim, const CellLevel<double>& L, const double* x, const double* b, float* r32,
                   const double* scale, double* partials, cudaStream_t s)
 {
-    if (dim == 2) MGP_LAUNCH(k_resid64<2><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
-    else MGP_LAUNCH(k_resid64<3><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+    if (dim == 2) {
+        if (L.diag) MGP_LAUNCH(k_resid64<2, true><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+        else MGP_LAUNCH(k_resid64<2, false><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+    } else {
+        if (L.diag) MGP_LAUNCH(k_resid64<3, true><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+        else MGP_LAUNCH(k_resid64<3, false><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+    }
+}
+
+void cell_diag(int dim, const CellLevel<double>& L, double* diag, cudaStream_t s)
+{
+    long long n = (long long)L.nx * L.ny * L.nz;
+    if (dim == 2) MGP_LAUNCH(k_diag<2><<<nb(n), kThreads, 0, s>>>(L, diag));
+    else MGP_LAUNCH(k_diag<3><<<nb(n), kThreads, 0, s>>>(L, diag));
 }
 
 void cell_apply64(int dim, const CellLevel<double>& L, const double* x, double* out, cudaStream_t s)

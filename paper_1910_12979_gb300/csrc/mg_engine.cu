@@ -10,13 +10,15 @@
 
 #include <atomic>
 #include <chrono>
+#include <algorithm>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "../../include/mg.h"
-#include "mg_internal.cuh"
+#include "mg_device.cuh"
 
 using namespace mgp;
 
@@ -108,6 +110,7 @@ struct Level {
     size_t ncell, nvec;  // cells; unknown-vector length (cells or stored nodes)
     double* B64[3];
     double* invd64;
+    double* diag64;    // level 0: diagonal for the FP64 residual
     float* B32[3];
     double* sig64;
     float* sig32;
@@ -138,6 +141,9 @@ struct mg_handle {
     size_t ws_bytes;
     bool own_ws;
     std::atomic<int> busy;
+    // graph-resident solve loops: [0] rhs taken from the caller, [1] rhs already in f64
+    cudaGraphExec_t gx[2];
+    long long g_fixed[2], g_body[2];  // kernel launches outside the loop / per iteration
 };
 
 namespace {
@@ -172,6 +178,7 @@ mg_status check_problem(const mg_geometry* g, const mg_bc* bc, const mg_options*
     if (o->max_iters < 1) return fail(MG_ERR_INVALID_ARG, "max_iters must be >= 1");
     if (o->interp_order != 0 && o->interp_order != 1) return fail(MG_ERR_INVALID_ARG, "interp_order must be 0 or 1");
     if (!(o->omega > 0.0 && o->omega <= 1.5)) return fail(MG_ERR_INVALID_ARG, "omega out of range");
+    if (o->inner_cycles < 0 || o->inner_cycles > 16) return fail(MG_ERR_INVALID_ARG, "inner_cycles out of range");
     return MG_OK;
 }
 
@@ -199,6 +206,7 @@ mg_status plan(mg_handle* h, Bump& B)
         v.ncell = (size_t)n[0] * n[1] * n[2];
         v.nvec = nodal ? (size_t)v.N[0] * v.N[1] * v.N[2] : v.ncell;
         const size_t nc = v.ncell, nv = v.nvec;
+        if (L == 0) v.diag64 = B.take<double>(nv);
         if (!nodal) {
             for (int d = 0; d < dim; ++d) {
                 size_t m = (size_t)(n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2));
@@ -246,13 +254,13 @@ template <>
 CellLevel<double> cview<double>(const mg_handle* h, int l)
 {
     const Level& v = h->lev[l];
-    return CellLevel<double>{v.n[0], v.n[1], v.n[2], h->bc, v.B64[0], v.B64[1], v.B64[2], v.invd64};
+    return CellLevel<double>{v.n[0], v.n[1], v.n[2], h->bc, v.B64[0], v.B64[1], v.B64[2], v.invd64, v.diag64};
 }
 template <>
 CellLevel<float> cview<float>(const mg_handle* h, int l)
 {
     const Level& v = h->lev[l];
-    return CellLevel<float>{v.n[0], v.n[1], v.n[2], h->bc, v.B32[0], v.B32[1], v.B32[2], nullptr};
+    return CellLevel<float>{v.n[0], v.n[1], v.n[2], h->bc, v.B32[0], v.B32[1], v.B32[2], nullptr, nullptr};
 }
 
 template <typename T>
@@ -262,14 +270,14 @@ NodeLevel<double> nview<double>(const mg_handle* h, int l)
 {
     const Level& v = h->lev[l];
     return NodeLevel<double>{v.n[0], v.n[1], v.n[2], v.N[0], v.N[1], v.N[2], h->bc, v.sig64,
-                             1.0 / (v.h[0] * v.h[0]), v.invd64};
+                             1.0 / (v.h[0] * v.h[0]), v.invd64, v.diag64};
 }
 template <>
 NodeLevel<float> nview<float>(const mg_handle* h, int l)
 {
     const Level& v = h->lev[l];
     return NodeLevel<float>{v.n[0], v.n[1], v.n[2], v.N[0], v.N[1], v.N[2], h->bc, v.sig32,
-                            (float)(1.0 / (v.h[0] * v.h[0])), nullptr};
+                            (float)(1.0 / (v.h[0] * v.h[0])), nullptr, nullptr};
 }
 
 // Step a1: coefficients on every level and the dense inverse of the coarsest operator.
@@ -307,6 +315,12 @@ mg_status build_coefficients(mg_handle* h, const mg_coeff* c)
                 cell_invdiag(dim, V, v.invd64, s);
             }
         }
+        {
+            CellLevel<double> V = cview<double>(h, 0);
+            V.invd = nullptr;
+            V.diag = nullptr;
+            cell_diag(dim, V, h->lev[0].diag64, s);
+        }
         const int n = h->Nd + h->singular;
         cell_dense_assemble(dim, cview<double>(h, h->nlev - 1), h->A, 2 * n, s);
     } else {
@@ -323,12 +337,18 @@ mg_status build_coefficients(mg_handle* h, const mg_coeff* c)
                 node_invdiag(dim, V, v.invd64, s);
             }
         }
+        {
+            NodeLevel<double> V = nview<double>(h, 0);
+            V.invd = nullptr;
+            V.diag = nullptr;
+            node_diag(dim, V, h->lev[0].diag64, s);
+        }
         const int n = h->Nd + h->singular;
         NodeLevel<double> C = nview<double>(h, h->nlev - 1);
         C.invd = nullptr;
         node_dense_assemble(dim, C, h->A, 2 * n, s);
     }
-    dense_invert(h->A, h->Nd, h->singular, h->Minv, reinterpret_cast<int*>(&h->d->pad[0]), s);
+    dense_invert(h->A, h->Nd, h->singular, h->Minv, &h->d->info, s);
     MG_CK(cudaGetLastError());
     return MG_OK;
 }
@@ -366,7 +386,7 @@ void finish_rhs(mg_handle* h, int fslot, int srcslot)
     MGP_LAUNCH(k_keep<<<1, 1, 0, s>>>(h->d, fslot, -1));
 }
 
-// ||f - L phi||^2 -> d->rnorm2; optional FP32 copy of the residual / fscale.
+// ||f - L phi||^2 / ||f||^2 -> d->rnorm2; optional FP32 copy of the residual / ||f||.
 void residual64(mg_handle* h, const double* phi, float* r32)
 {
     cudaStream_t s = h->stream;
@@ -514,6 +534,25 @@ void gauge(mg_handle* h, double* phi)
     vec_sub_mean(phi, n, &h->d->red[0], (double)n, s);
 }
 
+int inner_cycles(const mg_handle* h)
+{
+    if (h->opt.inner_cycles > 0) return h->opt.inner_cycles;
+    return h->loc == MG_LOC_NODAL ? 2 : 1;
+}
+
+// Mixed refinement step: a few FP32 V-cycles on A e = r / ||f|| from e = 0,
+// then phi += ||f|| e in FP64.
+void mixed_correction(mg_handle* h, double* phi)
+{
+    float* e = h->lev[0].x32;
+    const int m = inner_cycles(h);
+    for (int j = 0; j < m; ++j) {
+        if (h->loc == MG_LOC_NODAL) vcycle_node<float>(h, e, h->lev[0].b32, j == 0);
+        else vcycle_cell<float>(h, e, h->lev[0].b32, j == 0);
+    }
+    vec_axpy_f32(phi, e, &h->d->fscale, h->lev[0].nvec, h->stream);
+}
+
 // Iterate on L phi = f64 (rhs and ||f|| already prepared on the device).
 mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
 {
@@ -525,7 +564,7 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
     residual64(h, phi, r32);
     mg_status rc = readback(h);
     if (rc != MG_OK) return rc;
-    if (*reinterpret_cast<int*>(&h->hs->pad[0]) != 0)
+    if (h->hs->info != 0)
         return fail(MG_ERR_UNSUPPORTED, "the coarsest-level operator is singular");
     const double fn2 = h->hs->fnorm2;
     if (st) { st->rhs_norm = sqrt(fn2); st->iters = 0; st->rel_resid = 0.0; }
@@ -533,7 +572,7 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
         zero(phi, h->lev[0].nvec, s);
         return MG_OK;
     }
-    double rel = sqrt(h->hs->rnorm2 / fn2);
+    double rel = sqrt(h->hs->rnorm2);
     const double rel0 = rel;
     double best = rel;
     int stall = 0, it = 0;
@@ -541,10 +580,7 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
     while (rel > tol) {
         if (it >= h->opt.max_iters) { status = MG_ERR_NOT_CONVERGED; break; }
         if (mixed) {
-            float* e = h->lev[0].x32;
-            if (nodal) vcycle_node<float>(h, e, h->lev[0].b32, true);
-            else vcycle_cell<float>(h, e, h->lev[0].b32, true);
-            vec_axpy_f32(phi, e, &h->d->fscale, h->lev[0].nvec, s);
+            mixed_correction(h, phi);
         } else {
             if (nodal) vcycle_node<double>(h, phi, h->f64, false);
             else vcycle_cell<double>(h, phi, h->f64, false);
@@ -553,7 +589,7 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
         residual64(h, phi, r32);
         rc = readback(h);
         if (rc != MG_OK) return rc;
-        rel = sqrt(h->hs->rnorm2 / fn2);
+        rel = sqrt(h->hs->rnorm2);
         if (!isfinite(rel) || rel > 1e6 * (rel0 > 1.0 ? rel0 : 1.0)) { status = MG_ERR_DIVERGED; break; }
         if (rel < 0.9 * best) { best = rel; stall = 0; }
         else if (++stall >= 4) { status = rel <= tol ? MG_OK : MG_ERR_NOT_CONVERGED; break; }
@@ -567,6 +603,272 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
         g_last_error = buf;
     }
     return status;
+}
+
+
+// ======================================================= graph-resident solves
+//
+// A whole solve is captured once into a CUDA graph: rhs staging, the initial
+// residual, a conditional WHILE node whose body is one V-cycle (+ refinement
+// update) followed by the FP64 residual and a one-thread check kernel that
+// decides on the device whether to iterate again (cudaGraphSetConditional),
+// then the gauge, the copy-out of phi and a copy of the scalar block to pinned
+// host memory.  A solve is then one graph launch and one synchronisation; the
+// per-call pointers and tolerance reach the graph through the scalar block
+// (k_set_io), so the captured graph stays valid for every call.  The decisions
+// are the host loop's, made with the same formulas, so both paths iterate the
+// same number of times and produce the same phi.
+
+__global__ void k_set_io(DevScalars* d, const double* rhs, double* phi, double tol, int maxit)
+{
+    d->rhs_in = rhs;
+    d->phi_io = phi;
+    d->tol = tol;
+    d->maxit = maxit;
+}
+
+// dir 0: dst <- rhs_in; 1: dst <- phi_io; 2: phi_io <- dst.  No-op when aliased.
+__global__ void k_copy_io(double* __restrict__ dst, const DevScalars* __restrict__ d, size_t n, int dir)
+{
+    const double* src = dir == 0 ? d->rhs_in : (dir == 1 ? d->phi_io : dst);
+    double* out = dir == 2 ? d->phi_io : dst;
+    if (src == out) return;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        out[t] = src[t];
+}
+
+__global__ void k_zero_if_f0(double* __restrict__ phi, size_t n, const DevScalars* __restrict__ d)
+{
+    if (d->fnorm2 != 0.0) return;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        phi[t] = 0.0;
+}
+
+// Convergence decision after a residual (first: the initial one).  Mirrors the
+// host loop of solve_core.
+__global__ void k_check(DevScalars* d, cudaGraphConditionalHandle c, int first)
+{
+    if (threadIdx.x != 0) return;
+    const double fn2 = d->fnorm2;
+    unsigned cont = 0;
+    if (fn2 == 0.0) {
+        d->rel = 0.0;
+        if (first) d->iters = 0;
+        d->status = MG_OK;
+    } else {
+        const double rel = sqrt(d->rnorm2);
+        d->rel = rel;
+        int st = MG_OK, stop = 0;
+        if (first) {
+            d->iters = 0;
+            d->rel0 = rel;
+            d->best = rel;
+            d->stall = 0;
+        } else {
+            d->iters += 1;
+            const double r0 = d->rel0 > 1.0 ? d->rel0 : 1.0;
+            if (!isfinite(rel) || rel > 1e6 * r0) { st = MG_ERR_DIVERGED; stop = 1; }
+            else if (rel < 0.9 * d->best) { d->best = rel; d->stall = 0; }
+            else if (++d->stall >= 4) { st = rel <= d->tol ? MG_OK : MG_ERR_NOT_CONVERGED; stop = 1; }
+            if (!stop && rel < d->best) d->best = rel;
+        }
+        if (!stop && rel > d->tol && d->iters >= d->maxit) { st = MG_ERR_NOT_CONVERGED; stop = 1; }
+        d->status = st;
+        cont = (!stop && rel > d->tol) ? 1u : 0u;
+    }
+    cudaGraphSetConditional(c, cont);
+}
+
+// One refinement iteration (mixed) or V-cycle (FP64) on phi, then the residual.
+void iterate_once(mg_handle* h, double* phi, float* r32)
+{
+    const bool nodal = h->loc == MG_LOC_NODAL;
+    if (h->prec == MG_PREC_MIXED) {
+        mixed_correction(h, phi);
+    } else {
+        if (nodal) vcycle_node<double>(h, phi, h->f64, false);
+        else vcycle_cell<double>(h, phi, h->f64, false);
+    }
+    residual64(h, phi, r32);
+}
+
+mg_status capture_deps(cudaStream_t s, cudaGraph_t* g, std::vector<cudaGraphNode_t>& deps)
+{
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    MG_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, g, &d, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return fail(MG_ERR_CUDA, "stream is not capturing");
+    deps.assign(d, d + nd);
+    return MG_OK;
+}
+
+// Enqueue one whole solve of L phi_int = f64 on h->stream, which is capturing.
+mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream, long long& fixed, long long& body)
+{
+    cudaStream_t s = h->stream;
+    const size_t n = h->lev[0].nvec;
+    const bool nodal = h->loc == MG_LOC_NODAL;
+    double* phi = h->phi_int;
+    float* r32 = h->prec == MG_PREC_MIXED ? h->lev[0].b32 : nullptr;
+    const long long c0 = launch_count();
+    if (rhs_from_io) {
+        MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(h->f64, h->d, n, 0));
+        if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), h->f64, s);
+        vec_sum_sq(h->f64, n, h->partials, s);
+        reduce_finalize(h->partials, 2, h->d->red, s);
+        finish_rhs(h, 1, -1);
+    }
+    MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(phi, h->d, n, 1));
+    if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), phi, s);
+    residual64(h, phi, r32);
+    cudaGraph_t g;
+    std::vector<cudaGraphNode_t> deps;
+    mg_status rc = capture_deps(s, &g, deps);
+    if (rc != MG_OK) return rc;
+    cudaGraphConditionalHandle cond;
+    MG_CK(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+    MGP_LAUNCH(k_check<<<1, 32, 0, s>>>(h->d, cond, 1));
+    rc = capture_deps(s, &g, deps);
+    if (rc != MG_OK) return rc;
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = cond;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    MG_CK(cudaGraphAddNode(&wnode, g, deps.data(), nullptr, deps.size(), &prm));
+    MG_CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    const long long c1 = launch_count();
+    cudaGraph_t bodyg = prm.conditional.phGraph_out[0];
+    MG_CK(cudaStreamBeginCaptureToGraph(body_stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    h->stream = body_stream;
+    iterate_once(h, phi, r32);
+    MGP_LAUNCH(k_check<<<1, 32, 0, body_stream>>>(h->d, cond, 0));
+    h->stream = s;
+    MG_CK(cudaStreamEndCapture(body_stream, &bodyg));
+    const long long c2 = launch_count();
+    if (h->singular) gauge(h, phi);
+    MGP_LAUNCH(k_zero_if_f0<<<kRedBlocks, kThreads, 0, s>>>(phi, n, h->d));
+    MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(phi, h->d, n, 2));
+    MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    const long long c3 = launch_count();
+    fixed = (c1 - c0) + (c3 - c2);
+    body = c2 - c1;
+    MG_CK(cudaGetLastError());
+    return MG_OK;
+}
+
+struct CaptureStreams {
+    cudaStream_t main = nullptr, body = nullptr;
+    ~CaptureStreams()
+    {
+        if (main) cudaStreamDestroy(main);
+        if (body) cudaStreamDestroy(body);
+    }
+    mg_status make()
+    {
+        MG_CK(cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking));
+        MG_CK(cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking));
+        return MG_OK;
+    }
+};
+
+// Capture the handles' solves as independent branches of one graph.
+mg_status build_graph(mg_handle* const* hs, int count, bool rhs_from_io, cudaGraphExec_t* exec,
+                      std::vector<long long>& fixed, std::vector<long long>& body)
+{
+    CaptureStreams cs;
+    mg_status rc = cs.make();
+    if (rc != MG_OK) return rc;
+    fixed.assign(count, 0);
+    body.assign(count, 0);
+    MG_CK(cudaStreamBeginCapture(cs.main, cudaStreamCaptureModeRelaxed));
+    std::vector<cudaGraphNode_t> join;
+    for (int i = 0; i < count && rc == MG_OK; ++i) {
+        // every branch starts from the (empty) root of the graph
+        cudaStreamUpdateCaptureDependencies(cs.main, nullptr, nullptr, 0, cudaStreamSetCaptureDependencies);
+        cudaStream_t saved = hs[i]->stream;
+        hs[i]->stream = cs.main;
+        rc = capture_solve(hs[i], rhs_from_io, cs.body, fixed[i], body[i]);
+        hs[i]->stream = saved;
+        cudaGraph_t g;
+        std::vector<cudaGraphNode_t> sinks;
+        if (rc == MG_OK) rc = capture_deps(cs.main, &g, sinks);
+        join.insert(join.end(), sinks.begin(), sinks.end());
+    }
+    if (rc == MG_OK)
+        cudaStreamUpdateCaptureDependencies(cs.main, join.data(), nullptr, join.size(), cudaStreamSetCaptureDependencies);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs.main, &graph);
+    long long captured = 0;
+    for (int i = 0; i < count; ++i) captured += fixed[i] + body[i];
+    add_launches(-captured);  // capture enqueues nothing; replays are counted after each run
+    if (rc != MG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return MG_OK;
+}
+
+bool use_graph(const mg_handle* h) { return !(h->opt.flags & MG_FLAG_NO_GRAPH) && !prof().on; }
+
+mg_status ensure_graph(mg_handle* h, int which)
+{
+    if (h->gx[which]) return MG_OK;
+    std::vector<long long> f, b;
+    mg_status rc = build_graph(&h, 1, which == 0, &h->gx[which], f, b);
+    if (rc != MG_OK) return rc;
+    h->g_fixed[which] = f[0];
+    h->g_body[which] = b[0];
+    return MG_OK;
+}
+
+// Result of a finished graph solve (the scalar block is in h->hs).
+mg_status graph_result(mg_handle* h, long long fixed, long long body, mg_stats* st)
+{
+    const DevScalars& r = *h->hs;
+    add_launches(fixed + body * r.iters);
+    if (r.info != 0) return fail(MG_ERR_UNSUPPORTED, "the coarsest-level operator is singular");
+    if (st) {
+        st->iters = r.iters;
+        st->rel_resid = r.rel;
+        st->rhs_norm = sqrt(r.fnorm2);
+    }
+    if (r.status != MG_OK) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "stopped after %d iterations at relative residual %.3e (tol %.3e)", r.iters, r.rel,
+                 r.tol);
+        g_last_error = buf;
+    }
+    return (mg_status)r.status;
+}
+
+// Batch graphs, cached by the exact ordered list of handles.
+struct BatchGraph {
+    std::vector<mg_handle*> hs;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> fixed, body;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph*> g_batches;
+
+void drop_batches_of(mg_handle* h)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batches.size();) {
+        BatchGraph* b = g_batches[i];
+        bool has = false;
+        for (mg_handle* x : b->hs) has = has || x == h;
+        if (has) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            delete b;
+            g_batches.erase(g_batches.begin() + i);
+        } else {
+            ++i;
+        }
+    }
 }
 
 struct BusyGuard {
@@ -602,6 +904,7 @@ void mg_default_options(mg_options* o)
     o->omega = 0.9;
     o->stream = nullptr;
     o->flags = 0;
+    o->inner_cycles = 0;
 }
 
 static mg_status init_handle(mg_handle* h, const mg_geometry* g, const mg_bc* bc, const mg_options* o)
@@ -704,14 +1007,24 @@ mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_
     const double t0 = now_ms();
     cudaStream_t s = h->stream;
     const size_t n = h->lev[0].nvec;
-    vec_copy_f64(h->f64, rhs, n, s);
-    if (h->loc == MG_LOC_NODAL) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), h->f64, s);
-    vec_sum_sq(h->f64, n, h->partials, s);
-    reduce_finalize(h->partials, 2, h->d->red, s);
-    finish_rhs(h, 1, -1);
     mg_stats local;
     memset(&local, 0, sizeof local);
-    mg_status rc = solve_core(h, phi, tol, &local);
+    mg_status rc;
+    if (use_graph(h)) {
+        rc = ensure_graph(h, 0);
+        if (rc != MG_OK) return rc;
+        MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(h->d, rhs, phi, tol, h->opt.max_iters));
+        MG_CK(cudaGraphLaunch(h->gx[0], s));
+        MG_CK(cudaStreamSynchronize(s));
+        rc = graph_result(h, h->g_fixed[0], h->g_body[0], &local);
+    } else {
+        vec_copy_f64(h->f64, rhs, n, s);
+        if (h->loc == MG_LOC_NODAL) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), h->f64, s);
+        vec_sum_sq(h->f64, n, h->partials, s);
+        reduce_finalize(h->partials, 2, h->d->red, s);
+        finish_rhs(h, 1, -1);
+        rc = solve_core(h, phi, tol, &local);
+    }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "mg_solve");
     local.ms = now_ms() - t0;
@@ -748,7 +1061,17 @@ mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* b0, const
     mg_stats local;
     memset(&local, 0, sizeof local);
     // a3-a8
-    mg_status rc = solve_core(h, phi, tol, &local);
+    mg_status rc;
+    if (use_graph(h)) {
+        rc = ensure_graph(h, 1);
+        if (rc != MG_OK) return rc;
+        MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(h->d, nullptr, phi, tol, h->opt.max_iters));
+        MG_CK(cudaGraphLaunch(h->gx[1], s));
+        MG_CK(cudaStreamSynchronize(s));
+        rc = graph_result(h, h->g_fixed[1], h->g_body[1], &local);
+    } else {
+        rc = solve_core(h, phi, tol, &local);
+    }
     if (rc == MG_OK || rc == MG_ERR_NOT_CONVERGED) {
         // a9: projection update; a10: constraint
         if (h->loc == MG_LOC_CELL) {
@@ -777,9 +1100,56 @@ mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double*
                          int count, mg_stats* st)
 {
     if (count < 0 || (count > 0 && (!hs || !rhs || !phi || !tol))) return fail(MG_ERR_INVALID_ARG, "bad batch");
-    mg_status worst = MG_OK;
+    if (count == 0) return MG_OK;
+    bool graph = true;
     for (int i = 0; i < count; ++i) {
-        mg_status rc = mg_solve(hs[i], rhs[i], phi[i], tol[i], st ? &st[i] : nullptr);
+        if (!hs[i] || !rhs[i] || !phi[i] || !(tol[i] > 0.0)) return fail(MG_ERR_INVALID_ARG, "bad batch entry");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(MG_ERR_INVALID_ARG, "a handle appears twice in the batch");
+        graph = graph && use_graph(hs[i]);
+    }
+    mg_status worst = MG_OK;
+    if (!graph) {
+        for (int i = 0; i < count; ++i) {
+            mg_status rc = mg_solve(hs[i], rhs[i], phi[i], tol[i], st ? &st[i] : nullptr);
+            if (rc != MG_OK && worst == MG_OK) worst = rc;
+        }
+        return worst;
+    }
+    std::vector<std::unique_ptr<BusyGuard>> guards;
+    for (int i = 0; i < count; ++i) {
+        guards.emplace_back(new BusyGuard(hs[i]));
+        if (!guards.back()->ok) return fail(MG_ERR_BUSY, "handle in use");
+    }
+    const double t0 = now_ms();
+    BatchGraph* bg = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (BatchGraph* b : g_batches)
+            if ((int)b->hs.size() == count && std::equal(b->hs.begin(), b->hs.end(), hs)) bg = b;
+    }
+    if (!bg) {
+        std::unique_ptr<BatchGraph> nb(new BatchGraph());
+        nb->hs.assign(hs, hs + count);
+        mg_status rc = build_graph(hs, count, true, &nb->exec, nb->fixed, nb->body);
+        if (rc != MG_OK) return rc;
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        bg = nb.release();
+        g_batches.push_back(bg);
+    }
+    cudaStream_t s = hs[0]->stream;
+    for (int i = 0; i < count; ++i)
+        MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(hs[i]->d, rhs[i], phi[i], tol[i], hs[i]->opt.max_iters));
+    MG_CK(cudaGraphLaunch(bg->exec, s));
+    MG_CK(cudaStreamSynchronize(s));
+    const double ms = now_ms() - t0;
+    for (int i = 0; i < count; ++i) {
+        mg_stats local;
+        memset(&local, 0, sizeof local);
+        mg_status rc = graph_result(hs[i], bg->fixed[i], bg->body[i], &local);
+        local.ms = ms;
+        local.status = rc;
+        if (st) st[i] = local;
         if (rc != MG_OK && worst == MG_OK) worst = rc;
     }
     return worst;
@@ -800,6 +1170,9 @@ void mg_destroy(mg_handle* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    drop_batches_of(h);
+    for (int i = 0; i < 2; ++i)
+        if (h->gx[i]) cudaGraphExecDestroy(h->gx[i]);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->hs) cudaFreeHost(h->hs);
     delete h;

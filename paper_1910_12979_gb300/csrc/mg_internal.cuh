@@ -33,6 +33,7 @@ struct CellLevel {
     const T* by;
     const T* bz;
     const T* invd;  // optional 1/diagonal (FP64 levels); nullptr -> computed
+    const T* diag;  // optional diagonal for the FP64 residual; nullptr -> computed
 };
 
 // One nodal level: n cells per axis, N nodes per axis, sigma per cell, h^-2.
@@ -44,23 +45,33 @@ struct NodeLevel {
     const T* sigma;
     T ih2;
     const T* invd;      // optional 1/diagonal; nullptr -> computed
+    const T* diag;      // optional diagonal for the FP64 residual; nullptr -> computed
 };
 
-// Device scalars of one solve (reduction results).
+// Device scalars of one solve (reduction results and the iteration state that
+// the graph-resident solve loop keeps on the device).
 struct DevScalars {
     double red[kRedSlots];     // last reduction results
     double fnorm2;             // ||f||^2 of the system being solved
-    double rnorm2;             // ||f - L phi||^2, latest
+    double rnorm2;             // ||f - L phi||^2 / ||f||^2, latest (squared relative residual)
     double fscale;             // r32 = (f - L phi) / fscale in mixed refinement
     double mean;               // mean removed from f (singular problems)
     double src2;               // ||beta0 S||^2 or ||S_N||^2
     double con2;               // post-projection constraint^2
-    double pad[6];
+    double tol;                // relative tolerance of the current solve
+    double rel, rel0, best;    // relative residual: latest, initial, best
+    int info;                  // dense coarsest factorisation: 0 ok, k > 0 zero pivot
+    int iters, stall, status;  // iteration count, stalled iterations, mg_status
+    int maxit;
+    int pad_i;
+    const double* rhs_in;      // caller rhs of the current call (graph mode)
+    double* phi_io;            // caller phi of the current call (graph mode)
 };
 
 // Every kernel launch of the library goes through MGP_LAUNCH, which counts it
 // (mg_launch_count reports the total).
 void note_launch();
+void add_launches(long long n);
 long long launch_count();
 #define MGP_LAUNCH(...) (::mgp::note_launch(), __VA_ARGS__)
 
@@ -73,6 +84,7 @@ void cell_scale_faces(int dim, const CellLevel<double>& L, const double* const f
 void cell_coarsen_faces(int dim, const CellLevel<double>& F, const CellLevel<double>& C, double* bx, double* by,
                         double* bz, cudaStream_t s);
 void cell_invdiag(int dim, const CellLevel<double>& L, double* invd, cudaStream_t s);
+void cell_diag(int dim, const CellLevel<double>& L, double* diag, cudaStream_t s);
 template <typename T>
 void cell_gsrb(int dim, const CellLevel<T>& L, T* x, const T* b, int color, cudaStream_t s);
 // one full red-then-black sweep xin -> xout in a single launch (when ok)
@@ -85,7 +97,8 @@ void cell_resid_restrict(int dim, const CellLevel<T>& F, const T* x, const T* b,
 template <typename T>
 void cell_prolong_add(int dim, const CellLevel<T>& F, const CellLevel<T>& C, T* xf, const T* xc, int order,
                       cudaStream_t s);
-// r = b - L x in FP64; optional FP32 copy r/scale; ||r||^2 partials
+// r = b - L x in FP64; optional FP32 copy r/scale; partials of sum (r/scale)^2
+// (accumulated in FP32: the norm only steers convergence decisions)
 void cell_resid64(int dim, const CellLevel<double>& L, const double* x, const double* b, float* r32,
                   const double* scale, double* partials, cudaStream_t s);
 void cell_apply64(int dim, const CellLevel<double>& L, const double* x, double* out, cudaStream_t s);
@@ -102,6 +115,7 @@ void cell_dense_assemble(int dim, const CellLevel<T>& L, double* A, int lda, cud
 void node_coarsen_sigma(int dim, const NodeLevel<double>& F, const NodeLevel<double>& C, double* sc,
                         cudaStream_t s);
 void node_invdiag(int dim, const NodeLevel<double>& L, double* invd, cudaStream_t s);
+void node_diag(int dim, const NodeLevel<double>& L, double* diag, cudaStream_t s);
 // tiled: allow the shared-memory tiled kernel (3-D levels of at least 32 x 8 nodes)
 template <typename T>
 void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s);

@@ -317,28 +317,43 @@ k_node_tiled(NodeLevel<T> L, const T* __restrict__ x, T* __restrict__ out, const
 
 // -------------------------------------------------------- FP64 residuals
 
-template <int DIM>
+template <int DIM, bool HAS_DIAG>
 __global__ void k_node_resid64(NodeLevel<double> L, const double* __restrict__ x, const double* __restrict__ b,
                                float* __restrict__ r32, const double* __restrict__ scale,
                                double* __restrict__ partials)
 {
     const int total = L.Nx * L.Ny * L.Nz;
-    const double inv = (r32 && scale) ? 1.0 / *scale : 1.0;
-    double acc[1] = {0.0};
+    const double inv = 1.0 / *scale;
+    float acc = 0.f;
     const NodePhi<double> ph{x, L.Nx, L.Ny};
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         int i, j, k;
         unflat(t, L.Nx, L.Ny, i, j, k);
-        double r = 0.0;
+        float rs = 0.f;
         if (!node_dirichlet(L, i, j, k, DIM)) {
             double off, dg;
             node_row<DIM>(L, i, j, k, ph, off, dg);
-            r = b[t] - (off + dg * x[t]);
+            const double d = HAS_DIAG ? L.diag[t] : dg;
+            rs = (float)((b[t] - (off + d * x[t])) * inv);
         }
-        acc[0] += r * r;
-        if (r32) r32[t] = (float)(r * inv);
+        acc = fmaf(rs, rs, acc);
+        if (r32) r32[t] = rs;
     }
-    block_reduce_store<1>(acc, partials);
+    double a[1] = {(double)acc};
+    block_reduce_store<1>(a, partials);
+}
+
+template <int DIM>
+__global__ void k_node_diag(NodeLevel<double> L, double* __restrict__ diag)
+{
+    const int total = L.Nx * L.Ny * L.Nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    unflat(t, L.Nx, L.Ny, i, j, k);
+    double off, dg;
+    node_row<DIM>(L, i, j, k, [](int, int, int) { return 0.0; }, off, dg);
+    diag[t] = node_dirichlet(L, i, j, k, DIM) ? 0.0 : dg;
 }
 
 template <int DIM>
@@ -536,8 +551,19 @@ void node_prolong_add(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, T* 
 void node_resid64(int dim, const NodeLevel<double>& L, const double* x, const double* b, float* r32,
                   const double* scale, double* partials, cudaStream_t s)
 {
-    if (dim == 2) MGP_LAUNCH(k_node_resid64<2><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
-    else MGP_LAUNCH(k_node_resid64<3><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+    if (dim == 2) {
+        if (L.diag) MGP_LAUNCH(k_node_resid64<2, true><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+        else MGP_LAUNCH(k_node_resid64<2, false><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+    } else {
+        if (L.diag) MGP_LAUNCH(k_node_resid64<3, true><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+        else MGP_LAUNCH(k_node_resid64<3, false><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+    }
+}
+
+void node_diag(int dim, const NodeLevel<double>& L, double* diag, cudaStream_t s)
+{
+    if (dim == 2) MGP_LAUNCH(k_node_diag<2><<<nb(nnod(L)), kThreads, 0, s>>>(L, diag));
+    else MGP_LAUNCH(k_node_diag<3><<<nb(nnod(L)), kThreads, 0, s>>>(L, diag));
 }
 
 void node_apply64(int dim, const NodeLevel<double>& L, const double* x, double* out, cudaStream_t s)

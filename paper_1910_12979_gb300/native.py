@@ -18,6 +18,7 @@ MG_BC_PERIODIC, MG_BC_NEUMANN, MG_BC_DIRICHLET = 0, 1, 2
 MG_LOC_CELL, MG_LOC_NODAL = 0, 1
 MG_PREC_FP64, MG_PREC_MIXED = 0, 1
 MG_FLAG_NO_FUSED = 1
+MG_FLAG_NO_GRAPH = 2
 
 BC = {"periodic": MG_BC_PERIODIC, "neumann": MG_BC_NEUMANN, "dirichlet": MG_BC_DIRICHLET}
 
@@ -43,7 +44,7 @@ class mg_beta0(ctypes.Structure):
 class mg_options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("coarsest_max", ctypes.c_int), ("interp_order", ctypes.c_int), ("omega", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("flags", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("flags", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):

@@ -31,7 +31,7 @@ class ProjectionSolver:
     """
 
     def __init__(self, geom, sigma, loc="cell", prec="mixed", faces=None, nu1=2, nu2=2, max_iters=100,
-                 coarsest_max=64, interp_order=1, omega=0.9, stream=None, flags=0):
+                 coarsest_max=64, interp_order=1, omega=0.9, stream=None, flags=0, inner_cycles=0):
         N.load()
         self.dim = int(geom["dim"])
         n = list(geom["n"]) + [1] * (3 - len(geom["n"]))
@@ -49,6 +49,7 @@ class ProjectionSolver:
         opt.nu1, opt.nu2, opt.max_iters = nu1, nu2, max_iters
         opt.coarsest_max, opt.interp_order, opt.omega = coarsest_max, interp_order, omega
         opt.flags = flags
+        opt.inner_cycles = inner_cycles
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt.stream = self.stream.cuda_stream
         self.opt = opt

@@ -1,0 +1,107 @@
+"""Graph-resident solve loop and the one-launch batch, through the C ABI.
+
+The graph path makes the convergence decisions on the device with the same
+formulas as the host loop (MG_FLAG_NO_GRAPH), so both must return the same phi
+bit for bit after the same number of iterations.  mg_solve_batch runs every
+solve as a branch of one graph; each branch must equal the solve run alone.
+"""
+import numpy as np
+import pytest
+
+import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1910_12979_gb300 import ProjectionSolver, solve_batch  # noqa: E402
+from paper_1910_12979_gb300 import native as N  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+@pytest.mark.parametrize("loc", ["cell", "nodal"])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_graph_equals_host_loop(loc, prec):
+    p = I.stratified(32, seed=21, contrast=1e3)
+    res = []
+    for flags in (0, N.MG_FLAG_NO_GRAPH):
+        s = ProjectionSolver(p["geom"], T(p["sigma"]), loc=loc, prec=prec, flags=flags)
+        f = T(np.random.default_rng(8).normal(size=s.vec_shape))
+        phi = torch.zeros_like(f)
+        st = s.solve(f, phi, tol=1e-11)
+        res.append((phi, st))
+        s.close()
+    (a, sa), (b, sb) = res
+    assert sa["iters"] == sb["iters"] and sa["rel_resid"] == sb["rel_resid"]
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("loc", ["cell", "nodal"])
+def test_graph_projection_equals_host_loop(loc):
+    p = I.stratified(32, seed=22, contrast=1e2)
+    out = []
+    for flags in (0, N.MG_FLAG_NO_GRAPH):
+        s = ProjectionSolver(p["geom"], T(p["sigma"]), loc=loc, prec="mixed", flags=flags)
+        U = [T(u) for u in (p["U_mac"] if loc == "cell" else p["U_cell"])]
+        kw = {"beta0_face": [T(b) for b in p["beta0_face"]]} if loc == "cell" else {}
+        st = s.project(U, T(p["beta0"]), T(p["S"]), tol=1e-10, **kw)
+        out.append((U, st))
+    (ua, sa), (ub, sb) = out
+    assert sa["iters"] == sb["iters"] and sa["rel_constraint"] == sb["rel_constraint"]
+    for x, y in zip(ua, ub):
+        assert torch.equal(x, y)
+
+
+def test_batch_one_launch_equals_alone():
+    """Uneven sizes, both locations and both precisions in one graph launch."""
+    specs = [(16, "cell", "mixed"), (32, "cell", "mixed"), (24, "nodal", "mixed"), (32, "cell", "fp64"),
+             (48, "cell", "mixed"), (16, "nodal", "fp64")]
+    solvers, rhs = [], []
+    for i, (n, loc, prec) in enumerate(specs):
+        p = I.stratified(n, seed=30 + i, contrast=10.0 ** (1 + i % 3), mac=False, nodal=False)
+        s = ProjectionSolver(p["geom"], T(p["sigma"]), loc=loc, prec=prec)
+        solvers.append(s)
+        rhs.append(T(np.random.default_rng(i).normal(size=s.vec_shape)))
+    alone = []
+    for s, f in zip(solvers, rhs):
+        phi = torch.zeros_like(f)
+        st = s.solve(f, phi, tol=1e-10)
+        alone.append((phi, st))
+    for _ in range(2):  # the second call replays the cached batch graph
+        phis = [torch.full_like(f, 7.0) * 0 for f in rhs]
+        stats = solve_batch(solvers, rhs, phis, [1e-10] * len(rhs))
+        for (pa, sa), pb, sb in zip(alone, phis, stats):
+            assert sb["iters"] == sa["iters"] and sb["status"] == N.MG_OK
+            assert torch.equal(pa, pb)
+
+
+def test_batch_reports_per_solve_status():
+    p = I.stratified(32, seed=3, contrast=1e3, mac=False, nodal=False)
+    a = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed")
+    b = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", max_iters=2)
+    f = T(np.random.default_rng(1).normal(size=a.vec_shape))
+    pa, pb = torch.zeros_like(f), torch.zeros_like(f)
+    st = solve_batch([a, b], [f, f], [pa, pb], [1e-10, 1e-12], allow_not_converged=True)
+    assert st[0]["status"] == N.MG_OK and st[1]["status"] == N.MG_ERR_NOT_CONVERGED and st[1]["iters"] == 2
+    with pytest.raises(N.MGError):
+        solve_batch([a, a], [f, f], [pa, pb], [1e-10, 1e-10])
+
+
+def test_graph_zero_rhs_and_warm_start():
+    p = I.stratified(32, seed=4, contrast=1e3, mac=False, nodal=False)
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed")
+    phi = torch.ones(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.solve(torch.zeros_like(phi), phi, tol=1e-10)
+    assert st["iters"] == 0 and float(phi.abs().max()) == 0.0
+    f = T(np.random.default_rng(2).normal(size=s.vec_shape))
+    phi = torch.zeros_like(f)
+    s.solve(f, phi, tol=1e-10)
+    st2 = s.solve(f, phi, tol=1e-10)   # warm start at the solution: no iteration needed
+    assert st2["iters"] == 0

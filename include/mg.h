@@ -234,6 +234,32 @@ typedef enum {
     MG_PROF_COUNT = 4
 } mg_prof_kernel;
 
+/* Allocation-free check of the MAC constraint.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory at the
+ * moment they need the answer -- code running while a CUDA graph is being
+ * captured, or a process whose device-memory budget is already handed out --
+ * and it calls no cudaMalloc, cudaFree or allocating library routine.  For MAC
+ * face velocities U it writes, for v = D(beta0 U) - beta0 S over the cells,
+ *   out[0] = sum v,   out[1] = sum (beta0 S)^2,   out[2] = sum v^2
+ * (the relative constraint reported by mg_project is sqrt(out[2] / out[1])).
+ *   geom    cell grid (loc MG_LOC_CELL), at most MG_NOALLOC_MAX_CELLS cells;
+ *           larger grids return MG_ERR_UNSUPPORTED (the scratch holds one
+ *           partial sum per 2048 cells)
+ *   U, beta0, S   device arrays as for mg_project (beta0->face required)
+ *   out     device, 3 doubles, written by the call
+ *   stream  cudaStream_t (NULL: the legacy default stream); asynchronous
+ * Its reduction scratch is a fixed device array of 3 * MG_NOALLOC_MAX_CELLS /
+ * 2048 doubles (384 KiB) that every GPU loading the library holds until the
+ * process exits.  Each call overwrites every slot it reads, so nothing needs
+ * clearing between calls; but all calls share that one array, so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * device address (once per device, with that device current): make that first
+ * call before any stream capture. */
+#define MG_NOALLOC_MAX_CELLS (1 << 25)
+mg_status mg_mac_constraint_noalloc(const mg_geometry* geom, const double* const U[3], const mg_beta0* beta0,
+                                    const double* S, double* out, void* stream);
+
 void mg_prof_enable(int on);
 /* Total number of CUDA kernels this library has launched in the process. */
 long long mg_launch_count(void);

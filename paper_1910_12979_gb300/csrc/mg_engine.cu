@@ -120,6 +120,8 @@ struct Level {
 
 }  // namespace
 
+void mgp::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct mg_handle {
     mg_geometry geo;
     mg_bc bcin;

@@ -70,6 +70,8 @@ struct DevScalars {
 
 // Every kernel launch of the library goes through MGP_LAUNCH, which counts it
 // (mg_launch_count reports the total).
+// sets the message mg_last_error() returns on this thread
+void set_last_error(const char* msg);
 void note_launch();
 void add_launches(long long n);
 long long launch_count();

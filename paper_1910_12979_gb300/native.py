@@ -77,6 +77,9 @@ SIGNATURES = [
     ("mg_destroy", None, [ctypes.c_void_p]),
     ("mg_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("mg_last_error", ctypes.c_char_p, []),
+    ("mg_mac_constraint_noalloc", ctypes.c_int, [ctypes.POINTER(mg_geometry), ctypes.c_void_p * 3,
+                                                 ctypes.POINTER(mg_beta0), ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
     ("mg_prof_enable", None, [ctypes.c_int]),
     ("mg_launch_count", ctypes.c_longlong, []),
     ("mg_prof_query", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),

@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="time only the mixed-precision step (no graph-path, FP64, e2e or CPU legs): the "
+                         "command used for ncu captures")
     return ap.parse_args()
 
 
@@ -322,13 +325,17 @@ def main():
             "solver": {"mac": {k: st_mac[k] for k in ("iters", "rel_resid", "rel_constraint")},
                        "nodal": {k: st_nod[k] for k in ("iters", "rel_resid", "rel_constraint")}}}
 
+    if args.only_mixed:
+        args.no_fp64 = args.no_e2e = args.no_cpu = True
     # the same step with the graph-resident solve loop (no per-kernel events)
-    msg, launches_g, _, _ = timed(mixed, args.steps, 1)
-    value_graph = 2.0 * args.steps * world / (msg / 1e3)
-    line["graph_path"] = {"value": value_graph, "unit": UNIT, "ms_per_step": msg / args.steps,
-                          "gpu_launches": launches_g,
-                          "note": "same step, iterations driven by CUDA-graph conditional nodes; the headline "
-                                  "value uses the host-driven loop so that per-kernel CUDA events can be recorded"}
+    msg, launches_g, _, _ = (0.0, 0, None, None) if args.only_mixed else timed(mixed, args.steps, 1)
+    value_graph = 2.0 * args.steps * world / (msg / 1e3) if msg > 0 else None
+    if not args.only_mixed:
+        line["graph_path"] = {"value": value_graph, "unit": UNIT, "ms_per_step": msg / args.steps,
+                              "gpu_launches": launches_g,
+                              "note": "same step, iterations driven by CUDA-graph conditional nodes; the headline "
+                                      "value uses the host-driven loop so that per-kernel CUDA events can be "
+                                      "recorded"}
 
     # plain FP64 GPU multigrid on the same workload (graph path, like graph_path above)
     if not args.no_fp64:

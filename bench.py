@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="stratified", choices=["stratified", "batch", "serve"],
+                    help="stratified: the default 256^3 MAC + nodal step; batch: 64 uneven MAC solves in one "
+                         "graph launch; serve: Poisson stream of polytrope-star projections (p50/p99)")
+    ap.add_argument("--budget-gb", type=float, default=24.0, help="serve: device-memory budget of the slots")
+    ap.add_argument("--inflight", type=int, default=8, help="serve: concurrent solves")
+    ap.add_argument("--serve-count", type=int, default=256, help="serve: requests per arrival rate")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed-precision step (no graph-path, FP64, e2e or CPU legs): the "
                          "command used for ncu captures")
@@ -195,6 +201,130 @@ def ncu_traffic(kernel_class):
     return e.get("bytes_per_launch")
 
 
+def run_batch(args, dev, world, dist):
+    """64 independent MAC solves of uneven size (32-128^3), one graph launch per step."""
+    import numpy as np
+    import torch
+
+    import inputs as I
+    from paper_1910_12979_gb300 import ProjectionSolver, solve_batch
+    from paper_1910_12979_gb300 import native as N
+
+    specs = I.batch_specs(64, seed=4)
+    stream = torch.cuda.Stream(device=dev)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    solvers, rhs, phis, cells = [], [], [], 0
+    with torch.cuda.stream(stream):
+        for sp in specs:
+            p = I.batch_problem(sp)
+            s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", stream=stream)
+            f = s.rhs([T(u) for u in p["U_mac"]], T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]])
+            solvers.append(s)
+            rhs.append(f)
+            phis.append(torch.zeros_like(f))
+            cells += sp["n"] ** 3
+    stream.synchronize()
+    tols = [args.tol] * len(solvers)
+
+    def step():
+        with torch.cuda.stream(stream):
+            for ph in phis:
+                ph.zero_()
+        return solve_batch(solvers, rhs, phis, tols, allow_not_converged=True)
+
+    for _ in range(args.warmup):
+        st = step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = N.mg_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = N.mg_launch_count() - l0
+    # the same solves one after another (one graph launch and one sync per solve)
+    t_seq = 0.0
+    for s, f, ph in zip(solvers, rhs, phis):
+        ph.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            s.solve(f, ph, tol=args.tol, allow_not_converged=True)
+        b.record(stream)
+        b.synchronize()
+        t_seq += a.elapsed_time(b)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = len(solvers) * args.steps * world / (ms / 1e3)
+    return {"metric": "independent projection solves/s, uneven batch in one graph launch", "value": value,
+            "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (mixed)", "data": "synthetic",
+            "config": {"workload": "batch of 64 MAC solves, n in {32,64,96,128} (seed 4), contrast log-uniform "
+                                   "in [1e1,1e4], one graph launch per step", "cells": cells, "tol": args.tol,
+                       "l2": "aggregate inputs larger than L2"},
+            "gpu_launches": launches,
+            "iters": {"min": min(x["iters"] for x in st), "max": max(x["iters"] for x in st)},
+            "worst_rel_resid": max(x["rel_resid"] for x in st),
+            "sequential": {"value": len(solvers) / (t_seq / 1e3), "unit": "solves/s",
+                           "note": "the same 64 solves issued one mg_solve at a time"}}
+
+
+def run_serve(args, dev, rank, world, dist):
+    """Poisson stream of polytrope-star MAC projections, sizes 64..256^3."""
+    import numpy as np
+    import torch
+
+    import inputs as I
+    from paper_1910_12979_gb300 import native as N
+    from paper_1910_12979_gb300.serve import GpuBackend, Scheduler, device_problem, latency_stats, make_requests, shard
+
+    sizes = (64, 96, 128, 192, 256)
+    problems = {n: [device_problem(I.polytrope_star(n, seed=500 + n + k), dev) for k in range(2)] for n in sizes}
+    budget = int(args.budget_gb * 2 ** 30)
+    l0 = N.mg_launch_count()
+
+    def serve(reqs):
+        sch = Scheduler(GpuBackend(problems, device=str(dev), tol=args.tol), budget, max_inflight=args.inflight)
+        done = sch.run_stream(reqs, timeout=900)
+        ev = sch.evictions
+        sch.close()
+        return done, ev
+
+    rng = np.random.default_rng(5)
+    # saturation: every request present at t = 0
+    sat_n = args.serve_count // 4
+    ns = [int(x) for x in rng.choice(sizes, size=sat_n)]
+    serve(make_requests([0.0] * 8, ns[:8], 2))                     # warm-up: slot creation, graphs
+    done, _ = serve(shard(make_requests([0.0] * sat_n, ns, 2), rank, world))
+    mu = latency_stats(done)["solves_per_s"]
+    rates = {}
+    for frac in (0.5, 0.8, 0.95):
+        t, ns2 = I.poisson_arrivals(frac * mu * world, args.serve_count, seed=5, sizes=sizes)
+        reqs = shard(make_requests(t, ns2, 2, seed=5), rank, world)
+        done, ev = serve(reqs)
+        bad = sum(isinstance(r.status, Exception) for r in done)
+        rates[str(frac)] = dict(latency_stats(done), evictions=ev, failed=bad)
+    launches = N.mg_launch_count() - l0
+    head = rates["0.8"]
+    out = {"metric": "serving: projection solves/s and p50/p99 latency at 0.8 x saturation", "value":
+           head["solves_per_s"] * world, "unit": "solves/s", "n_gpus": world, "steps": args.serve_count,
+           "warmup": 8, "ms_per_step": 1e3 / head["solves_per_s"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+           "config": {"workload": "Poisson arrivals of polytrope (n=3) star MAC projections, Dirichlet, "
+                                  "sizes {64,96,128,192,256}^3 (seed 5)", "budget_gb": args.budget_gb,
+                      "max_inflight": args.inflight, "tol": args.tol},
+           "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "saturation_solves_per_s": mu * world,
+           "rates": rates, "gpu_launches": launches}
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -224,6 +354,15 @@ def main():
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if args.workload != "stratified":
+        line = run_batch(args, dev, world, dist) if args.workload == "batch" else run_serve(args, dev, rank, world,
+                                                                                              dist)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     stream = torch.cuda.Stream(device=dev)
     n = args.n
     p = I.stratified(n, seed=3, contrast=1e3)

@@ -190,6 +190,14 @@ mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_
 mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* beta0, const double* S, double* phi,
                      double tol, mg_stats* stats);
 
+/* Right-hand side of the projection system (step a2) into a caller buffer f
+ * (device, unknown layout: cells for MAC, nodes for nodal):
+ *   MAC    f = D(beta0 U) - beta0 S     (beta0->face required)
+ *   nodal  f = D_N(beta0 U) - S_N       (Dirichlet nodes 0)
+ * with the mean removed when the problem is singular.  Synchronises the
+ * handle's stream. */
+mg_status mg_rhs(mg_handle* h, const double* const U[3], const mg_beta0* beta0, const double* S, double* f);
+
 /* Solve count independent problems (any mix of grids, precisions and
  * locations; each handle at most once) as ONE CUDA graph launch on the first
  * handle's stream: every solve is a branch of the graph with its own

@@ -145,6 +145,30 @@ __global__ void k_coarsen_faces(CellLevel<double> F, CellLevel<double> C, const 
     coarse[t] = s * (0.25 / nsub);
 }
 
+// The diagonal of row (i,j,k) alone: the dg sum of cell_row, in the same order.
+template <int DIM>
+__device__ __forceinline__ double cell_dg(const CellLevel<double>& L, int i, int j, int k)
+{
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    double dg = 0.0;
+    auto term = [&](double b, bool inside, int bc) {
+        if (inside || bc == BCP) dg += b;
+        else if (bc == BCD) dg += 2.0 * b;
+    };
+    const size_t rx = ((size_t)k * ny + j) * (nx + 1) + i;
+    term(L.bx[rx], i > 0, L.bc.lo[0]);
+    term(L.bx[rx + 1], i < nx - 1, L.bc.hi[0]);
+    const size_t ry = ((size_t)k * (ny + 1) + j) * nx + i;
+    term(L.by[ry], j > 0, L.bc.lo[1]);
+    term(L.by[ry + nx], j < ny - 1, L.bc.hi[1]);
+    if (DIM == 3) {
+        const size_t rz = ((size_t)k * ny + j) * nx + i, pl = (size_t)nx * ny;
+        term(L.bz[rz], k > 0, L.bc.lo[2]);
+        term(L.bz[rz + pl], k < nz - 1, L.bc.hi[2]);
+    }
+    return dg;
+}
+
 template <int DIM>
 __global__ void k_invdiag(CellLevel<double> L, double* __restrict__ invd)
 {
@@ -153,9 +177,7 @@ __global__ void k_invdiag(CellLevel<double> L, double* __restrict__ invd)
     if (t >= total) return;
     int i, j, k;
     unflat(t, L.nx, L.ny, i, j, k);
-    double off, dg;
-    cell_row<DIM>(L, i, j, k, [](int, int, int) { return 0.0; }, off, dg);
-    invd[t] = recip(dg);
+    invd[t] = recip(cell_dg<DIM>(L, i, j, k));
 }
 
 // ------------------------------------------------------------- smoothing
@@ -291,9 +313,7 @@ __global__ void k_diag(CellLevel<double> L, double* __restrict__ diag)
     if (t >= total) return;
     int i, j, k;
     unflat(t, L.nx, L.ny, i, j, k);
-    double off, dg;
-    cell_row<DIM>(L, i, j, k, [](int, int, int) { return 0.0; }, off, dg);
-    diag[t] = dg;
+    diag[t] = cell_dg<DIM>(L, i, j, k);
 }
 
 template <int DIM>

@@ -182,6 +182,64 @@ __global__ void __launch_bounds__(kGJThreads) k_gauss_jordan(double* __restrict_
     }
 }
 
+// Same elimination with the augmented matrix resident in shared memory
+// (n <= kGJSmemMax): one global read of A, one global write of Minv.
+constexpr int kGJSmemMax = 112;
+
+__global__ void __launch_bounds__(kGJThreads) k_gauss_jordan_smem(const double* __restrict__ A, int n, int N,
+                                                                 double* __restrict__ Minv, int* __restrict__ info)
+{
+    extern __shared__ double W[];  // n x 2n
+    const int ld = 2 * n;
+    for (int t = threadIdx.x; t < n * ld; t += blockDim.x) {
+        const int r = t / ld, c = t - r * ld;
+        W[t] = c < n ? A[(size_t)r * ld + c] : ((c - n) == r ? 1.0 : 0.0);
+    }
+    __shared__ int piv;
+    __shared__ double pval;
+    if (threadIdx.x == 0) *info = 0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {  // n <= 112: a serial pivot search is cheaper than a reduction
+            double b = -1.0;
+            int p = k;
+            for (int r = k; r < n; ++r) {
+                const double v = fabs(W[r * ld + k]);
+                if (v > b) { b = v; p = r; }
+            }
+            piv = p;
+            pval = W[p * ld + k];
+            if (b <= 0.0) *info = k + 1;
+        }
+        __syncthreads();
+        if (pval == 0.0) return;
+        const int p = piv;
+        if (p != k)
+            for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+                const double tmp = W[k * ld + c];
+                W[k * ld + c] = W[p * ld + c];
+                W[p * ld + c] = tmp;
+            }
+        __syncthreads();
+        const double inv = 1.0 / pval;
+        for (int c = threadIdx.x; c < ld; c += blockDim.x) W[k * ld + c] *= inv;
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * ld; t += blockDim.x) {
+            const int r = t / ld, c = t - r * ld;
+            if (r == k || c == k) continue;
+            W[t] -= W[r * ld + k] * W[k * ld + c];
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x)
+            if (r != k) W[r * ld + k] = 0.0;
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+        const int r = t / N, c = t - r * N;
+        Minv[t] = W[r * ld + n + c];
+    }
+}
+
 __global__ void k_extract(const double* __restrict__ W, int n, int N, double* __restrict__ Minv)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N * N; t += gridDim.x * blockDim.x) {
@@ -196,6 +254,17 @@ int dense_invert(double* A, int N, int singular, double* Minv, int* info, cudaSt
 {
     const int n = N + (singular ? 1 : 0);
     if (singular) MGP_LAUNCH(k_border<<<1, 256, 0, s>>>(A, N, 2 * n));
+    if (n <= kGJSmemMax) {
+        const size_t smem = (size_t)n * 2 * n * sizeof(double);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kGJSmemMax * 2 * kGJSmemMax * sizeof(double)));
+            attr = true;
+        }
+        MGP_LAUNCH(k_gauss_jordan_smem<<<1, kGJThreads, smem, s>>>(A, n, N, Minv, info));
+        return 0;
+    }
     MGP_LAUNCH(k_gauss_jordan<<<1, kGJThreads, 0, s>>>(A, n, info));
     MGP_LAUNCH(k_extract<<<64, 256, 0, s>>>(A, n, N, Minv));
     return 0;

@@ -11,12 +11,13 @@ __host__ __device__ inline int ceil_div(long long a, long long b) { return (int)
 
 // Deterministic block reduction of NS doubles; thread 0 stores the block's
 // partial sums at partials[q * kRedBlocks + blockIdx.x].  The grid must have
-// exactly kRedBlocks blocks of kThreads threads.
+// exactly kRedBlocks blocks (1-D grid) of kThreads threads (any block shape).
 template <int NS>
 __device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* __restrict__ partials)
 {
     __shared__ double sh[NS][kThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);  // 1-D or 2-D blocks
+    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         double x = v[q];

@@ -101,6 +101,23 @@ __global__ void k_coarsen_sigma(NodeLevel<double> F, NodeLevel<double> C, double
     sc[t] = s / (1 << DIM);
 }
 
+// The diagonal of node row (i,j,k) alone: node_row's dg, same order of sums.
+template <int DIM>
+__device__ __forceinline__ double node_dg(const NodeLevel<double>& L, int i, int j, int k)
+{
+    double ssum = 0.0;
+#pragma unroll
+    for (int c = 0; c < (1 << DIM); ++c) {
+        const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1, sz = (c & 4) ? 1 : -1;
+        int ci, cj, ck = 0;
+        if (!cell_ok(sx > 0 ? i : i - 1, L.nx, L.bc.lo[0], ci)) continue;
+        if (!cell_ok(sy > 0 ? j : j - 1, L.ny, L.bc.lo[1], cj)) continue;
+        if (DIM == 3 && !cell_ok(sz > 0 ? k : k - 1, L.nz, L.bc.lo[2], ck)) continue;
+        ssum += L.sigma[((size_t)ck * L.ny + cj) * L.nx + ci];
+    }
+    return DIM == 3 ? -ssum * (L.ih2 / 3.0) : -ssum * (L.ih2 * 2.0 / 3.0);
+}
+
 template <int DIM>
 __global__ void k_node_invdiag(NodeLevel<double> L, double* __restrict__ invd)
 {
@@ -109,9 +126,7 @@ __global__ void k_node_invdiag(NodeLevel<double> L, double* __restrict__ invd)
     if (t >= total) return;
     int i, j, k;
     unflat(t, L.Nx, L.Ny, i, j, k);
-    double off, dg;
-    node_row<DIM>(L, i, j, k, [](int, int, int) { return 0.0; }, off, dg);
-    invd[t] = node_dirichlet(L, i, j, k, DIM) ? 0.0 : recip(dg);
+    invd[t] = node_dirichlet(L, i, j, k, DIM) ? 0.0 : recip(node_dg<DIM>(L, i, j, k));
 }
 
 // ------------------------------------------------------------- smoothing
@@ -351,9 +366,7 @@ __global__ void k_node_diag(NodeLevel<double> L, double* __restrict__ diag)
     if (t >= total) return;
     int i, j, k;
     unflat(t, L.Nx, L.Ny, i, j, k);
-    double off, dg;
-    node_row<DIM>(L, i, j, k, [](int, int, int) { return 0.0; }, off, dg);
-    diag[t] = node_dirichlet(L, i, j, k, DIM) ? 0.0 : dg;
+    diag[t] = node_dirichlet(L, i, j, k, DIM) ? 0.0 : node_dg<DIM>(L, i, j, k);
 }
 
 template <int DIM>
@@ -411,6 +424,92 @@ __global__ void k_node_rhs(NodeLevel<double> L, double h, CPtr3 U, const double*
         acc[0] += v;
         acc[1] += lump * lump;
         acc[2] += v * v;
+    }
+    block_reduce_store<3>(acc, partials);
+}
+
+// Tiled 3-D version of k_node_rhs.  Per z-plane the cells around a 32 x 8 node
+// tile get W = beta0 U (3 components) and beta0 S computed once into shared
+// memory; each node then forms D_N from signed sums of its 8 cells (additions
+// only) and the lumped source from their sum.  Cells outside a non-periodic
+// boundary hold 0 (natural boundary condition).  The fixed kRedBlocks grid
+// strides over (tile, z-chunk) work items, so the reduction stays deterministic.
+struct NodeRhsShared {
+    double w[2][4][kNTY + 1][kNTX + 1];  // [plane ring][Wx, Wy, Wz, beta0 S][y][x]
+};
+
+__global__ void __launch_bounds__(kNTX * kNTY)
+k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restrict__ b0, const double* __restrict__ S,
+                 double* __restrict__ f, double* __restrict__ partials, int kz)
+{
+    constexpr int TX = kNTX, TY = kNTY;
+    __shared__ NodeRhsShared sh;
+    const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
+    const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
+    const int tx_n = (Nx + TX - 1) / TX, ty_n = (Ny + TY - 1) / TY, tz_n = (Nz + kz - 1) / kz;
+    const int items = tx_n * ty_n * tz_n;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const double wdiv = 1.0 / (4.0 * h), wl = 1.0 / 8.0;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int bx = it % tx_n, by = (it / tx_n) % ty_n, bz = it / (tx_n * ty_n);
+        const int x0 = bx * TX, y0 = by * TY, z0 = bz * kz, z1 = min(z0 + kz, Nz);
+        auto load = [&](int c) {  // cell plane c -> ring slot
+            int gz = c;
+            bool zok = true;
+            if (gz < 0 || gz >= nz) { if (pz) gz = gz < 0 ? gz + nz : gz - nz; else zok = false; }
+            const int slot = (c + 2) & 1;
+            for (int q = tid; q < (TX + 1) * (TY + 1); q += TX * TY) {
+                const int ly = q / (TX + 1), lx = q - ly * (TX + 1);
+                int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+                bool ok = zok;
+                if (gx < 0 || gx >= nx) { if (px) gx = gx < 0 ? gx + nx : gx - nx; else ok = false; }
+                if (gy < 0 || gy >= ny) { if (py) gy = gy < 0 ? gy + ny : gy - ny; else ok = false; }
+                if (gx >= nx || gy >= ny) ok = false;
+                double w0 = 0.0, w1 = 0.0, w2 = 0.0, ws = 0.0;
+                if (ok) {
+                    const size_t id = ((size_t)gz * ny + gy) * nx + gx;
+                    const double bb = b0[id];
+                    w0 = bb * U.p[0][id];
+                    w1 = bb * U.p[1][id];
+                    w2 = bb * U.p[2][id];
+                    ws = bb * S[id];
+                }
+                sh.w[slot][0][ly][lx] = w0;
+                sh.w[slot][1][ly][lx] = w1;
+                sh.w[slot][2][ly][lx] = w2;
+                sh.w[slot][3][ly][lx] = ws;
+            }
+        };
+        load(z0 - 1);
+        for (int k = z0; k < z1; ++k) {
+            load(k);
+            __syncthreads();
+            const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+            if (i < Nx && j < Ny) {
+                const size_t id = ((size_t)k * Ny + j) * Nx + i;
+                double v = 0.0, lump = 0.0;
+                if (!node_dirichlet(L, i, j, k, 3)) {
+                    const int lx = threadIdx.x, ly = threadIdx.y;  // cell (i-1, j-1) is at (lx, ly)
+                    const int sp = (k + 2) & 1, sm = (k + 1) & 1;   // cell planes k and k-1
+                    auto W = [&](int s, int q, int a, int b) { return sh.w[s][q][ly + b][lx + a]; };
+                    const double dx = (W(sp, 0, 1, 1) + W(sp, 0, 1, 0) + W(sm, 0, 1, 1) + W(sm, 0, 1, 0)) -
+                                      (W(sp, 0, 0, 1) + W(sp, 0, 0, 0) + W(sm, 0, 0, 1) + W(sm, 0, 0, 0));
+                    const double dy = (W(sp, 1, 1, 1) + W(sp, 1, 0, 1) + W(sm, 1, 1, 1) + W(sm, 1, 0, 1)) -
+                                      (W(sp, 1, 1, 0) + W(sp, 1, 0, 0) + W(sm, 1, 1, 0) + W(sm, 1, 0, 0));
+                    const double dz = (W(sp, 2, 1, 1) + W(sp, 2, 0, 1) + W(sp, 2, 1, 0) + W(sp, 2, 0, 0)) -
+                                      (W(sm, 2, 1, 1) + W(sm, 2, 0, 1) + W(sm, 2, 1, 0) + W(sm, 2, 0, 0));
+                    lump = ((W(sp, 3, 1, 1) + W(sp, 3, 0, 1)) + (W(sp, 3, 1, 0) + W(sp, 3, 0, 0)) +
+                            (W(sm, 3, 1, 1) + W(sm, 3, 0, 1)) + (W(sm, 3, 1, 0) + W(sm, 3, 0, 0))) * wl;
+                    v = (dx + dy + dz) * wdiv - lump;
+                }
+                if (f) f[id] = v;
+                acc[0] += v;
+                acc[1] += lump * lump;
+                acc[2] += v * v;
+            }
+            __syncthreads();
+        }
     }
     block_reduce_store<3>(acc, partials);
 }
@@ -576,6 +675,14 @@ void node_rhs(int dim, const NodeLevel<double>& L, double h, const double* const
               const double* S, double* f, double* partials, cudaStream_t s)
 {
     CPtr3 u{{U[0], U[1], dim == 3 ? U[2] : nullptr}};
+    if (dim == 3 && L.Nx >= kNTX && L.Ny >= kNTY) {
+        // about 4 work items per block
+        const long long tiles = (long long)((L.Nx + kNTX - 1) / kNTX) * ((L.Ny + kNTY - 1) / kNTY);
+        int kz = (int)((tiles * L.Nz + kRedBlocks * 4 - 1) / (kRedBlocks * 4));
+        kz = kz < 4 ? 4 : kz;
+        MGP_LAUNCH(k_node_rhs_tiled<<<kRedBlocks, dim3(kNTX, kNTY), 0, s>>>(L, h, u, b0, S, f, partials, kz));
+        return;
+    }
     if (dim == 2) MGP_LAUNCH(k_node_rhs<2><<<kRedBlocks, kThreads, 0, s>>>(L, h, u, b0, S, f, partials));
     else MGP_LAUNCH(k_node_rhs<3><<<kRedBlocks, kThreads, 0, s>>>(L, h, u, b0, S, f, partials));
 }

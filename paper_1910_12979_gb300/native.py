@@ -69,6 +69,8 @@ SIGNATURES = [
                                 ctypes.POINTER(mg_stats)]),
     ("mg_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p * 3, ctypes.POINTER(mg_beta0), ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(mg_stats)]),
+    ("mg_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p * 3, ctypes.POINTER(mg_beta0), ctypes.c_void_p,
+                              ctypes.c_void_p]),
     ("mg_solve_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                       ctypes.POINTER(mg_stats)]),
@@ -177,6 +179,12 @@ def mg_project(h, U_ptrs, beta0, S_ptr, phi_ptr, tol, allow=(MG_OK,)):
                            ctypes.c_void_p(phi_ptr) if phi_ptr else None, ctypes.c_double(tol), ctypes.byref(st))
     check(rc, "mg_project", allow)
     return st
+
+
+def mg_rhs(h, U_ptrs, beta0, S_ptr, f_ptr):
+    arr = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(p) if p else None for p in U_ptrs])
+    return check(load().mg_rhs(h, arr, ctypes.byref(beta0), ctypes.c_void_p(S_ptr), ctypes.c_void_p(f_ptr)),
+                 "mg_rhs")
 
 
 def mg_solve_batch(handles, rhs_ptrs, phi_ptrs, tols, allow=(MG_OK,)):

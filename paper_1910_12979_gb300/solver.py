@@ -118,6 +118,26 @@ class ProjectionSolver:
                           _ptr(phi, "phi", self.vec_shape) if phi is not None else None, tol, allow)
         return st.as_dict()
 
+    def _beta0(self, beta0_cell, beta0_face):
+        b0 = N.mg_beta0()
+        b0.cell = _ptr(beta0_cell, "beta0_cell", self.cell_shape)
+        if self.loc == "cell":
+            if beta0_face is None:
+                raise ValueError("the MAC projection needs beta0 at faces")
+            for d in range(self.dim):
+                b0.face[d] = _ptr(beta0_face[d], f"beta0_face[{d}]", self.face_shape(d))
+        return b0
+
+    def rhs(self, U, beta0_cell, S, beta0_face=None, out=None):
+        """f = D(beta0 U) - beta0 S (MAC) or D_N(beta0 U) - S_N (nodal), mean-free if singular."""
+        if out is None:
+            out = torch.empty(self.vec_shape, dtype=torch.float64, device=self.device)
+        shp = (lambda d: self.face_shape(d)) if self.loc == "cell" else (lambda d: self.cell_shape)
+        ptrs = [_ptr(U[d], f"U[{d}]", shp(d)) for d in range(self.dim)] + [None] * (3 - self.dim)
+        N.mg_rhs(self.handle, ptrs, self._beta0(beta0_cell, beta0_face), _ptr(S, "S", self.cell_shape),
+                 _ptr(out, "f", self.vec_shape))
+        return out
+
     def apply(self, phi, out=None):
         if out is None:
             out = torch.empty(self.vec_shape, dtype=torch.float64, device=self.device)

@@ -50,8 +50,10 @@ __device__ __forceinline__ void unflat(int t, int nx, int ny, int& i, int& j, in
 
 template <typename T>
 __device__ __forceinline__ T recip(T d);
+// FP32 levels only precondition the FP64 refinement: the fast reciprocal
+// (about 2 ulp) is accurate far beyond what the V-cycle needs.
 template <>
-__device__ __forceinline__ float recip<float>(float d) { return d != 0.f ? 1.f / d : 0.f; }
+__device__ __forceinline__ float recip<float>(float d) { return d != 0.f ? __fdividef(1.f, d) : 0.f; }
 template <>
 __device__ __forceinline__ double recip<double>(double d) { return d != 0.0 ? 1.0 / d : 0.0; }
 

@@ -441,8 +441,9 @@ void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, i
 {
     cudaStream_t s = h->stream;
     const double cells = (double)h->lev[l].ncell;
-    if (!(h->opt.flags & MG_FLAG_NO_FUSED) && cell_gsrb_fused_ok<T>(h->dim, V)) {
-        T* t = lt<T>(h, l);
+    T* t = lt<T>(h, l);
+    auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    if (!(h->opt.flags & MG_FLAG_NO_FUSED) && cell_gsrb_fused_ok<T>(h->dim, V) && a16(x) && a16(t) && a16(b)) {
         T* src = x;
         T* dst = t;
         for (int k = 0; k < nu; ++k) {
@@ -1096,6 +1097,29 @@ mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* b0, const
     local.status = rc;
     if (st) *st = local;
     return rc;
+}
+
+mg_status mg_rhs(mg_handle* h, const double* const U[3], const mg_beta0* b0, const double* S, double* f)
+{
+    if (!h || !U || !b0 || !b0->cell || !S || !f) return fail(MG_ERR_INVALID_ARG, "null argument");
+    for (int d = 0; d < h->dim; ++d) {
+        if (!U[d]) return fail(MG_ERR_INVALID_ARG, "U[d] is null");
+        if (h->loc == MG_LOC_CELL && !b0->face[d]) return fail(MG_ERR_INVALID_ARG, "beta0 faces are required (MAC)");
+    }
+    BusyGuard g(h);
+    if (!g.ok) return fail(MG_ERR_BUSY, "handle in use");
+    cudaStream_t s = h->stream;
+    const Level& v0 = h->lev[0];
+    const double* Uc[3] = {U[0], U[1], h->dim == 3 ? U[2] : nullptr};
+    if (h->loc == MG_LOC_CELL) cell_rhs(h->dim, cview<double>(h, 0), v0.h, Uc, b0->face, b0->cell, S, f, h->partials, s);
+    else node_rhs(h->dim, nview<double>(h, 0), v0.h[0], Uc, b0->cell, S, f, h->partials, s);
+    if (h->singular) {
+        reduce_finalize(h->partials, 1, h->d->red, s);
+        vec_sub_mean(f, v0.nvec, &h->d->red[0], (double)v0.nvec, s);
+    }
+    MG_CK(cudaGetLastError());
+    MG_CK(cudaStreamSynchronize(s));
+    return MG_OK;
 }
 
 mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double* const* phi, const double* tol,

@@ -1,59 +1,67 @@
 // mg_sweep.cu -- pipelined one-launch red-black Gauss-Seidel sweep (cell-centred, 3-D).
 //
 // One full sweep (red, then black) of the variable-coefficient 7-point
-// operator, reading xin and writing xout (ping-pong).  A CTA owns a 32 x TY
+// operator, reading xin and writing xout (ping-pong).  A CTA owns a 32 x 8
 // column tile and marches through a chunk of z-planes.  Every operand of a
 // plane -- xin with a 2-cell halo, b and the three face-coefficient planes over
 // the tile plus a 1-cell ring -- is copied into a 5-slot shared-memory ring by
 // cp.async two planes ahead of its use, so the HBM latency of plane k+2
 // overlaps the arithmetic of plane k.  Per plane:
-//   red on plane k over the tile + ring (old black neighbours from xin), then
-//   black on plane k-1 over the tile (new red neighbours), write plane k-1.
+//   red on plane k over the tile + ring (old black neighbours from xin):
+//       thread t < 170 owns one red cell of the 34 x 10 ring region;
+//   black on plane k-1 over the tile (new red neighbours): thread t < 128 owns
+//       one red/black pair of the tile, computes the black cell and stores the
+//       pair with one 8-byte write.
 // The ring's red values are recomputed by neighbouring CTAs; that redundancy is
 // what lets one launch replace two dependent colour passes.  The row arithmetic
-// (order of the six face terms, boundary handling, the diagonal) is the same as
-// k_gsrb's, so the result equals two colour passes bit for bit.
+// (order of the six face terms, boundary handling, the diagonal) is that of
+// k_gsrb, so the result equals two colour passes bit for bit.
 //
-// Requirements (checked by the launcher): nx % 32 == 0, ny % TY == 0, nz >= 2,
-// z not periodic.
+// Every staged array starts at column x0 - 2 (even, so pairs of cells can be
+// copied 8 bytes at a time, and pairs never straddle a periodic wrap because nx
+// is even).  Requirements (checked by the launcher): nx % 32 == 0,
+// ny % 8 == 0, nz >= 2, z not periodic.
 #include "mg_device.cuh"
 
 namespace mgp {
 
-constexpr int kPX = 32;       // tile width
-constexpr int kPSlots = 5;    // ring depth (planes)
+constexpr int kPX = 32;        // tile width
+constexpr int kPY = 8;         // tile height
+constexpr int kPSlots = 5;     // ring depth (planes)
+constexpr int kPW = kPX + 4;   // staged row width: columns x0-2 .. x0+33
+constexpr int kPT = kPX * kPY; // threads
+constexpr int kRedCells = (kPX + 2) * (kPY + 2) / 2;  // red cells of the tile + ring: 170
 
-template <typename T, int TY>
+template <typename T>
 struct PipeSlot {
-    T X[TY + 4][kPX + 4];     // xin, 2-cell halo
-    T Bb[TY + 2][kPX + 2];    // b over the tile + ring
-    T FX[TY + 2][kPX + 3];    // x-faces of the tile + ring cells
-    T FY[TY + 3][kPX + 2];    // y-faces
-    T FZ[TY + 2][kPX + 2];    // low z-faces of the plane
-    T IV[TY + 2][kPX + 2];    // 1/diagonal (FP64 levels only)
+    T X[kPY + 4][kPW];   // xin, rows y0-2 .. y0+9
+    T Bb[kPY + 2][kPW];  // b, rows y0-1 .. y0+8
+    T FZ[kPY + 2][kPW];  // low z-faces of the plane
+    T IV[kPY + 2][kPW];  // 1/diagonal (FP64 levels only)
+    T FY[kPY + 3][kPW];  // y-faces, rows y0-1 .. y0+9
+    T FX[kPY + 2][kPW];  // x-faces x0-2 .. x0+33 of rows y0-1 .. y0+8
 };
 
-template <typename T, int TY>
+template <typename T>
 struct PipeShared {
-    PipeSlot<T, TY> slot[kPSlots];
-    T rs[3][TY + 2][kPX + 2];  // new red values, planes k-2..k
+    PipeSlot<T> slot[kPSlots];
+    T rs[3][kPY + 2][kPW];  // new red values of planes k-2..k (columns as Bb)
 };
 
-__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem, bool valid, int bytes)
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool valid, int bytes)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     const int n = valid ? bytes : 0;  // src-size 0: zero fill, nothing read
-    if (bytes == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+    if (bytes == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+    else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+    else asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// global index along an axis of n cells for a tile-local position, wrapped
-// when periodic; -1 when outside a non-periodic axis.  faces: n + 1 entries.
+// global position along an axis of n cells (faces: n + 1 entries) for a
+// tile-relative position, wrapped when periodic; -1 outside a non-periodic axis
 __device__ __forceinline__ int axis_pos(int g, int n, bool periodic, bool faces)
 {
     const int hi = faces ? n : n - 1;
@@ -62,170 +70,156 @@ __device__ __forceinline__ int axis_pos(int g, int n, bool periodic, bool faces)
     return g < 0 ? g + n : g - n;
 }
 
-template <typename T, int TY>
-struct PipeArrays {  // per-array copy geometry: columns, rows, elements per thread
-    static constexpr int NT = kPX * TY;
-    static constexpr int NX = (TY + 4) * (kPX + 4);
-    static constexpr int NB = (TY + 2) * (kPX + 2);
-    static constexpr int NFX = (TY + 2) * (kPX + 3);
-    static constexpr int NFY = (TY + 3) * (kPX + 2);
-    static constexpr int PX = (NX + NT - 1) / NT, PB = (NB + NT - 1) / NT, PFX = (NFX + NT - 1) / NT,
-                         PFY = (NFY + NT - 1) / NT;
+// One staged array: each thread copies at most one element pair (or element)
+// per plane; its in-plane source offset is fixed for the whole march.
+struct CopyDesc {
+    int dst;  // element index within the slot array, or -1: no copy by this thread
+    int src;  // in-plane element offset, or -1: outside the domain (zero fill)
 };
 
-template <typename T, int TY>
-__global__ void __launch_bounds__(kPX * TY)
+template <typename T>
+__global__ void __launch_bounds__(kPT)
 k_gsrb_pipe(CellLevel<T> L, const T* __restrict__ xin, T* __restrict__ xout, const T* __restrict__ b, int kz)
 {
-    using A = PipeArrays<T, TY>;
-    constexpr int TX = kPX, NT = A::NT, RX = TX + 4, QX = TX + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PipeShared<T, TY>& sh = *reinterpret_cast<PipeShared<T, TY>*>(smem_raw);
+    PipeShared<T>& sh = *reinterpret_cast<PipeShared<T>*>(smem_raw);
 
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
     const int z0 = blockIdx.z * kz, z1 = min(z0 + kz, nz);
-    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int tid = threadIdx.x;
     const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP;
     const bool has_iv = L.invd != nullptr;
     const size_t plane = (size_t)nx * ny, fxplane = (size_t)(nx + 1) * ny, fyplane = (size_t)nx * (ny + 1);
 
-    // plane-independent in-plane offsets (-1: outside the domain -> zero fill)
-    int offX[A::PX], offB[A::PB], offFX[A::PFX], offFY[A::PFY];
+    // ---- copy descriptors (pairs for X, Bb, FZ, IV, FY; single elements for FX)
+    constexpr int PAIRS = kPW / 2;  // 18 pairs per row
+    auto pair_desc = [&](int rows, int row0, int idx, bool face_rows, int pitch) {
+        CopyDesc d{-1, -1};
+        if (idx < rows * PAIRS) {
+            const int r = idx / PAIRS, c = 2 * (idx - r * PAIRS);
+            d.dst = r * kPW + c;
+            const int gx = axis_pos(x0 - 2 + c, nx, px, false), gy = axis_pos(row0 + r, ny, py, face_rows);
+            d.src = (gx >= 0 && gy >= 0) ? gy * pitch + gx : -1;
+        }
+        return d;
+    };
+    const CopyDesc dX = pair_desc(kPY + 4, y0 - 2, tid, false, nx);
+    const CopyDesc dB = pair_desc(kPY + 2, y0 - 1, tid, false, nx);
+    const CopyDesc dY = pair_desc(kPY + 3, y0 - 1, tid, true, nx);
+    CopyDesc dF[2];
 #pragma unroll
-    for (int e = 0; e < A::PX; ++e) {
-        const int q = tid + e * NT, ly = q / RX, lx = q - ly * RX;
-        const int gx = axis_pos(x0 - 2 + lx, nx, px, false), gy = axis_pos(y0 - 2 + ly, ny, py, false);
-        offX[e] = (q < A::NX && gx >= 0 && gy >= 0) ? gy * nx + gx : -1;
+    for (int e = 0; e < 2; ++e) {
+        const int q = tid + e * kPT;
+        dF[e] = CopyDesc{-1, -1};
+        if (q < (kPY + 2) * kPW) {
+            const int r = q / kPW, c = q - r * kPW;
+            dF[e].dst = q;
+            const int fx = axis_pos(x0 - 2 + c, nx, px, true), gy = axis_pos(y0 - 1 + r, ny, py, false);
+            dF[e].src = (fx >= 0 && gy >= 0) ? gy * (nx + 1) + fx : -1;
+        }
     }
-#pragma unroll
-    for (int e = 0; e < A::PB; ++e) {
-        const int q = tid + e * NT, ly = q / QX, lx = q - ly * QX;
-        const int gx = axis_pos(x0 - 1 + lx, nx, px, false), gy = axis_pos(y0 - 1 + ly, ny, py, false);
-        offB[e] = (q < A::NB && gx >= 0 && gy >= 0) ? gy * nx + gx : -1;
-    }
-#pragma unroll
-    for (int e = 0; e < A::PFX; ++e) {
-        const int q = tid + e * NT, ly = q / (QX + 1), lx = q - ly * (QX + 1);
-        const int fx = axis_pos(x0 - 1 + lx, nx, px, true), gy = axis_pos(y0 - 1 + ly, ny, py, false);
-        offFX[e] = (q < A::NFX && fx >= 0 && gy >= 0) ? gy * (nx + 1) + fx : -1;
-    }
-#pragma unroll
-    for (int e = 0; e < A::PFY; ++e) {
-        const int q = tid + e * NT, ly = q / QX, lx = q - ly * QX;
-        const int gx = axis_pos(x0 - 1 + lx, nx, px, false), fy = axis_pos(y0 - 1 + ly, ny, py, true);
-        offFY[e] = (q < A::NFY && gx >= 0 && fy >= 0) ? fy * nx + gx : -1;
-    }
+    constexpr int PB = 2 * sizeof(T);  // bytes of one pair
 
-    // stage plane p (X, b, faces for p < nz; the low z-face plane for p <= nz)
     auto issue = [&](int p) {
         if (p >= 0 && p <= nz) {
-            PipeSlot<T, TY>& S = sh.slot[p % kPSlots];
+            PipeSlot<T>& S = sh.slot[p % kPSlots];
             const bool cellp = p < nz;
-            T* X = &S.X[0][0];
-            T* Bb = &S.Bb[0][0];
-            T* FX = &S.FX[0][0];
-            T* FY = &S.FY[0][0];
-            T* FZ = &S.FZ[0][0];
-            T* IV = &S.IV[0][0];
-#pragma unroll
-            for (int e = 0; e < A::PX; ++e) {
-                const int q = tid + e * NT;
-                if (q < A::NX) cp_async_elem(X + q, xin + (cellp ? p * plane : 0) + (offX[e] < 0 ? 0 : offX[e]),
-                                             cellp && offX[e] >= 0, sizeof(T));
+            const T* xp = xin + (cellp ? p * plane : 0);
+            const T* bp = b + (cellp ? p * plane : 0);
+            const T* zp = L.bz + p * plane;
+            const T* yp = L.by + (cellp ? p * fyplane : 0);
+            const T* fp = L.bx + (cellp ? p * fxplane : 0);
+            if (dX.dst >= 0) cp_async(&S.X[0][0] + dX.dst, xp + (dX.src < 0 ? 0 : dX.src), cellp && dX.src >= 0, PB);
+            if (dB.dst >= 0) {
+                const int o = dB.src < 0 ? 0 : dB.src;
+                cp_async(&S.Bb[0][0] + dB.dst, bp + o, cellp && dB.src >= 0, PB);
+                cp_async(&S.FZ[0][0] + dB.dst, zp + o, dB.src >= 0, PB);
+                if (has_iv) cp_async(&S.IV[0][0] + dB.dst, L.invd + (cellp ? p * plane : 0) + o, cellp && dB.src >= 0, PB);
             }
+            if (dY.dst >= 0) cp_async(&S.FY[0][0] + dY.dst, yp + (dY.src < 0 ? 0 : dY.src), cellp && dY.src >= 0, PB);
 #pragma unroll
-            for (int e = 0; e < A::PB; ++e) {
-                const int q = tid + e * NT;
-                if (q < A::NB) {
-                    const size_t o = (offB[e] < 0 ? 0 : offB[e]);
-                    cp_async_elem(Bb + q, b + (cellp ? p * plane : 0) + o, cellp && offB[e] >= 0, sizeof(T));
-                    cp_async_elem(FZ + q, L.bz + p * plane + o, offB[e] >= 0, sizeof(T));
-                    if (has_iv)
-                        cp_async_elem(IV + q, L.invd + (cellp ? p * plane : 0) + o, cellp && offB[e] >= 0, sizeof(T));
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < A::PFX; ++e) {
-                const int q = tid + e * NT;
-                if (q < A::NFX)
-                    cp_async_elem(FX + q, L.bx + (cellp ? p * fxplane : 0) + (offFX[e] < 0 ? 0 : offFX[e]),
-                                  cellp && offFX[e] >= 0, sizeof(T));
-            }
-#pragma unroll
-            for (int e = 0; e < A::PFY; ++e) {
-                const int q = tid + e * NT;
-                if (q < A::NFY)
-                    cp_async_elem(FY + q, L.by + (cellp ? p * fyplane : 0) + (offFY[e] < 0 ? 0 : offFY[e]),
-                                  cellp && offFY[e] >= 0, sizeof(T));
-            }
+            for (int e = 0; e < 2; ++e)
+                if (dF[e].dst >= 0)
+                    cp_async(&S.FX[0][0] + dF[e].dst, fp + (dF[e].src < 0 ? 0 : dF[e].src), cellp && dF[e].src >= 0,
+                             sizeof(T));
         }
         cp_async_commit();
     };
 
-    // The row of cell (gx, gy, k) at ring position (lx, ly) (R1 coordinates),
-    // in k_gsrb's order: x low, x high, y low, y high, z low, z high.
-    // Neighbour values come from V(dx, dy, dz).
-    auto row = [&](const PipeSlot<T, TY>& Sk, const PipeSlot<T, TY>& Sk1, int gx, int gy, int k, int lx, int ly,
-                   auto V, T& off, T& dg) {
+    // ---- the row arithmetic, in k_gsrb's order.  (cx, cy): the cell's column
+    // in the staged arrays (x0-2 origin) and its row in the ring arrays
+    // (y0-1 origin); V(dx, dy, dz) returns the neighbour value.
+    auto row = [&](const PipeSlot<T>& Sk, const PipeSlot<T>& Sk1, int gx, int gy, int k, int cx, int cy, auto V,
+                   T& off, T& dg) {
         off = T(0);
         dg = T(0);
-        const T bxl = Sk.FX[ly][lx], bxh = Sk.FX[ly][lx + 1];
+        const T bxl = Sk.FX[cy][cx], bxh = Sk.FX[cy][cx + 1];
         if (gx > 0 || L.bc.lo[0] == BCP) { off += bxl * V(-1, 0, 0); dg += bxl; }
         else if (L.bc.lo[0] == BCD) { dg += T(2) * bxl; }
         if (gx < nx - 1 || L.bc.hi[0] == BCP) { off += bxh * V(1, 0, 0); dg += bxh; }
         else if (L.bc.hi[0] == BCD) { dg += T(2) * bxh; }
-        const T byl = Sk.FY[ly][lx], byh = Sk.FY[ly + 1][lx];
+        const T byl = Sk.FY[cy][cx], byh = Sk.FY[cy + 1][cx];
         if (gy > 0 || L.bc.lo[1] == BCP) { off += byl * V(0, -1, 0); dg += byl; }
         else if (L.bc.lo[1] == BCD) { dg += T(2) * byl; }
         if (gy < ny - 1 || L.bc.hi[1] == BCP) { off += byh * V(0, 1, 0); dg += byh; }
         else if (L.bc.hi[1] == BCD) { dg += T(2) * byh; }
-        const T bzl = Sk.FZ[ly][lx], bzh = Sk1.FZ[ly][lx];
+        const T bzl = Sk.FZ[cy][cx], bzh = Sk1.FZ[cy][cx];
         if (k > 0) { off += bzl * V(0, 0, -1); dg += bzl; }
         else if (L.bc.lo[2] == BCD) { dg += T(2) * bzl; }
         if (k < nz - 1) { off += bzh * V(0, 0, 1); dg += bzh; }
         else if (L.bc.hi[2] == BCD) { dg += T(2) * bzh; }
     };
 
+    // ---- red cell of this thread (t < 170): ring row ry, pair index rix
+    const bool red_thread = tid < kRedCells;
+    const int ry = tid / (kPX / 2 + 1), rix = tid - ry * (kPX / 2 + 1);
+    const int rgy = axis_pos(y0 - 1 + ry, ny, py, false);
+    // ---- black pair of this thread (t < 128): tile row by, pair bp
+    const bool black_thread = tid < kPT / 2;
+    const int by = tid / (kPX / 2), bp = tid - by * (kPX / 2);
+
     auto red = [&](int k) {
-        const PipeSlot<T, TY>& Sk = sh.slot[k % kPSlots];
-        const PipeSlot<T, TY>& Sk1 = sh.slot[(k + 1) % kPSlots];
-        const PipeSlot<T, TY>& Skm = sh.slot[(k + kPSlots - 1) % kPSlots];
-#pragma unroll
-        for (int e = 0; e < A::PB; ++e) {
-            const int q = tid + e * NT;
-            if (q >= A::NB) continue;
-            const int ly = q / QX, lx = q - ly * QX;
-            const int gx = axis_pos(x0 - 1 + lx, nx, px, false), gy = axis_pos(y0 - 1 + ly, ny, py, false);
-            if (gx < 0 || gy < 0 || ((gx + gy + k) & 1) != 0) continue;
-            auto V = [&](int dx, int dy, int dz) -> T {
-                const PipeSlot<T, TY>& S = dz < 0 ? Skm : (dz > 0 ? Sk1 : Sk);
-                return S.X[ly + 1 + dy][lx + 1 + dx];
-            };
-            T off, dg;
-            row(Sk, Sk1, gx, gy, k, lx, ly, V, off, dg);
-            const T inv = has_iv ? Sk.IV[ly][lx] : recip(dg);
-            sh.rs[k % 3][ly][lx] = (off - Sk.Bb[ly][lx]) * inv;
-        }
+        if (!red_thread || rgy < 0) return;
+        const int lx = 2 * rix + ((1 + rgy + k) & 1);  // ring column 0..33 of a red cell
+        const int gx = axis_pos(x0 - 1 + lx, nx, px, false);
+        if (gx < 0) return;
+        const PipeSlot<T>& Sk = sh.slot[k % kPSlots];
+        const PipeSlot<T>& Sk1 = sh.slot[(k + 1) % kPSlots];
+        const PipeSlot<T>& Skm = sh.slot[(k + kPSlots - 1) % kPSlots];
+        const int cx = lx + 1, cy = ry;
+        auto V = [&](int dx, int dy, int dz) -> T {
+            const PipeSlot<T>& S = dz < 0 ? Skm : (dz > 0 ? Sk1 : Sk);
+            return S.X[cy + 1 + dy][cx + dx];
+        };
+        T off, dg;
+        row(Sk, Sk1, gx, rgy, k, cx, cy, V, off, dg);
+        const T inv = has_iv ? Sk.IV[cy][cx] : recip(dg);
+        sh.rs[k % 3][cy][cx] = (off - Sk.Bb[cy][cx]) * inv;
     };
 
     auto black = [&](int k) {
-        const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-        const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-        const size_t id = (size_t)k * plane + (size_t)gy * nx + gx;
-        T v;
-        if (((gx + gy + k) & 1) == 0) {
-            v = sh.rs[k % 3][ly][lx];
-        } else {
-            const PipeSlot<T, TY>& Sk = sh.slot[k % kPSlots];
-            const PipeSlot<T, TY>& Sk1 = sh.slot[(k + 1) % kPSlots];
-            auto V = [&](int dx, int dy, int dz) -> T { return sh.rs[(k + dz + 3) % 3][ly + dy][lx + dx]; };
-            T off, dg;
-            row(Sk, Sk1, gx, gy, k, lx, ly, V, off, dg);
-            const T inv = has_iv ? Sk.IV[ly][lx] : recip(dg);
-            v = (off - Sk.Bb[ly][lx]) * inv;
-        }
-        xout[id] = v;
+        if (!black_thread) return;
+        const int gy = y0 + by, xa = x0 + 2 * bp;          // the pair's first cell
+        const int bx = 2 * bp + ((xa + gy + k + 1) & 1);    // black cell, tile column
+        const int gx = x0 + bx;
+        const int cx = bx + 2, cy = by + 1;
+        const PipeSlot<T>& Sk = sh.slot[k % kPSlots];
+        const PipeSlot<T>& Sk1 = sh.slot[(k + 1) % kPSlots];
+        const int r0 = k % 3, rm = (k + 2) % 3, rp = (k + 1) % 3;
+        auto V = [&](int dx, int dy, int dz) -> T {
+            const int r = dz < 0 ? rm : (dz > 0 ? rp : r0);
+            return sh.rs[r][cy + dy][cx + dx];
+        };
+        T off, dg;
+        row(Sk, Sk1, gx, gy, k, cx, cy, V, off, dg);
+        const T inv = has_iv ? Sk.IV[cy][cx] : recip(dg);
+        const T vb = (off - Sk.Bb[cy][cx]) * inv;
+        const T vr = sh.rs[r0][cy][cx + (bx & 1 ? -1 : 1)];  // the pair's red cell
+        const size_t id = (size_t)k * plane + (size_t)gy * nx + xa;
+        T* dst = xout + id;
+        if (bx & 1) { dst[0] = vr; dst[1] = vb; }
+        else { dst[0] = vb; dst[1] = vr; }
     };
 
     const int kfirst = max(z0 - 1, 0), klast = min(z1, nz - 1);
@@ -252,25 +246,24 @@ k_gsrb_pipe(CellLevel<T> L, const T* __restrict__ xin, T* __restrict__ xout, con
 template <typename T>
 bool cell_gsrb_fused_ok(int dim, const CellLevel<T>& L)
 {
-    return dim == 3 && L.nx % kPX == 0 && L.ny % 8 == 0 && L.nz >= 2 && L.bc.lo[2] != BCP;
+    return dim == 3 && L.nx % kPX == 0 && L.ny % kPY == 0 && L.nz >= 2 && L.bc.lo[2] != BCP;
 }
 
 template <typename T>
 void cell_gsrb_sweep(int dim, const CellLevel<T>& L, const T* xin, T* xout, const T* b, cudaStream_t s)
 {
-    constexpr int TY = 8;
-    const size_t smem = sizeof(PipeShared<T, TY>);
+    const size_t smem = sizeof(PipeShared<T>);
     static bool attr_set = false;  // one attribute call per instantiation
     if (!attr_set) {
-        cudaFuncSetAttribute(k_gsrb_pipe<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_gsrb_pipe<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
     // a chunk of z-planes per CTA: about 4 CTAs per SM over 152 SMs
-    const long long tiles = (long long)(L.nx / kPX) * (L.ny / TY);
+    const long long tiles = (long long)(L.nx / kPX) * (L.ny / kPY);
     int kz = (int)((tiles * L.nz + 152 * 4 - 1) / (152 * 4));
     kz = kz < 8 ? 8 : kz;
-    dim3 grid(L.nx / kPX, L.ny / TY, (L.nz + kz - 1) / kz);
-    MGP_LAUNCH(k_gsrb_pipe<T, TY><<<grid, dim3(kPX, TY), smem, s>>>(L, xin, xout, b, kz));
+    dim3 grid(L.nx / kPX, L.ny / kPY, (L.nz + kz - 1) / kz);
+    MGP_LAUNCH(k_gsrb_pipe<T><<<grid, kPT, smem, s>>>(L, xin, xout, b, kz));
 }
 
 template bool cell_gsrb_fused_ok<float>(int, const CellLevel<float>&);

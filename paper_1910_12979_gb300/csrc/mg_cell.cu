@@ -221,6 +221,31 @@ __global__ void k_resid_restrict(CellLevel<T> F, const T* __restrict__ x, const 
     bc[t] = s * (T(1) / T(1 << DIM));
 }
 
+// 3-D residual + restriction with one thread per fine cell: a (32, 2, 2) block
+// covers the 2 x 2 x 2 children of 16 coarse cells; the residuals are summed
+// over x by a shuffle and over y and z through shared memory, in the fixed order
+// (x pair, then y, then z).  Used when nx % 32 == 0 and ny, nz are even.
+template <typename T>
+__global__ void __launch_bounds__(128) k_resid_restrict_t(CellLevel<T> F, const T* __restrict__ x,
+                                                          const T* __restrict__ b, T* __restrict__ bc)
+{
+    __shared__ T sh[2][2][16];
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 2 + threadIdx.y, k = blockIdx.z * 2 + threadIdx.z;
+    const size_t id = ((size_t)k * F.ny + j) * F.nx + i;
+    T off, dg;
+    cell_row<3>(F, i, j, k, GlobalPhi<T>{x, F.nx, F.ny}, off, dg);
+    T r = b[id] - (off - dg * x[id]);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    if ((threadIdx.x & 1) == 0) sh[threadIdx.z][threadIdx.y][threadIdx.x >> 1] = r;
+    __syncthreads();
+    if (threadIdx.y == 0 && threadIdx.z == 0 && (threadIdx.x & 1) == 0) {
+        const int q = threadIdx.x >> 1;
+        const T s2 = (sh[0][0][q] + sh[0][1][q]) + (sh[1][0][q] + sh[1][1][q]);
+        const int cnx = F.nx / 2, cny = F.ny / 2;
+        bc[((size_t)blockIdx.z * cny + blockIdx.y) * cnx + (i >> 1)] = s2 * T(0.125);
+    }
+}
+
 // coarse value seen from fine cell index i along one axis (linear interpolation):
 // parent P = i/2 with weight 3/4, the neighbour Q on the fine cell's side with 1/4;
 // beyond a boundary the neighbour is the periodic image, the mirror (Neumann) or
@@ -477,6 +502,10 @@ void cell_gsrb(int dim, const CellLevel<T>& L, T* x, const T* b, int color, cuda
 template <typename T>
 void cell_resid_restrict(int dim, const CellLevel<T>& F, const T* x, const T* b, T* bc, cudaStream_t s)
 {
+    if (dim == 3 && F.nx % 32 == 0 && F.ny % 2 == 0 && F.nz % 2 == 0) {
+        MGP_LAUNCH(k_resid_restrict_t<T><<<dim3(F.nx / 32, F.ny / 2, F.nz / 2), dim3(32, 2, 2), 0, s>>>(F, x, b, bc));
+        return;
+    }
     const int cnx = F.nx / 2, cny = F.ny / 2, cnz = dim == 3 ? F.nz / 2 : 1;
     long long n = (long long)cnx * cny * cnz;
     if (dim == 2) MGP_LAUNCH(k_resid_restrict<2, T><<<nb(n), kThreads, 0, s>>>(F, x, b, bc, cnx, cny, cnz));

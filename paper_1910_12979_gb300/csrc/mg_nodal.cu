@@ -233,101 +233,148 @@ __global__ void k_node_prolong(NodeLevel<T> F, NodeLevel<T> C, T* __restrict__ x
 // ------------------------------------------------------ tiled node sweeps
 //
 // The Jacobi sweep and the residual of k_jacobi / k_node_resid, one CTA per
-// 32 x 8 tile of node columns marching through a chunk of z-planes.  Shared
-// memory holds a ring of three phi planes with a 1-node halo and a ring of two
-// sigma planes (the cells around the tile's nodes, 0 outside the domain), so
-// phi, sigma and b are read and the result written once per node.  The cell
-// loop visits the cells in node_row's order; a missing cell adds 0 * (...),
-// which leaves both sums unchanged.  3-D only.
-constexpr int kNTX = 32, kNTY = 8;
+// 32 x 8 tile of node columns marching through a chunk of z-planes.  A 4-slot
+// shared-memory ring receives, two planes ahead of use and by cp.async, the
+// phi plane with a 1-node halo, the sigma plane of the cells around the tile's
+// nodes (0 outside the domain), b and (FP64) the inverse diagonal, so phi,
+// sigma and b are read and the result written once per node while the HBM
+// latency of later planes overlaps the arithmetic.  The cell loop visits the
+// cells in node_row's order; a missing cell adds 0 * (...), which leaves both
+// sums unchanged: the results equal k_jacobi's / k_node_resid's.  3-D only.
+constexpr int kNTX = 32, kNTY = 8, kNSlots = 4;
 
 template <typename T>
-struct NodeTileShared {
-    T xs[3][kNTY + 2][kNTX + 2];
-    T ss[2][kNTY + 1][kNTX + 1];
+struct NodePipeSlot {
+    T xs[kNTY + 2][kNTX + 2];   // phi, nodes x0-1 .. x0+32, y0-1 .. y0+8
+    T ss[kNTY + 1][kNTX + 1];   // sigma of cells x0-1 .. x0+31, y0-1 .. y0+7 (cell plane p)
+    T bb[kNTY][kNTX];           // b of the tile
+    T iv[kNTY][kNTX];           // 1/diagonal (FP64 levels)
 };
+
+__device__ __forceinline__ void cp_async_commit_n() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ncp_async(void* smem, const void* gmem, bool valid, int bytes)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? bytes : 0;
+    if (bytes == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+}
+
+__device__ __forceinline__ int npos(int g, int n, bool periodic)
+{
+    if (g >= 0 && g < n) return g;
+    if (!periodic) return -1;
+    return g < 0 ? g + n : g - n;
+}
 
 template <typename T, bool RESID>
 __global__ void __launch_bounds__(kNTX * kNTY)
 k_node_tiled(NodeLevel<T> L, const T* __restrict__ x, T* __restrict__ out, const T* __restrict__ b, T omega, int kz)
 {
-    constexpr int TX = kNTX, TY = kNTY;
-    __shared__ NodeTileShared<T> sh;
+    constexpr int TX = kNTX, TY = kNTY, NT = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    NodePipeSlot<T>* slot = reinterpret_cast<NodePipeSlot<T>*>(smem_raw);
     const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * kz, z1 = min(z0 + kz, Nz);
     const int tid = threadIdx.y * TX + threadIdx.x;
     const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
+    const bool has_iv = !RESID && L.invd != nullptr;
+    const size_t nplane = (size_t)Nx * Ny, cplane = (size_t)nx * ny;
 
-    auto load_x = [&](int p) {  // node plane p, possibly -1 or Nz
-        int gz = p;
-        bool zok = true;
-        if (gz < 0 || gz >= Nz) { if (pz) gz = gz < 0 ? gz + Nz : gz - Nz; else zok = false; }
-        T(*dst)[TX + 2] = sh.xs[(p + 3) % 3];
-        for (int q = tid; q < (TX + 2) * (TY + 2); q += TX * TY) {
+    // plane-independent copy offsets (-1: outside the domain -> zero fill)
+    int ox[2], os[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int q = tid + e * NT;
+        ox[e] = -2;
+        if (q < (TX + 2) * (TY + 2)) {
             const int ly = q / (TX + 2), lx = q - ly * (TX + 2);
-            int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-            bool ok = zok;
-            if (gx < 0 || gx >= Nx) { if (px) gx = gx < 0 ? gx + Nx : gx - Nx; else ok = false; }
-            if (gy < 0 || gy >= Ny) { if (py) gy = gy < 0 ? gy + Ny : gy - Ny; else ok = false; }
-            if (gx >= Nx || gy >= Ny) ok = false;
-            dst[ly][lx] = ok ? x[((size_t)gz * Ny + gy) * Nx + gx] : T(0);
+            const int gx = npos(x0 - 1 + lx, Nx, px), gy = npos(y0 - 1 + ly, Ny, py);
+            ox[e] = (gx >= 0 && gy >= 0) ? gy * Nx + gx : -1;
         }
-    };
-    auto load_s = [&](int c) {  // cell plane c, possibly -1 or nz
-        int gz = c;
-        bool zok = true;
-        if (gz < 0 || gz >= nz) { if (pz) gz = gz < 0 ? gz + nz : gz - nz; else zok = false; }
-        T(*dst)[TX + 1] = sh.ss[(c + 2) & 1];
-        for (int q = tid; q < (TX + 1) * (TY + 1); q += TX * TY) {
+        os[e] = -2;
+        if (q < (TX + 1) * (TY + 1)) {
             const int ly = q / (TX + 1), lx = q - ly * (TX + 1);
-            int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-            bool ok = zok;
-            if (gx < 0 || gx >= nx) { if (px) gx = gx < 0 ? gx + nx : gx - nx; else ok = false; }
-            if (gy < 0 || gy >= ny) { if (py) gy = gy < 0 ? gy + ny : gy - ny; else ok = false; }
-            if (gx >= nx || gy >= ny) ok = false;
-            dst[ly][lx] = ok ? L.sigma[((size_t)gz * ny + gy) * nx + gx] : T(0);
+            const int gx = npos(x0 - 1 + lx, nx, px), gy = npos(y0 - 1 + ly, ny, py);
+            os[e] = (gx >= 0 && gy >= 0) ? gy * nx + gx : -1;
         }
+    }
+    const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+    const bool own = i < Nx && j < Ny;
+    const int ob = own ? j * Nx + i : 0;
+
+    // stage node plane p (phi, b, 1/diag) and cell plane p (sigma); p may be
+    // -1 or Nz (wrapped when z is periodic, else zero)
+    auto issue = [&](int p) {
+        if (p >= -1 && p <= Nz) {
+            NodePipeSlot<T>& S = slot[(p + kNSlots) % kNSlots];
+            int pn = p, pc = p;
+            bool nok = true, cok = true;
+            if (pn < 0 || pn >= Nz) { if (pz) pn = pn < 0 ? pn + Nz : pn - Nz; else nok = false; }
+            if (pc < 0 || pc >= nz) { if (pz) pc = pc < 0 ? pc + nz : pc - nz; else cok = false; }
+            const T* xp = x + (nok ? pn * nplane : 0);
+            const T* sp = L.sigma + (cok ? pc * cplane : 0);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int q = tid + e * NT;
+                if (ox[e] >= -1) ncp_async(&S.xs[0][0] + q, xp + (ox[e] < 0 ? 0 : ox[e]), nok && ox[e] >= 0, sizeof(T));
+                if (os[e] >= -1) ncp_async(&S.ss[0][0] + q, sp + (os[e] < 0 ? 0 : os[e]), cok && os[e] >= 0, sizeof(T));
+            }
+            const bool bok = own && p >= 0 && p < Nz;
+            ncp_async(&S.bb[threadIdx.y][threadIdx.x], b + (bok ? p * nplane + ob : 0), bok, sizeof(T));
+            if (has_iv)
+                ncp_async(&S.iv[threadIdx.y][threadIdx.x], L.invd + (bok ? p * nplane + ob : 0), bok, sizeof(T));
+        }
+        cp_async_commit_n();
     };
 
-    load_x(z0 - 1);
-    load_x(z0);
-    load_s(z0 - 1);
+    issue(z0 - 1);
+    issue(z0);
+    issue(z0 + 1);
+    issue(z0 + 2);
     const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-    const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
     for (int k = z0; k < z1; ++k) {
-        load_x(k + 1);
-        load_s(k);
+        cp_async_wait_n<1>();  // planes <= k + 1 have landed
         __syncthreads();
-        if (i < Nx && j < Ny) {
-            const size_t id = ((size_t)k * Ny + j) * Nx + i;
+        if (own) {
+            const size_t id = (size_t)k * nplane + ob;
             if (node_dirichlet(L, i, j, k, 3)) {
                 out[id] = T(0);
             } else {
-                const int sk = (k + 3) % 3;
+                const NodePipeSlot<T>& Sk = slot[(k + kNSlots) % kNSlots];
+                const NodePipeSlot<T>& Sm = slot[(k - 1 + kNSlots) % kNSlots];
+                const NodePipeSlot<T>& Sp = slot[(k + 1 + kNSlots) % kNSlots];
                 T acc = T(0), ssum = T(0);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1, sz = (c & 4) ? 1 : -1;
-                    const T sg = sh.ss[(sz > 0 ? k + 2 : k + 1) & 1][ly + (sy > 0 ? 0 : -1)][lx + (sx > 0 ? 0 : -1)];
-                    const int se = (k + sz + 3) % 3;
-                    const int a = lx + sx, bb = ly + sy;
-                    acc += sg * (sh.xs[sk][bb][a] + sh.xs[se][ly][a] + sh.xs[se][bb][lx] + sh.xs[se][bb][a]);
+                    const NodePipeSlot<T>& Sc = sz > 0 ? Sk : Sm;   // cell plane k or k-1
+                    const NodePipeSlot<T>& Se = sz > 0 ? Sp : Sm;   // node plane k+sz
+                    const T sg = Sc.ss[ly + (sy > 0 ? 0 : -1)][lx + (sx > 0 ? 0 : -1)];
+                    const int a = lx + sx, bb2 = ly + sy;
+                    acc += sg * (Sk.xs[bb2][a] + Se.xs[ly][a] + Se.xs[bb2][lx] + Se.xs[bb2][a]);
                     ssum += sg;
                 }
                 const T off = acc * (L.ih2 / T(12));
                 const T dg = -ssum * (L.ih2 / T(3));
-                const T xi = sh.xs[sk][ly][lx];
+                const T xi = Sk.xs[ly][lx];
+                const T bv = Sk.bb[threadIdx.y][threadIdx.x];
                 if (RESID) {
-                    out[id] = b[id] - (off + dg * xi);
+                    out[id] = bv - (off + dg * xi);
                 } else {
-                    const T inv = L.invd ? L.invd[id] : recip(dg);
-                    out[id] = xi + omega * (b[id] - (off + dg * xi)) * inv;
+                    const T inv = has_iv ? Sk.iv[threadIdx.y][threadIdx.x] : recip(dg);
+                    out[id] = xi + omega * (bv - (off + dg * xi)) * inv;
                 }
             }
         }
         __syncthreads();
+        issue(k + 3);
     }
+    cp_async_wait_n<0>();
 }
 
 // -------------------------------------------------------- FP64 residuals
@@ -605,13 +652,25 @@ static dim3 node_tiled_grid(const NodeLevel<T>& L, int& kz)
     return dim3((unsigned)tx, (unsigned)ty, (unsigned)((L.Nz + kz - 1) / kz));
 }
 
+template <typename T, bool RESID>
+static void launch_node_tiled(const NodeLevel<T>& L, const T* x, T* out, const T* b, T omega, cudaStream_t s)
+{
+    const size_t smem = kNSlots * sizeof(NodePipeSlot<T>);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_node_tiled<T, RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    int kz;
+    const dim3 g = node_tiled_grid(L, kz);
+    MGP_LAUNCH(k_node_tiled<T, RESID><<<g, dim3(kNTX, kNTY), smem, s>>>(L, x, out, b, omega, kz));
+}
+
 template <typename T>
 void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s)
 {
     if (node_tiled_ok(dim, L, tiled)) {
-        int kz;
-        const dim3 g = node_tiled_grid(L, kz);
-        MGP_LAUNCH(k_node_tiled<T, false><<<g, dim3(kNTX, kNTY), 0, s>>>(L, x, xo, b, omega, kz));
+        launch_node_tiled<T, false>(L, x, xo, b, omega, s);
     } else if (dim == 2) {
         MGP_LAUNCH(k_jacobi<2, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, xo, b, omega));
     } else {
@@ -623,9 +682,7 @@ template <typename T>
 void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bool tiled, cudaStream_t s)
 {
     if (node_tiled_ok(dim, L, tiled)) {
-        int kz;
-        const dim3 g = node_tiled_grid(L, kz);
-        MGP_LAUNCH(k_node_tiled<T, true><<<g, dim3(kNTX, kNTY), 0, s>>>(L, x, r, b, T(0), kz));
+        launch_node_tiled<T, true>(L, x, r, b, T(0), s);
     } else if (dim == 2) {
         MGP_LAUNCH(k_node_resid<2, T><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, b, r));
     } else {

@@ -50,9 +50,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="stratified", choices=["stratified", "batch", "serve"],
-                    help="stratified: the default 256^3 MAC + nodal step; batch: 64 uneven MAC solves in one "
-                         "graph launch; serve: Poisson stream of polytrope-star projections (p50/p99)")
+    ap.add_argument("--workload", default="stratified", choices=["stratified", "batch", "serve", "config1", "config2"],
+                    help="stratified: the default 256^3 MAC + nodal mixed step; batch: 64 uneven MAC solves in "
+                         "one graph launch; serve: Poisson stream of polytrope-star projections (p50/p99); "
+                         "config1: 2-D 64^2 manufactured solve; config2: 128^3 FP64 MAC + nodal step")
+    ap.add_argument("--parity", action="store_true",
+                    help="also solve the MAC system of the workload with the CPU oracle and report rel-L2 of phi")
     ap.add_argument("--budget-gb", type=float, default=24.0, help="serve: device-memory budget of the slots")
     ap.add_argument("--inflight", type=int, default=8, help="serve: concurrent solves")
     ap.add_argument("--serve-count", type=int, default=256, help="serve: requests per arrival rate")
@@ -177,10 +180,15 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def source_hash():
+# the source files whose change invalidates a kernel class's ncu counters
+PROF_SOURCES = {"cell_smooth_fine": ["mg_sweep.cu"], "node_smooth_fine": ["mg_nodal.cu"],
+                "cell_restrict_fine": ["mg_cell.cu"], "cell_resid64": ["mg_cell.cu"], "node_resid64": ["mg_nodal.cu"]}
+
+
+def source_hash(kernel_class):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1910_12979_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(PROF_SOURCES.get(kernel_class, []) + ["mg_device.cuh", "mg_internal.cuh"]):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -188,7 +196,7 @@ def source_hash():
 def ncu_traffic(kernel_class):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel sources; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None
     try:
@@ -196,7 +204,7 @@ def ncu_traffic(kernel_class):
     except Exception:
         return None
     e = d.get(kernel_class)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(kernel_class):
         return None
     return e.get("bytes_per_launch")
 
@@ -325,6 +333,119 @@ def run_serve(args, dev, rank, world, dist):
     return out
 
 
+def _timed_solves(fn, K, W, stream):
+    import torch
+    for _ in range(W):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_config1(args, dev):
+    """2-D 64^2 manufactured solve, FP64 and mixed, against the oracle and the exact phi."""
+    import numpy as np
+    import torch
+
+    import inputs as I
+    import oracle as O
+    from paper_1910_12979_gb300 import ProjectionSolver
+
+    p = I.manufactured_2d(64)
+    g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+    ref, _ = O.mac_solve_mg(g, O.mac_faces(g, p["sigma"]), p["f"])
+    ref = ref - ref.mean()
+    stream = torch.cuda.Stream(device=dev)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        with torch.cuda.stream(stream):
+            s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec=prec, stream=stream)
+            f = T(p["f"])
+            phi = torch.zeros_like(f)
+
+        def solve():
+            with torch.cuda.stream(stream):
+                phi.zero_()
+                return s.solve(f, phi, tol=1e-12)
+        ms, st = _timed_solves(solve, args.steps, args.warmup, stream)
+        ph = phi.cpu().numpy()
+        ph = ph - ph.mean()
+        ex = p["phi_exact"] - p["phi_exact"].mean()
+        res[prec] = {"solves_per_s": args.steps / (ms / 1e3), "iters": st["iters"], "rel_resid": st["rel_resid"],
+                     "rel_l2_vs_oracle": float(np.linalg.norm(ph - ref) / np.linalg.norm(ref)),
+                     "rms_error_vs_exact_phi": float(np.sqrt(np.mean((ph - ex) ** 2)))}
+    return {"metric": "2-D 64^2 manufactured MAC-type solve, solves/s", "value": res["fp64"]["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / res["fp64"]["solves_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2-D 64x64 stratified rho = exp(-y/0.25), beta0 = rho^(3/5), manufactured "
+                                   "phi = cos(2 pi x) cos(2 pi y); periodic x, Neumann y; tol 1e-12"},
+            "fp64": res["fp64"], "mixed": res["mixed"]}
+
+
+def run_config2(args, dev):
+    """128^3 stratified MAC + nodal step in FP64 (and the MAC rel-L2 against the oracle)."""
+    import numpy as np
+    import torch
+
+    import inputs as I
+    from paper_1910_12979_gb300 import ProjectionSolver
+
+    p = I.stratified(128, seed=2, contrast=1e3)
+    stream = torch.cuda.Stream(device=dev)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    with torch.cuda.stream(stream):
+        sigma, beta0, S = T(p["sigma"]), T(p["beta0"]), T(p["S"])
+        b0f = [T(b) for b in p["beta0_face"]]
+        U0m, U0c = [T(u) for u in p["U_mac"]], [T(u) for u in p["U_cell"]]
+        Um, Uc = [u.clone() for u in U0m], [u.clone() for u in U0c]
+        out = {}
+        for prec in ("fp64", "mixed"):
+            mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream)
+            nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream)
+            phim = torch.zeros_like(sigma)
+            phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)
+
+            def step():
+                with torch.cuda.stream(stream):
+                    mac.update_coeff(sigma)
+                    nod.update_coeff(sigma)
+                    for a, b in zip(Um + Uc, U0m + U0c):
+                        a.copy_(b)
+                    phim.zero_()
+                    phin.zero_()
+                    a = mac.project(Um, beta0, S, beta0_face=b0f, phi=phim, tol=args.tol, allow_not_converged=True)
+                    b = nod.project(Uc, beta0, S, phi=phin, tol=args.tol, allow_not_converged=True)
+                    return a, b
+            ms, (a, b) = _timed_solves(step, args.steps, args.warmup, stream)
+            out[prec] = {"solves_per_s": 2 * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                         "mac": {k: a[k] for k in ("iters", "rel_resid", "rel_constraint")},
+                         "nodal": {k: b[k] for k in ("iters", "rel_resid", "rel_constraint")},
+                         "phi_mac": phim.cpu().numpy()}
+    line = {"metric": "128^3 MAC + nodal projection step, FP64 plain multigrid, solves/s",
+            "value": out["fp64"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "stratified atmosphere 128^3 (contrast 1e3, seed 2), MAC + nodal, tol %g" % args.tol},
+            "mixed_vs_fp64": out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]}
+    if args.parity:
+        import oracle as O
+        g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+        ref = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-13)
+    for prec in ("fp64", "mixed"):
+        ph = out[prec].pop("phi_mac")
+        if args.parity:
+            out[prec]["mac"]["rel_l2_vs_oracle"] = float(np.linalg.norm(ph - ref["phi"]) / np.linalg.norm(ref["phi"]))
+        line[prec] = out[prec]
+    return line
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -355,8 +476,14 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     if args.workload != "stratified":
-        line = run_batch(args, dev, world, dist) if args.workload == "batch" else run_serve(args, dev, rank, world,
-                                                                                              dist)
+        if args.workload == "batch":
+            line = run_batch(args, dev, world, dist)
+        elif args.workload == "serve":
+            line = run_serve(args, dev, rank, world, dist)
+        elif args.workload == "config1":
+            line = run_config1(args, dev)
+        else:
+            line = run_config2(args, dev)
         if rank == 0:
             print(json.dumps(line), flush=True)
         if dist is not None:
@@ -440,27 +567,44 @@ def main():
     value = 2.0 * args.steps * world / (ms / 1e3)
     st_mac, st_nod = dict(stats["mac"]), dict(stats["nodal"])
 
-    # roofline of the dominant (largest total time) instrumented kernel class
+    # roofline of the dominant (largest total time) instrumented kernel class;
+    # the FP64 residuals are bound by the FP64 pipe, the FP32 sweeps by HBM
     hbm, bf16, src = peaks()
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    dk = prof[dom]
-    per_launch_ms = dk["ms"] / max(dk["launches"], 1)
-    per_launch_bytes = dk["bytes"] / max(dk["launches"], 1)
-    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": ncu_traffic(dom), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
-            "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": per_launch_ms,
-            "launches": dk["launches"],
-            "share_of_step": dk["ms"] / ms if ms > 0 else None,
-            "all": {k: {"avg_ms": v["ms"] / max(v["launches"], 1), "launches": v["launches"],
-                        "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
-                    for k, v in prof.items()}}
+    fp64_peak = 1.25  # TFLOP/s: nominal GB300 FP64 rate (no measured FP64 peak is available)
+
+    def roof(name):
+        k = prof[name]
+        n = max(k["launches"], 1)
+        t = k["ms"] / n * 1e-3
+        if name in N.PROF_FP64_BOUND:
+            ach = k["flops"] / n / t / 1e12
+            return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak, "traffic": ncu_traffic(name),
+                    "peak_source": "nominal FP64 rate of the GB300 (1.25 TFLOP/s), not measured",
+                    "algorithmic_flops_per_launch": k["flops"] / n, "algorithmic_bytes_per_launch": k["bytes"] / n,
+                    "hbm_GBps": k["bytes"] / n / t / 1e9, "avg_launch_ms": t * 1e3, "launches": k["launches"],
+                    "share_of_step": k["ms"] / ms if ms > 0 else None}
+        ach = k["bytes"] / n / t / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": ncu_traffic(name), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": k["bytes"] / n, "avg_launch_ms": t * 1e3,
+                "launches": k["launches"], "share_of_step": k["ms"] / ms if ms > 0 else None}
+
+    live = [k for k in prof if prof[k]["launches"] > 0]
+    dom = max(live, key=lambda k: prof[k]["ms"])
+    roof_line = roof(dom)
+    hbm_classes = [k for k in live if k not in N.PROF_FP64_BOUND]
+    roof_line["hbm_kernel"] = roof(max(hbm_classes, key=lambda k: prof[k]["ms"])) if hbm_classes else None
+    roof_line["all"] = {k: roof(k) for k in live}
+    for v in roof_line["all"].values():
+        v.pop("traffic", None)
+        v.pop("peak_source", None)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": dict(workload_config(n, args.tol), parallelism=f"independent solves x{world}"),
-            "clocks": clocks, "gpu_launches": launches, "roofline": roof,
+            "clocks": clocks, "gpu_launches": launches, "roofline": roof_line,
             "solver": {"mac": {k: st_mac[k] for k in ("iters", "rel_resid", "rel_constraint")},
                        "nodal": {k: st_nod[k] for k in ("iters", "rel_resid", "rel_constraint")}}}
 
@@ -528,6 +672,20 @@ def main():
             mse = float(t.item())
         line["e2e"] = {"value": 2.0 * Ke * world / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": mse / Ke}
+
+    if args.parity and rank == 0:
+        import oracle as O
+        g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+        ref = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-13)
+        mixed[0].update_coeff(sigma)
+        for a, b in zip(Um, U0m):
+            a.copy_(b)
+        phim = mixed[2]
+        phim.zero_()
+        mixed[0].project(Um, beta0, S, beta0_face=b0f, phi=phim, tol=args.tol, allow_not_converged=True)
+        ph = phim.cpu().numpy()
+        line["parity"] = {"mac_phi_rel_l2_vs_oracle": float(np.linalg.norm(ph - ref["phi"]) / np.linalg.norm(ref["phi"])),
+                          "oracle_relres": ref["relres"], "tol": args.tol}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n)

@@ -198,6 +198,26 @@ mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* beta0, co
  * handle's stream. */
 mg_status mg_rhs(mg_handle* h, const double* const U[3], const mg_beta0* beta0, const double* S, double* f);
 
+/* Base state on the device (Eq. 5).  beta0 on a radial grid from tabulated
+ * p0 > 0 (device, nr values, increasing radius), Gamma1 per point (device, or
+ * NULL to use gamma1_const) and rho0 at the first point:
+ *   beta0_0 = rho0_base,
+ *   beta0_{k+1} = rho0_base exp( sum_{m<=k} (1/2)(1/Gamma1_m + 1/Gamma1_{m+1}) (ln p0_{m+1} - ln p0_m) ),
+ * the trapezoid rule for the integral of (1/Gamma1) d(ln p0) = dp0/dr / (Gamma1 p0) dr of
+ * Eq. 5 (exact when Gamma1 is constant).  beta0: device, nr values.  Asynchronous on stream. */
+mg_status mg_base_state_beta0(const double* p0, const double* gamma1, double gamma1_const, double rho0_base, int nr,
+                              double* beta0, void* stream);
+
+/* Map radial base-state tables (beta0_r, rho0_r: device, nr values at r0 + k dr)
+ * onto the grid by linear interpolation (clamped to the end values): every cell
+ * or face centre gets r = its distance to center (spherical != 0) or its height
+ * (the last axis; center ignored).  Writes sigma = beta0/rho0 and beta0 at cell
+ * centres and beta0 at the face centres of each axis (device arrays in the
+ * layouts above; any output may be NULL).  Asynchronous on stream. */
+mg_status mg_base_state_map(const mg_geometry* geom, int spherical, const double center[3], double r0, double dr,
+                            int nr, const double* beta0_r, const double* rho0_r, double* sigma, double* beta0_cell,
+                            double* const beta0_face[3], void* stream);
+
 /* Solve count independent problems (any mix of grids, precisions and
  * locations; each handle at most once) as ONE CUDA graph launch on the first
  * handle's stream: every solve is a branch of the graph with its own
@@ -224,22 +244,28 @@ const char* mg_last_error(void);
 
 /* Live per-kernel timing (diagnostics, used by the benchmark's roofline).
  * mg_prof_enable(1) clears the record and starts bracketing every launch of
- * the kernels below with a pair of CUDA events on the launching stream;
- * mg_prof_enable(0) stops.  mg_prof_query (call after the stream has been
- * synchronised) returns, for one kernel class, the summed event time, the
- * launch count and the summed ALGORITHMIC bytes of those launches (the words
- * the method must move: see each class).  Returns MG_ERR_INVALID_ARG for an
- * unknown class.  Recording stops silently after 65536 launches. */
+ * the kernels below with a pair of CUDA events on the launching stream (solves
+ * then use the host-driven loop: a graph replay cannot be bracketed per
+ * launch); mg_prof_enable(0) stops.  mg_prof_query (call after the stream has
+ * been synchronised) returns, for one kernel class, the summed event time, the
+ * launch count and the summed ALGORITHMIC bytes and FP64 flops of those
+ * launches (what the method must move and compute, see each class).  Returns
+ * MG_ERR_INVALID_ARG for an unknown class.  Recording stops silently after
+ * 65536 launches. */
 typedef enum {
     MG_PROF_CELL_SMOOTH_FINE = 0, /* one fused red-black sweep on the finest cell level
                                      (phi, f, sigma read, phi written: 4 words/cell), or one
                                      colour pass where the level does not tile (2 words/cell) */
-    MG_PROF_RESID64 = 1,          /* FP64 fine residual (+ FP32 copy in mixed mode):
-                                     phi, f, sigma in FP64 (+ r in FP32) per unknown */
+    MG_PROF_RESID64 = 1,          /* FP64 fine residual of a cell system (+ FP32 copy in mixed
+                                     mode): phi, f, sigma in FP64 (+ r in FP32) per cell;
+                                     17 FP64 flops per cell */
     MG_PROF_NODE_SMOOTH_FINE = 2, /* one Jacobi sweep on the finest nodal level: phi, f, sigma read, phi written */
     MG_PROF_CELL_RESTRICT_FINE = 3, /* fused residual + restriction on the finest cell level:
                                        phi, f, sigma read, 1/2^dim word written per cell */
-    MG_PROF_COUNT = 4
+    MG_PROF_NODE_RESID64 = 4,     /* FP64 fine residual of a nodal system (+ FP32 copy):
+                                     phi, f, sigma in FP64 (+ r in FP32) per node; 45 FP64
+                                     flops per node (27-point operator assembled from 8 sigma) */
+    MG_PROF_COUNT = 5
 } mg_prof_kernel;
 
 /* Allocation-free check of the MAC constraint.  The paper has no counterpart:
@@ -271,7 +297,7 @@ mg_status mg_mac_constraint_noalloc(const mg_geometry* geom, const double* const
 void mg_prof_enable(int on);
 /* Total number of CUDA kernels this library has launched in the process. */
 long long mg_launch_count(void);
-mg_status mg_prof_query(int kernel, double* total_ms, int* launches, double* bytes);
+mg_status mg_prof_query(int kernel, double* total_ms, int* launches, double* bytes, double* flops);
 
 #ifdef __cplusplus
 }

@@ -65,7 +65,8 @@ def _L():
         for name in ("orc_mac_faces", "orc_mac_apply", "orc_mac_div", "orc_mac_rhs", "orc_mac_grad_update",
                      "orc_mac_solve_dense", "orc_mac_solve_mg", "orc_mac_project", "orc_nodal_apply",
                      "orc_nodal_div", "orc_nodal_lump", "orc_nodal_grad", "orc_nodal_rhs",
-                     "orc_nodal_solve_dense", "orc_nodal_solve_mg", "orc_nodal_project"):
+                     "orc_nodal_solve_dense", "orc_nodal_solve_mg", "orc_nodal_project", "orc_beta0_eq5",
+                     "orc_map_radial"):
             getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -332,3 +333,27 @@ def nodal_project(g: Grid, sigma, beta0, U, S, tol=1e-14, dense=False):
         raise RuntimeError(f"oracle nodal projection did not converge (relres {st.relres:.3e})")
     return {"phi": phi, "U": U, "iters": st.iters, "relres": st.relres, "constraint": st.constraint,
             "src_norm": st.src_norm, "rhs_norm": st.rhs_norm}
+
+
+# ------------------------------------------------------------- base state
+
+def beta0_eq5(p0, rho00, gamma1=None, g1=5.0 / 3.0):
+    """beta0 of Eq. 5 on a radial grid from tabulated p0 (and optional Gamma1 per point)."""
+    p0 = _f64(p0)
+    out = np.zeros_like(p0)
+    ga = _f64(gamma1) if gamma1 is not None else None
+    _L().orc_beta0_eq5(_p(p0), _p(ga) if ga is not None else None, ctypes.c_double(g1), ctypes.c_double(rho00),
+                       ctypes.c_int(len(p0)), _p(out))
+    return out
+
+
+def map_radial(g: Grid, spherical, center, r0, dr, beta0_r, rho0_r):
+    """(sigma, beta0_cell, beta0_face list) from uniform radial tables."""
+    b, rho = _f64(beta0_r), _f64(rho0_r)
+    sigma, bc = np.zeros(g.cell_shape), np.zeros(g.cell_shape)
+    bf = [np.zeros(g.face_shape(d)) for d in range(g.dim)]
+    c = (ctypes.c_double * 3)(*(list(center) + [0.0] * (3 - len(center))))
+    _L().orc_map_radial(ctypes.byref(g.c()), ctypes.c_int(1 if spherical else 0), c, ctypes.c_double(r0),
+                        ctypes.c_double(dr), ctypes.c_int(len(b)), _p(b), _p(rho), _p(sigma), _p(bc),
+                        _arr3(_ptr3(bf)))
+    return sigma, bc, bf

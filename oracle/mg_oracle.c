@@ -1299,3 +1299,77 @@ int orc_nodal_project(const orc_grid* g, const double* sigma, const double* beta
     free(f);
     return rc;
 }
+
+/* ======================================================================== */
+/* Base state (Eq. 5) and its mapping onto the grid                          */
+/* ======================================================================== */
+
+/* beta0 of Eq. 5 on a radial grid:
+ *   beta0(r) = rho0(r_0) exp( int (1 / (Gamma1 p0)) dp0 ),
+ * written as the integral of (1/Gamma1) d(ln p0) and evaluated by the
+ * trapezoid rule in ln p0: the increment between r_k and r_{k+1} is
+ *   (1/2)(1/Gamma1_k + 1/Gamma1_{k+1}) (ln p0_{k+1} - ln p0_k).
+ * gamma1 may be NULL (then the constant g1 is used). */
+int orc_beta0_eq5(const double* p0, const double* gamma1, double g1, double rho00, int nr, double* beta0)
+{
+    double acc = 0.0;
+    beta0[0] = rho00;
+    for (int k = 0; k + 1 < nr; ++k) {
+        double ga = gamma1 ? gamma1[k] : g1, gb = gamma1 ? gamma1[k + 1] : g1;
+        acc += 0.5 * (1.0 / ga + 1.0 / gb) * (log(p0[k + 1]) - log(p0[k]));
+        beta0[k + 1] = rho00 * exp(acc);
+    }
+    return 0;
+}
+
+/* linear interpolation in a uniform radial table f(r0 + k dr), clamped to the ends */
+static double radial_interp(const double* f, int nr, double r0, double dr, double r)
+{
+    double s = (r - r0) / dr;
+    if (s <= 0.0) return f[0];
+    if (s >= (double)(nr - 1)) return f[nr - 1];
+    int k = (int)floor(s);
+    double w = s - k;
+    return (1.0 - w) * f[k] + w * f[k + 1];
+}
+
+/* radius of a point: distance to the centre (spherical) or its height z
+ * (plane-parallel: the last axis) */
+static double point_radius(int dim, int spherical, const double* c, double x, double y, double z)
+{
+    if (!spherical) return dim == 3 ? z : y;
+    double dx = x - c[0], dy = y - c[1], dz = dim == 3 ? z - c[2] : 0.0;
+    return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+/* sigma = beta0/rho0 and beta0 at cell centres, beta0 at face centres, from
+ * uniform radial tables of beta0 and rho0.  Output pointers may be NULL. */
+int orc_map_radial(const orc_grid* g, int spherical, const double* center, double r0, double dr, int nr,
+                   const double* beta0_r, const double* rho0_r, double* sigma, double* beta0_cell,
+                   double* const beta0_face[3])
+{
+    int c[3];
+    for (c[2] = 0; c[2] < g->n[2]; ++c[2])
+        for (c[1] = 0; c[1] < g->n[1]; ++c[1])
+            for (c[0] = 0; c[0] < g->n[0]; ++c[0]) {
+                double x = (c[0] + 0.5) * g->h[0], y = (c[1] + 0.5) * g->h[1], z = (c[2] + 0.5) * g->h[2];
+                double r = point_radius(g->dim, spherical, center, x, y, z);
+                double b = radial_interp(beta0_r, nr, r0, dr, r), rho = radial_interp(rho0_r, nr, r0, dr, r);
+                long i = cell_index(g, c);
+                if (sigma) sigma[i] = b / rho;
+                if (beta0_cell) beta0_cell[i] = b;
+            }
+    for (int d = 0; d < g->dim; ++d) {
+        if (!beta0_face || !beta0_face[d]) continue;
+        int f[3];
+        for (f[2] = 0; f[2] < g->n[2] + (d == 2); ++f[2])
+            for (f[1] = 0; f[1] < g->n[1] + (d == 1); ++f[1])
+                for (f[0] = 0; f[0] < g->n[0] + (d == 0); ++f[0]) {
+                    double p[3];
+                    for (int e = 0; e < 3; ++e) p[e] = (f[e] + (e == d ? 0.0 : 0.5)) * g->h[e];
+                    double r = point_radius(g->dim, spherical, center, p[0], p[1], p[2]);
+                    beta0_face[d][face_index(g, d, f)] = radial_interp(beta0_r, nr, r0, dr, r);
+                }
+    }
+    return 0;
+}

@@ -23,32 +23,32 @@ __device__ __forceinline__ void cell_row(const CellLevel<T>& L, int i, int j, in
     {
         const size_t r = ((size_t)k * ny + j) * (nx + 1) + i;
         const T bl = L.bx[r], bh = L.bx[r + 1];
-        if (i > 0) { off += bl * phi(i - 1, j, k); dg += bl; }
-        else if (L.bc.lo[0] == BCP) { off += bl * phi(nx - 1, j, k); dg += bl; }
+        if (i > 0) { off = fmadd(bl, phi(i - 1, j, k), off); dg += bl; }
+        else if (L.bc.lo[0] == BCP) { off = fmadd(bl, phi(nx - 1, j, k), off); dg += bl; }
         else if (L.bc.lo[0] == BCD) { dg += T(2) * bl; }
-        if (i < nx - 1) { off += bh * phi(i + 1, j, k); dg += bh; }
-        else if (L.bc.hi[0] == BCP) { off += bh * phi(0, j, k); dg += bh; }
+        if (i < nx - 1) { off = fmadd(bh, phi(i + 1, j, k), off); dg += bh; }
+        else if (L.bc.hi[0] == BCP) { off = fmadd(bh, phi(0, j, k), off); dg += bh; }
         else if (L.bc.hi[0] == BCD) { dg += T(2) * bh; }
     }
     {
         const size_t r = ((size_t)k * (ny + 1) + j) * nx + i;
         const T bl = L.by[r], bh = L.by[r + nx];
-        if (j > 0) { off += bl * phi(i, j - 1, k); dg += bl; }
-        else if (L.bc.lo[1] == BCP) { off += bl * phi(i, ny - 1, k); dg += bl; }
+        if (j > 0) { off = fmadd(bl, phi(i, j - 1, k), off); dg += bl; }
+        else if (L.bc.lo[1] == BCP) { off = fmadd(bl, phi(i, ny - 1, k), off); dg += bl; }
         else if (L.bc.lo[1] == BCD) { dg += T(2) * bl; }
-        if (j < ny - 1) { off += bh * phi(i, j + 1, k); dg += bh; }
-        else if (L.bc.hi[1] == BCP) { off += bh * phi(i, 0, k); dg += bh; }
+        if (j < ny - 1) { off = fmadd(bh, phi(i, j + 1, k), off); dg += bh; }
+        else if (L.bc.hi[1] == BCP) { off = fmadd(bh, phi(i, 0, k), off); dg += bh; }
         else if (L.bc.hi[1] == BCD) { dg += T(2) * bh; }
     }
     if (DIM == 3) {
         const size_t r = ((size_t)k * ny + j) * nx + i;
         const size_t pl = (size_t)nx * ny;
         const T bl = L.bz[r], bh = L.bz[r + pl];
-        if (k > 0) { off += bl * phi(i, j, k - 1); dg += bl; }
-        else if (L.bc.lo[2] == BCP) { off += bl * phi(i, j, nz - 1); dg += bl; }
+        if (k > 0) { off = fmadd(bl, phi(i, j, k - 1), off); dg += bl; }
+        else if (L.bc.lo[2] == BCP) { off = fmadd(bl, phi(i, j, nz - 1), off); dg += bl; }
         else if (L.bc.lo[2] == BCD) { dg += T(2) * bl; }
-        if (k < nz - 1) { off += bh * phi(i, j, k + 1); dg += bh; }
-        else if (L.bc.hi[2] == BCP) { off += bh * phi(i, j, 0); dg += bh; }
+        if (k < nz - 1) { off = fmadd(bh, phi(i, j, k + 1), off); dg += bh; }
+        else if (L.bc.hi[2] == BCP) { off = fmadd(bh, phi(i, j, 0), off); dg += bh; }
         else if (L.bc.hi[2] == BCD) { dg += T(2) * bh; }
     }
 }

@@ -183,58 +183,75 @@ __global__ void __launch_bounds__(kGJThreads) k_gauss_jordan(double* __restrict_
 }
 
 // Same elimination with the augmented matrix resident in shared memory
-// (n <= kGJSmemMax): one global read of A, one global write of Minv.
+// (n <= kGJSmemMax): one global read of A, one global write of Minv.  Per
+// pivot column k: warp 0 finds the pivot (largest |entry|, smallest row on
+// ties); then the pivot row is swapped in, scaled and kept in prow; then every
+// other row is updated over the columns right of k only.  Columns left of k
+// are never read again (the inverse is the right half), so they are neither
+// updated nor cleared.  Three barriers per column.
 constexpr int kGJSmemMax = 112;
 
 __global__ void __launch_bounds__(kGJThreads) k_gauss_jordan_smem(const double* __restrict__ A, int n, int N,
                                                                  double* __restrict__ Minv, int* __restrict__ info)
 {
     extern __shared__ double W[];  // n x 2n
+    __shared__ double prow[2 * kGJSmemMax];
+    __shared__ int piv;
+    __shared__ double pval;
     const int ld = 2 * n;
-    for (int t = threadIdx.x; t < n * ld; t += blockDim.x) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < n * ld; t += nt) {
         const int r = t / ld, c = t - r * ld;
         W[t] = c < n ? A[(size_t)r * ld + c] : ((c - n) == r ? 1.0 : 0.0);
     }
-    __shared__ int piv;
-    __shared__ double pval;
-    if (threadIdx.x == 0) *info = 0;
+    if (tid == 0) *info = 0;
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        if (threadIdx.x == 0) {  // n <= 112: a serial pivot search is cheaper than a reduction
+        if (warp == 0) {
             double b = -1.0;
             int p = k;
-            for (int r = k; r < n; ++r) {
+            for (int r = k + lane; r < n; r += 32) {
                 const double v = fabs(W[r * ld + k]);
                 if (v > b) { b = v; p = r; }
             }
-            piv = p;
-            pval = W[p * ld + k];
-            if (b <= 0.0) *info = k + 1;
-        }
-        __syncthreads();
-        if (pval == 0.0) return;
-        const int p = piv;
-        if (p != k)
-            for (int c = threadIdx.x; c < ld; c += blockDim.x) {
-                const double tmp = W[k * ld + c];
-                W[k * ld + c] = W[p * ld + c];
-                W[p * ld + c] = tmp;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, b, o);
+                const int op = __shfl_xor_sync(0xffffffffu, p, o);
+                if (ob > b || (ob == b && op < p)) { b = ob; p = op; }
             }
-        __syncthreads();
-        const double inv = 1.0 / pval;
-        for (int c = threadIdx.x; c < ld; c += blockDim.x) W[k * ld + c] *= inv;
-        __syncthreads();
-        for (int t = threadIdx.x; t < n * ld; t += blockDim.x) {
-            const int r = t / ld, c = t - r * ld;
-            if (r == k || c == k) continue;
-            W[t] -= W[r * ld + k] * W[k * ld + c];
+            if (lane == 0) {
+                piv = p;
+                pval = W[p * ld + k];
+                if (b <= 0.0) *info = k + 1;
+            }
         }
         __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x)
-            if (r != k) W[r * ld + k] = 0.0;
+        const double pv = pval;
+        if (pv == 0.0) return;
+        const int p = piv;
+        const double inv = 1.0 / pv;
+        for (int c = k + tid; c < ld; c += nt) {
+            const double a = W[k * ld + c], b = W[p * ld + c];
+            if (p != k) W[p * ld + c] = a;
+            const double s = b * inv;
+            W[k * ld + c] = s;
+            prow[c] = s;
+        }
+        __syncthreads();
+        const int wdt = ld - k - 1;  // columns k+1 .. ld-1
+        int r = tid / wdt, c = tid - r * wdt;
+        const int dr = nt / wdt, dc = nt - dr * wdt;
+        for (; r < n;) {
+            if (r != k) W[r * ld + k + 1 + c] -= W[r * ld + k] * prow[k + 1 + c];
+            c += dc;
+            r += dr;
+            if (c >= wdt) { c -= wdt; ++r; }
+        }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    for (int t = tid; t < N * N; t += nt) {
         const int r = t / N, c = t - r * N;
         Minv[t] = W[r * ld + n + c];
     }

@@ -48,6 +48,12 @@ __device__ __forceinline__ void unflat(int t, int nx, int ny, int& i, int& j, in
     k = q / ny;
 }
 
+// a * b + c with one rounding.  The smoother and residual rows accumulate
+// their off-diagonal terms through this, so every kernel that evaluates a row
+// rounds the same chain the same way, whatever the compiler would contract.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T>
 __device__ __forceinline__ T recip(T d);
 // FP32 levels only precondition the FP64 refinement: the fast reciprocal

@@ -61,7 +61,7 @@ struct Bump {
 // ---- live per-kernel event timing (mg_prof_*)
 struct ProfRec {
     int id;
-    double bytes;
+    double bytes, flops;
     cudaEvent_t a, b;
 };
 struct Prof {
@@ -78,7 +78,7 @@ Prof& prof()
 constexpr size_t kProfMax = 65536;
 
 // Returns a record index (or -1) after recording the start event on s.
-int prof_begin(int id, double bytes, cudaStream_t s)
+int prof_begin(int id, double bytes, cudaStream_t s, double flops = 0.0)
 {
     Prof& P = prof();
     if (!P.on) return -1;
@@ -92,6 +92,7 @@ int prof_begin(int id, double bytes, cudaStream_t s)
     ProfRec& r = P.recs[P.used];
     r.id = id;
     r.bytes = bytes;
+    r.flops = flops;
     cudaEventRecord(r.a, s);
     return (int)P.used++;
 }
@@ -392,7 +393,10 @@ void finish_rhs(mg_handle* h, int fslot, int srcslot)
 void residual64(mg_handle* h, const double* phi, float* r32)
 {
     cudaStream_t s = h->stream;
-    const int pr = prof_begin(MG_PROF_RESID64, (24.0 + (r32 ? 4.0 : 0.0)) * h->lev[0].nvec, s);
+    const bool nodal = h->loc == MG_LOC_NODAL;
+    const double nv = (double)h->lev[0].nvec;
+    const int pr = prof_begin(nodal ? MG_PROF_NODE_RESID64 : MG_PROF_RESID64, (24.0 + (r32 ? 4.0 : 0.0)) * nv, s,
+                              (nodal ? 45.0 : 17.0) * nv);
     if (h->loc == MG_LOC_CELL)
         cell_resid64(h->dim, cview<double>(h, 0), phi, h->f64, r32, &h->d->fscale, h->partials, s);
     else
@@ -1233,12 +1237,12 @@ void mg_prof_enable(int on)
     P.on = on != 0;
 }
 
-mg_status mg_prof_query(int kernel, double* total_ms, int* launches, double* bytes)
+mg_status mg_prof_query(int kernel, double* total_ms, int* launches, double* bytes, double* flops)
 {
     if (kernel < 0 || kernel >= MG_PROF_COUNT) return fail(MG_ERR_INVALID_ARG, "unknown kernel class");
     Prof& P = prof();
     std::lock_guard<std::mutex> lk(P.mu);
-    double ms = 0.0, by = 0.0;
+    double ms = 0.0, by = 0.0, fl = 0.0;
     int cnt = 0;
     for (size_t i = 0; i < P.used; ++i) {
         const ProfRec& r = P.recs[i];
@@ -1248,11 +1252,13 @@ mg_status mg_prof_query(int kernel, double* total_ms, int* launches, double* byt
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
         ms += t;
         by += r.bytes;
+        fl += r.flops;
         ++cnt;
     }
     if (total_ms) *total_ms = ms;
     if (launches) *launches = cnt;
     if (bytes) *bytes = by;
+    if (flops) *flops = fl;
     return MG_OK;
 }
 

@@ -77,7 +77,10 @@ struct CopyDesc {
     int src;  // in-plane element offset, or -1: outside the domain (zero fill)
 };
 
-template <typename T>
+// FAST: x and y periodic, so every in-plane face term is present and every
+// staged position is inside the domain; the boundary logic reduces to the two
+// z tests, which are uniform per plane.
+template <typename T, bool FAST>
 __global__ void __launch_bounds__(kPT)
 k_gsrb_pipe(CellLevel<T> L, const T* __restrict__ xin, T* __restrict__ xout, const T* __restrict__ b, int kz)
 {
@@ -155,19 +158,19 @@ k_gsrb_pipe(CellLevel<T> L, const T* __restrict__ xin, T* __restrict__ xout, con
         off = T(0);
         dg = T(0);
         const T bxl = Sk.FX[cy][cx], bxh = Sk.FX[cy][cx + 1];
-        if (gx > 0 || L.bc.lo[0] == BCP) { off += bxl * V(-1, 0, 0); dg += bxl; }
+        if (gx > 0 || L.bc.lo[0] == BCP) { off = fmadd(bxl, V(-1, 0, 0), off); dg += bxl; }
         else if (L.bc.lo[0] == BCD) { dg += T(2) * bxl; }
-        if (gx < nx - 1 || L.bc.hi[0] == BCP) { off += bxh * V(1, 0, 0); dg += bxh; }
+        if (gx < nx - 1 || L.bc.hi[0] == BCP) { off = fmadd(bxh, V(1, 0, 0), off); dg += bxh; }
         else if (L.bc.hi[0] == BCD) { dg += T(2) * bxh; }
         const T byl = Sk.FY[cy][cx], byh = Sk.FY[cy + 1][cx];
-        if (gy > 0 || L.bc.lo[1] == BCP) { off += byl * V(0, -1, 0); dg += byl; }
+        if (gy > 0 || L.bc.lo[1] == BCP) { off = fmadd(byl, V(0, -1, 0), off); dg += byl; }
         else if (L.bc.lo[1] == BCD) { dg += T(2) * byl; }
-        if (gy < ny - 1 || L.bc.hi[1] == BCP) { off += byh * V(0, 1, 0); dg += byh; }
+        if (gy < ny - 1 || L.bc.hi[1] == BCP) { off = fmadd(byh, V(0, 1, 0), off); dg += byh; }
         else if (L.bc.hi[1] == BCD) { dg += T(2) * byh; }
         const T bzl = Sk.FZ[cy][cx], bzh = Sk1.FZ[cy][cx];
-        if (k > 0) { off += bzl * V(0, 0, -1); dg += bzl; }
+        if (k > 0) { off = fmadd(bzl, V(0, 0, -1), off); dg += bzl; }
         else if (L.bc.lo[2] == BCD) { dg += T(2) * bzl; }
-        if (k < nz - 1) { off += bzh * V(0, 0, 1); dg += bzh; }
+        if (k < nz - 1) { off = fmadd(bzh, V(0, 0, 1), off); dg += bzh; }
         else if (L.bc.hi[2] == BCD) { dg += T(2) * bzh; }
     };
 
@@ -178,6 +181,71 @@ k_gsrb_pipe(CellLevel<T> L, const T* __restrict__ xin, T* __restrict__ xout, con
     // ---- black pair of this thread (t < 128): tile row by, pair bp
     const bool black_thread = tid < kPT / 2;
     const int by = tid / (kPX / 2), bp = tid - by * (kPX / 2);
+
+    // FAST-path per-thread offsets for both plane parities (index 0: (1+gy+k) even)
+    // (plain scalars picked with a select: a runtime-indexed array would live in local memory)
+    const int fr0 = ry * kPW + 2 * rix + 1;               // red cell in the ring arrays (cx = lx + 1)
+    const int fb0 = (by + 1) * kPW + 2 * bp + 2;          // black cell in the ring arrays (cx = bx + 2)
+    const int rpar0 = (1 + (y0 - 1 + ry)) & 1;            // red column parity at k = 0 (wrap keeps parity)
+    const int bpar0 = (x0 + y0 + by + 1) & 1;             // black column parity at k = 0
+
+    // FAST row: x low, x high, y low, y high, z low, z high (k_gsrb's order)
+    auto row_fast = [&](const T* FXp, const T* FYp, const T* FZk, const T* FZk1, int o, int k, auto V, T& off,
+                        T& dg) {
+        const T bxl = FXp[o], bxh = FXp[o + 1], byl = FYp[o], byh = FYp[o + kPW];
+        off = fmadd(bxl, V(-1, 0, 0), T(0));
+        dg = bxl;
+        off = fmadd(bxh, V(1, 0, 0), off);
+        dg += bxh;
+        off = fmadd(byl, V(0, -1, 0), off);
+        dg += byl;
+        off = fmadd(byh, V(0, 1, 0), off);
+        dg += byh;
+        const T bzl = FZk[o], bzh = FZk1[o];
+        if (k > 0) { off = fmadd(bzl, V(0, 0, -1), off); dg += bzl; }
+        else if (L.bc.lo[2] == BCD) { dg += T(2) * bzl; }
+        if (k < nz - 1) { off = fmadd(bzh, V(0, 0, 1), off); dg += bzh; }
+        else if (L.bc.hi[2] == BCD) { dg += T(2) * bzh; }
+    };
+
+    auto red_fast = [&](int k, int sk, int sk1, int skm) {
+        if (!red_thread) return;
+        const int o = fr0 + (rpar0 ^ (k & 1));                 // ring-array offset of the red cell
+        const PipeSlot<T>& Sk = sh.slot[sk];
+        const T* X0 = &Sk.X[0][0] + kPW;                   // X row of ring row 0
+        const T* Xm = &sh.slot[skm].X[0][0] + kPW;
+        const T* Xp = &sh.slot[sk1].X[0][0] + kPW;
+        auto V = [&](int dx, int dy, int dz) -> T {
+            const T* Xs = dz < 0 ? Xm : (dz > 0 ? Xp : X0);
+            return Xs[o + dy * kPW + dx];
+        };
+        T off, dg;
+        row_fast(&Sk.FX[0][0], &Sk.FY[0][0], &Sk.FZ[0][0], &sh.slot[sk1].FZ[0][0], o, k, V, off, dg);
+        const T inv = has_iv ? (&Sk.IV[0][0])[o] : recip(dg);
+        (&sh.rs[k % 3][0][0])[o] = (off - (&Sk.Bb[0][0])[o]) * inv;
+    };
+
+    auto black_fast = [&](int k, int sk, int sk1) {
+        if (!black_thread) return;
+        const int q = bpar0 ^ (k & 1);                     // 1: black cell is the pair's second
+        const int o = fb0 + q;
+        const PipeSlot<T>& Sk = sh.slot[sk];
+        const T* R0 = &sh.rs[k % 3][0][0];
+        const T* Rm = &sh.rs[(k + 2) % 3][0][0];
+        const T* Rp = &sh.rs[(k + 1) % 3][0][0];
+        auto V = [&](int dx, int dy, int dz) -> T {
+            const T* Rs = dz < 0 ? Rm : (dz > 0 ? Rp : R0);
+            return Rs[o + dy * kPW + dx];
+        };
+        T off, dg;
+        row_fast(&Sk.FX[0][0], &Sk.FY[0][0], &Sk.FZ[0][0], &sh.slot[sk1].FZ[0][0], o, k, V, off, dg);
+        const T inv = has_iv ? (&Sk.IV[0][0])[o] : recip(dg);
+        const T vb = (off - (&Sk.Bb[0][0])[o]) * inv;
+        const T vr = R0[q ? o - 1 : o + 1];
+        T* dst = xout + (size_t)k * plane + (size_t)(y0 + by) * nx + (x0 + 2 * bp);
+        if (q) { dst[0] = vr; dst[1] = vb; }
+        else { dst[0] = vb; dst[1] = vr; }
+    };
 
     auto red = [&](int k) {
         if (!red_thread || rgy < 0) return;
@@ -231,14 +299,20 @@ k_gsrb_pipe(CellLevel<T> L, const T* __restrict__ xin, T* __restrict__ xout, con
     for (int k = kfirst; k <= klast; ++k) {
         cp_async_wait<1>();  // planes <= k + 1 have landed (k + 2 may be in flight)
         __syncthreads();
-        red(k);
+        const int sk = k % kPSlots, sk1 = (k + 1) % kPSlots, skm = (k + kPSlots - 1) % kPSlots;
+        if (FAST) red_fast(k, sk, sk1, skm);
+        else red(k);
         __syncthreads();
-        if (k - 1 >= z0 && k - 1 < z1) black(k - 1);
+        if (k - 1 >= z0 && k - 1 < z1) {
+            if (FAST) black_fast(k - 1, skm, sk);
+            else black(k - 1);
+        }
         issue(k + 3);
     }
     if (z1 == nz) {
         __syncthreads();
-        black(nz - 1);
+        if (FAST) black_fast(nz - 1, (nz - 1) % kPSlots, nz % kPSlots);
+        else black(nz - 1);
     }
     cp_async_wait<0>();
 }
@@ -255,15 +329,18 @@ void cell_gsrb_sweep(int dim, const CellLevel<T>& L, const T* xin, T* xout, cons
     const size_t smem = sizeof(PipeShared<T>);
     static bool attr_set = false;  // one attribute call per instantiation
     if (!attr_set) {
-        cudaFuncSetAttribute(k_gsrb_pipe<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_gsrb_pipe<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_gsrb_pipe<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
+    const bool fast = L.bc.lo[0] == BCP && L.bc.lo[1] == BCP;
     // a chunk of z-planes per CTA: about 4 CTAs per SM over 152 SMs
     const long long tiles = (long long)(L.nx / kPX) * (L.ny / kPY);
     int kz = (int)((tiles * L.nz + 152 * 4 - 1) / (152 * 4));
     kz = kz < 8 ? 8 : kz;
     dim3 grid(L.nx / kPX, L.ny / kPY, (L.nz + kz - 1) / kz);
-    MGP_LAUNCH(k_gsrb_pipe<T><<<grid, kPT, smem, s>>>(L, xin, xout, b, kz));
+    if (fast) MGP_LAUNCH(k_gsrb_pipe<T, true><<<grid, kPT, smem, s>>>(L, xin, xout, b, kz));
+    else MGP_LAUNCH(k_gsrb_pipe<T, false><<<grid, kPT, smem, s>>>(L, xin, xout, b, kz));
 }
 
 template bool cell_gsrb_fused_ok<float>(int, const CellLevel<float>&);

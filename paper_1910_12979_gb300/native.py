@@ -69,6 +69,12 @@ SIGNATURES = [
                                 ctypes.POINTER(mg_stats)]),
     ("mg_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p * 3, ctypes.POINTER(mg_beta0), ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(mg_stats)]),
+    ("mg_base_state_beta0", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mg_base_state_map", ctypes.c_int, [ctypes.POINTER(mg_geometry), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p * 3,
+                                         ctypes.c_void_p]),
     ("mg_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p * 3, ctypes.POINTER(mg_beta0), ctypes.c_void_p,
                               ctypes.c_void_p]),
     ("mg_solve_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -85,12 +91,16 @@ SIGNATURES = [
     ("mg_prof_enable", None, [ctypes.c_int]),
     ("mg_launch_count", ctypes.c_longlong, []),
     ("mg_prof_query", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
-                                     ctypes.POINTER(ctypes.c_double)]),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 ]
 
-MG_PROF_CELL_SMOOTH_FINE, MG_PROF_RESID64, MG_PROF_NODE_SMOOTH_FINE, MG_PROF_CELL_RESTRICT_FINE = range(4)
-PROF_NAMES = {MG_PROF_CELL_SMOOTH_FINE: "cell_smooth_fine", MG_PROF_RESID64: "resid64",
-              MG_PROF_NODE_SMOOTH_FINE: "node_smooth_fine", MG_PROF_CELL_RESTRICT_FINE: "cell_restrict_fine"}
+MG_PROF_CELL_SMOOTH_FINE, MG_PROF_RESID64, MG_PROF_NODE_SMOOTH_FINE, MG_PROF_CELL_RESTRICT_FINE, \
+    MG_PROF_NODE_RESID64 = range(5)
+PROF_NAMES = {MG_PROF_CELL_SMOOTH_FINE: "cell_smooth_fine", MG_PROF_RESID64: "cell_resid64",
+              MG_PROF_NODE_SMOOTH_FINE: "node_smooth_fine", MG_PROF_CELL_RESTRICT_FINE: "cell_restrict_fine",
+              MG_PROF_NODE_RESID64: "node_resid64"}
+# kernel classes bound by the FP64 pipe rather than by HBM
+PROF_FP64_BOUND = {"cell_resid64", "node_resid64"}
 
 _lib = None
 
@@ -228,6 +238,25 @@ def mg_prof_enable(on):
 
 
 def mg_prof_query(kernel):
-    ms, n, by = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
-    check(load().mg_prof_query(kernel, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)), "mg_prof_query")
-    return {"ms": ms.value, "launches": n.value, "bytes": by.value}
+    ms, n, by, fl = ctypes.c_double(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    check(load().mg_prof_query(kernel, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by), ctypes.byref(fl)),
+          "mg_prof_query")
+    return {"ms": ms.value, "launches": n.value, "bytes": by.value, "flops": fl.value}
+
+
+def mg_base_state_beta0(p0_ptr, gamma1_ptr, gamma1_const, rho0_base, nr, beta0_ptr, stream_ptr=None):
+    return check(load().mg_base_state_beta0(ctypes.c_void_p(p0_ptr), ctypes.c_void_p(gamma1_ptr) if gamma1_ptr else None,
+                                            ctypes.c_double(gamma1_const), ctypes.c_double(rho0_base), nr,
+                                            ctypes.c_void_p(beta0_ptr), ctypes.c_void_p(stream_ptr)),
+                 "mg_base_state_beta0")
+
+
+def mg_base_state_map(geom, spherical, center, r0, dr, nr, beta0_r_ptr, rho0_r_ptr, sigma_ptr, beta0_cell_ptr,
+                      beta0_face_ptrs, stream_ptr=None):
+    c = (ctypes.c_double * 3)(*center)
+    f = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(p) if p else None for p in beta0_face_ptrs])
+    return check(load().mg_base_state_map(ctypes.byref(geom), int(spherical), c, ctypes.c_double(r0),
+                                          ctypes.c_double(dr), nr, ctypes.c_void_p(beta0_r_ptr),
+                                          ctypes.c_void_p(rho0_r_ptr), ctypes.c_void_p(sigma_ptr),
+                                          ctypes.c_void_p(beta0_cell_ptr), f, ctypes.c_void_p(stream_ptr)),
+                 "mg_base_state_map")

@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=24.0, help="serve: device-memory budget of the slots")
     ap.add_argument("--inflight", type=int, default=8, help="serve: concurrent solves")
     ap.add_argument("--serve-count", type=int, default=256, help="serve: requests per arrival rate")
+    ap.add_argument("--sweep", default="v4", choices=["v4", "pipe"],
+                    help="FP32 cell smoother: two vectorised colour passes (v4) or the pipelined one-launch "
+                         "sweep (pipe, MG_FLAG_SWEEP_PIPE)")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed-precision step (no graph-path, FP64, e2e or CPU legs): the "
                          "command used for ncu captures")
@@ -181,8 +184,9 @@ class Clocks:
 
 
 # the source files whose change invalidates a kernel class's ncu counters
-PROF_SOURCES = {"cell_smooth_fine": ["mg_sweep.cu"], "node_smooth_fine": ["mg_nodal.cu"],
-                "cell_restrict_fine": ["mg_cell.cu"], "cell_resid64": ["mg_cell.cu"], "node_resid64": ["mg_nodal.cu"]}
+PROF_SOURCES = {"cell_smooth_fine": ["mg_sweep.cu"], "node_smooth_fine": ["mg_nodal.cu", "mg_nodal.cuh"],
+                "cell_restrict_fine": ["mg_cell.cu"], "cell_resid64": ["mg_cell.cu"],
+                "node_resid64": ["mg_nodal.cu", "mg_nodal.cuh"]}
 
 
 def source_hash(kernel_class):
@@ -504,7 +508,8 @@ def main():
     stream.synchronize()
 
     def make(prec):
-        mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream)
+        fl = N.MG_FLAG_SWEEP_PIPE if args.sweep == "pipe" else 0
+        mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream, flags=fl)
         nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream)
         phim = torch.zeros(mac.vec_shape, dtype=torch.float64, device=dev)
         phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)
@@ -603,7 +608,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-            "config": dict(workload_config(n, args.tol), parallelism=f"independent solves x{world}"),
+            "config": dict(workload_config(n, args.tol), parallelism=f"independent solves x{world}",
+                           cell_smoother=args.sweep),
             "clocks": clocks, "gpu_launches": launches, "roofline": roof_line,
             "solver": {"mac": {k: st_mac[k] for k in ("iters", "rel_resid", "rel_constraint")},
                        "nodal": {k: st_nod[k] for k in ("iters", "rel_resid", "rel_constraint")}}}

@@ -135,13 +135,17 @@ typedef struct {
     int inner_cycles;
 } mg_options;
 
-/* flags: run every smoothing sweep as separate colour passes, never the fused
- * one-launch kernels (same arithmetic, slower; for testing). */
+/* flags: run every smoothing sweep with the plain one-thread-per-cell kernels,
+ * never the tiled or vectorised ones (same arithmetic, slower; for testing). */
 #define MG_FLAG_NO_FUSED 1
 /* flags: drive the iterations from the host (one scalar read-back per
  * iteration) instead of the graph-resident loop (same decisions, same phi).
  * The host loop is also used while mg_prof_enable(1) is in effect. */
 #define MG_FLAG_NO_GRAPH 2
+/* flags: FP32 cell levels sweep with the shared-memory pipelined one-launch
+ * kernel (red and black of a sweep in one pass over memory) instead of two
+ * vectorised colour passes (same arithmetic). */
+#define MG_FLAG_SWEEP_PIPE 4
 
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
@@ -263,8 +267,10 @@ typedef enum {
     MG_PROF_CELL_RESTRICT_FINE = 3, /* fused residual + restriction on the finest cell level:
                                        phi, f, sigma read, 1/2^dim word written per cell */
     MG_PROF_NODE_RESID64 = 4,     /* FP64 fine residual of a nodal system (+ FP32 copy):
-                                     phi, f, sigma in FP64 (+ r in FP32) per node; 45 FP64
-                                     flops per node (27-point operator assembled from 8 sigma) */
+                                     phi, f, sigma in FP64 (+ r in FP32) per node; FP64 flops
+                                     per node of the form evaluated: 45 for the row assembled
+                                     from 8 sigma (2-D, small 3-D grids), about 26.8 for the
+                                     sum-factorised 3-D form (edge sigma sums set up once) */
     MG_PROF_COUNT = 5
 } mg_prof_kernel;
 
@@ -293,6 +299,21 @@ typedef enum {
 #define MG_NOALLOC_MAX_CELLS (1 << 25)
 mg_status mg_mac_constraint_noalloc(const mg_geometry* geom, const double* const U[3], const mg_beta0* beta0,
                                     const double* S, double* out, void* stream);
+
+/* Precision conversions of the mixed-precision path, exposed so that they can
+ * be checked against the hardware conversions.  The paper has no counterpart.
+ * mg_convert_f64_to_f32 rounds to nearest, ties to even; mg_convert_f32_to_f64
+ * is exact.  x, y: device arrays of n elements (no overlap); stream as
+ * cudaStream_t (NULL: legacy default stream); asynchronous.  Both are
+ * computed with 32-bit integer operations for normal results and zeros (the
+ * hardware conversion for the rest), as in the library's FP64 kernels.
+ * MG_ERR_INVALID_ARG for null pointers with n > 0. */
+mg_status mg_convert_f64_to_f32(const double* x, float* y, size_t n, void* stream);
+mg_status mg_convert_f32_to_f64(const float* x, double* y, size_t n, void* stream);
+/* y = 1/x as the library's FP64 kernels compute it where they divide (face
+ * coefficients, projection updates): Newton's method from a binary32 estimate,
+ * within about one ulp of the quotient; arguments as above. */
+mg_status mg_reciprocal_f64(const double* x, double* y, size_t n, void* stream);
 
 void mg_prof_enable(int on);
 /* Total number of CUDA kernels this library has launched in the process. */

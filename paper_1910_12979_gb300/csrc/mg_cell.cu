@@ -76,7 +76,7 @@ __device__ __forceinline__ T inv_diag(const CellLevel<T>& L, int idx, T dg)
 
 // ------------------------------------------------------------------ setup
 
-__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+__device__ __forceinline__ double harmonic(double a, double b) { return (2.0 * a * b) * recip_nr(a + b); }
 
 // face coefficient along axis d from cell sigma, scaled by 1/h_d^2
 template <int D>
@@ -209,15 +209,18 @@ __global__ void k_resid_restrict(CellLevel<T> F, const T* __restrict__ x, const 
     int ci, cj, ck;
     unflat(t, cnx, cny, ci, cj, ck);
     const GlobalPhi<T> ph{x, F.nx, F.ny};
-    T s = T(0);
+    T r[1 << DIM];
 #pragma unroll
     for (int q = 0; q < (1 << DIM); ++q) {
         const int i = 2 * ci + (q & 1), j = 2 * cj + ((q >> 1) & 1), k = DIM == 3 ? 2 * ck + ((q >> 2) & 1) : 0;
         T off, dg;
         cell_row<DIM>(F, i, j, k, ph, off, dg);
         const size_t id = ((size_t)k * F.ny + j) * F.nx + i;
-        s += b[id] - (off - dg * x[id]);
+        r[q] = b[id] - fmadd(-dg, x[id], off);
     }
+    // x pairs, then y, then z: the order of the tiled and vectorised variants
+    T s = (r[0] + r[1]) + (r[2] + r[3]);
+    if (DIM == 3) s = s + ((r[4] + r[5]) + (r[6] + r[7]));
     bc[t] = s * (T(1) / T(1 << DIM));
 }
 
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(128) k_resid_restrict_t(CellLevel<T> F, const 
     const size_t id = ((size_t)k * F.ny + j) * F.nx + i;
     T off, dg;
     cell_row<3>(F, i, j, k, GlobalPhi<T>{x, F.nx, F.ny}, off, dg);
-    T r = b[id] - (off - dg * x[id]);
+    T r = b[id] - fmadd(-dg, x[id], off);
     r += __shfl_xor_sync(0xffffffffu, r, 1);
     if ((threadIdx.x & 1) == 0) sh[threadIdx.z][threadIdx.y][threadIdx.x >> 1] = r;
     __syncthreads();
@@ -322,7 +325,7 @@ __global__ void k_resid64(CellLevel<double> L, const double* __restrict__ x, con
         double off, dg;
         cell_row<DIM>(L, i, j, k, ph, off, dg);
         const double d = HAS_DIAG ? L.diag[t] : dg;
-        const float rs = (float)((b[t] - (off - d * x[t])) * inv);
+        const float rs = f64_to_f32_rn((b[t] - (off - d * x[t])) * inv);
         acc = fmaf(rs, rs, acc);
         if (r32) r32[t] = rs;
     }
@@ -422,7 +425,7 @@ __global__ void k_project(CellLevel<double> L, double h, const double* __restric
     } else {
         flux = Bt[t] * h * (P(hi) - P(lo));
     }
-    U[t] -= flux / b0f[t];
+    U[t] -= flux * recip_nr(b0f[t]);
 }
 
 // ---------------------------------------------------------- dense coarsest

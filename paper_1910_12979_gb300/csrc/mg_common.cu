@@ -69,14 +69,36 @@ __global__ void k_copy64(double* __restrict__ d, const double* __restrict__ a, s
 __global__ void k_to32(float* __restrict__ d, const double* __restrict__ a, size_t n)
 {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-        d[t] = (float)a[t];
+        d[t] = f64_to_f32_rn(a[t]);
 }
 __global__ void k_axpy32(double* __restrict__ phi, const float* __restrict__ e, const double* __restrict__ scale,
                          size_t n)
 {
     const double s = *scale;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-        phi[t] += s * (double)e[t];
+        phi[t] = fmadd(s, f32_to_f64(e[t]), phi[t]);
+}
+
+__global__ void k_to64(double* __restrict__ d, const float* __restrict__ a, size_t n)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        d[t] = f32_to_f64(a[t]);
+}
+
+__global__ void k_recip(double* __restrict__ d, const double* __restrict__ a, size_t n)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        d[t] = recip_nr(a[t]);
+}
+
+void vec_recip(double* dst, const double* src, size_t n, cudaStream_t s)
+{
+    MGP_LAUNCH(k_recip<<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
+}
+
+void vec_to_f64(double* dst, const float* src, size_t n, cudaStream_t s)
+{
+    MGP_LAUNCH(k_to64<<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
 }
 
 void vec_copy_f64(double* dst, const double* src, size_t n, cudaStream_t s)

@@ -54,6 +54,61 @@ __device__ __forceinline__ void unflat(int t, int nx, int ny, int& i, int& j, in
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// IEEE-754 conversions between binary64 and binary32 done with 32-bit integer
+// operations.  GB300 issues about two FP64 operations per SM per clock and a
+// hardware conversion occupies that pipe like an FMA, so in the FP64-bound
+// kernels the conversions move to the integer pipe.  Normal results follow the
+// format definition: binary64 -> binary32 keeps the top 23 fraction bits and
+// rounds to nearest, ties to even, on the 29 bits dropped (a carry out of the
+// fraction increments the exponent, up to infinity); binary32 -> binary64 is
+// exact (exponent rebiased by 1023 - 127, fraction shifted left by 29).  Zeros
+// are handled here; subnormal, infinite and NaN operands or results take the
+// hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double v)
+{
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e - 897u <= 253u) {  // 897 <= e <= 1150: the binary32 exponent field e - 896 is 1 .. 254
+        unsigned r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu, half = 0x10000000u;
+        r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;
+        return __uint_as_float(r | (hi & 0x80000000u));
+    }
+    if (e == 0 && ((hi & 0xfffffu) | lo) == 0) return __uint_as_float(hi & 0x80000000u);
+    return __double2float_rn(v);
+}
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e - 1u < 254u) {  // normal
+        const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+        return __hiloint2double((int)hi, (int)(u << 29));
+    }
+    if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+}
+
+// 1/d by Newton's method on g(y) = 1/y - d, whose step y <- y + y (1 - d y)
+// squares the relative error.  The start is PTX rcp.approx.ftz.f32 of d rounded
+// to binary32 (relative error below about 2^-22 in all); two steps bring it to
+// the binary64 rounding level, so the result is within about one ulp of 1/d
+// (not always the correctly rounded quotient).  That is four FP64 FMAs; the
+// FP64 pipe is the bound of the kernels that divide (face coefficients,
+// projection updates).  Operands outside [2^-125, 2^126), and zeros,
+// infinities and NaNs, take the IEEE division.
+__device__ __forceinline__ double recip_nr(double d)
+{
+    const unsigned e = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
+    if (e - 898u > 250u) return 1.0 / d;
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(f64_to_f32_rn(d)));
+    double y = f32_to_f64(y0);
+    y = fmadd(y, fmadd(-d, y, 1.0), y);
+    y = fmadd(y, fmadd(-d, y, 1.0), y);
+    return y;
+}
+
 template <typename T>
 __device__ __forceinline__ T recip(T d);
 // FP32 levels only precondition the FP64 refinement: the fast reciprocal

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <memory>
 #include <mutex>
+#include <type_traits>
 #include <new>
 #include <string>
 #include <vector>
@@ -112,6 +113,8 @@ struct Level {
     double* B64[3];
     double* invd64;
     double* diag64;    // level 0: diagonal for the FP64 residual
+    double* ew64[3];   // level 0, 3-D nodal: edge sigma sums of the sum-factorised residual
+    double* dq64;      //   and its scaled diagonal part
     float* B32[3];
     double* sig64;
     float* sig32;
@@ -209,7 +212,14 @@ mg_status plan(mg_handle* h, Bump& B)
         v.ncell = (size_t)n[0] * n[1] * n[2];
         v.nvec = nodal ? (size_t)v.N[0] * v.N[1] * v.N[2] : v.ncell;
         const size_t nc = v.ncell, nv = v.nvec;
-        if (L == 0) v.diag64 = B.take<double>(nv);
+        if (L == 0) {
+            if (nodal && dim == 3 && v.N[0] >= 32 && v.N[1] >= 8) {
+                for (int d = 0; d < 3; ++d) v.ew64[d] = B.take<double>(nv);
+                v.dq64 = B.take<double>(nv);
+            } else {
+                v.diag64 = B.take<double>(nv);
+            }
+        }
         if (!nodal) {
             for (int d = 0; d < dim; ++d) {
                 size_t m = (size_t)(n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2));
@@ -344,7 +354,9 @@ mg_status build_coefficients(mg_handle* h, const mg_coeff* c)
             NodeLevel<double> V = nview<double>(h, 0);
             V.invd = nullptr;
             V.diag = nullptr;
-            node_diag(dim, V, h->lev[0].diag64, s);
+            const Level& v0 = h->lev[0];
+            if (v0.dq64) node_edges(V, NodeEdges{{v0.ew64[0], v0.ew64[1], v0.ew64[2]}, v0.dq64}, s);
+            else node_diag(dim, V, v0.diag64, s);
         }
         const int n = h->Nd + h->singular;
         NodeLevel<double> C = nview<double>(h, h->nlev - 1);
@@ -389,16 +401,27 @@ void finish_rhs(mg_handle* h, int fslot, int srcslot)
     MGP_LAUNCH(k_keep<<<1, 1, 0, s>>>(h->d, fslot, -1));
 }
 
+// FP64 operations per node of the sum-factorised nodal residual, an FMA
+// counted as two: per cell position 3 adds (2x2 phi sum) + 1 add + 1 mul (Q),
+// times 297/256 cell positions per node; per node 3 + 1 adds (2x2 Q sums),
+// 6 FMAs (edge terms), 1 mul + 1 FMA (scaling and diagonal), 1 sub, 1 mul.
+constexpr double kNodeResidSFFlops = 5.0 * 297.0 / 256.0 + 21.0;
+
 // ||f - L phi||^2 / ||f||^2 -> d->rnorm2; optional FP32 copy of the residual / ||f||.
 void residual64(mg_handle* h, const double* phi, float* r32)
 {
     cudaStream_t s = h->stream;
     const bool nodal = h->loc == MG_LOC_NODAL;
     const double nv = (double)h->lev[0].nvec;
+    const Level& v0 = h->lev[0];
+    const bool sf = nodal && v0.dq64;
     const int pr = prof_begin(nodal ? MG_PROF_NODE_RESID64 : MG_PROF_RESID64, (24.0 + (r32 ? 4.0 : 0.0)) * nv, s,
-                              (nodal ? 45.0 : 17.0) * nv);
+                              (sf ? kNodeResidSFFlops : nodal ? 45.0 : 17.0) * nv);
     if (h->loc == MG_LOC_CELL)
         cell_resid64(h->dim, cview<double>(h, 0), phi, h->f64, r32, &h->d->fscale, h->partials, s);
+    else if (sf)
+        node_resid64_sf(nview<double>(h, 0), NodeEdges{{v0.ew64[0], v0.ew64[1], v0.ew64[2]}, v0.dq64}, phi, h->f64,
+                        r32, &h->d->fscale, h->partials, s);
     else
         node_resid64(h->dim, nview<double>(h, 0), phi, h->f64, r32, &h->d->fscale, h->partials, s);
     prof_end(pr, s);
@@ -436,10 +459,11 @@ void zero(T* p, size_t n, cudaStream_t s)
     cudaMemsetAsync(p, 0, n * sizeof(T), s);
 }
 
-// nu red-black sweeps (red, then black) on level l.  Levels that tile run one
-// fused launch per sweep, ping-ponging between x and the level's temp vector;
-// the others run the two colour passes in place.  Both orders are the same
-// arithmetic.  The finest level's launches are timed when profiling.
+// nu red-black sweeps (red, then black) on level l.  FP32 levels run two
+// vectorised colour passes in place; with MG_FLAG_SWEEP_PIPE (or FP64 levels)
+// levels that tile run one pipelined launch per sweep, ping-ponging between x
+// and the level's temp vector; the rest run the plain colour passes.  All are
+// the same arithmetic.  The finest level's launches are timed when profiling.
 template <typename T>
 void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, int nu)
 {
@@ -447,6 +471,17 @@ void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, i
     const double cells = (double)h->lev[l].ncell;
     T* t = lt<T>(h, l);
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    if constexpr (std::is_same<T, float>::value) {
+        if (!(h->opt.flags & (MG_FLAG_NO_FUSED | MG_FLAG_SWEEP_PIPE)) && cell_gsrb_v4_ok(h->dim, V, x, b)) {
+            for (int k = 0; k < nu; ++k)
+                for (int color = 0; color < 2; ++color) {
+                    const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * cells, s) : -1;
+                    cell_gsrb_v4(h->dim, V, x, b, color, s);
+                    prof_end(pr, s);
+                }
+            return;
+        }
+    }
     if (!(h->opt.flags & MG_FLAG_NO_FUSED) && cell_gsrb_fused_ok<T>(h->dim, V) && a16(x) && a16(t) && a16(b)) {
         T* src = x;
         T* dst = t;
@@ -483,7 +518,15 @@ void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
         cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu1);
         const int pr = l == 0 ? prof_begin(MG_PROF_CELL_RESTRICT_FINE,
                                            (3.0 + 1.0 / (1 << dim)) * sizeof(T) * h->lev[0].ncell, s) : -1;
-        cell_resid_restrict<T>(dim, V, X(l), Bv(l), lb<T>(h, l + 1), s);
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (!(h->opt.flags & (MG_FLAG_NO_FUSED | MG_FLAG_SWEEP_PIPE)) &&
+                cell_resid_restrict_v4_ok(dim, V, X(l), Bv(l), lb<T>(h, l + 1))) {
+                cell_resid_restrict_v4(V, X(l), Bv(l), lb<T>(h, l + 1), s);
+                done = true;
+            }
+        }
+        if (!done) cell_resid_restrict<T>(dim, V, X(l), Bv(l), lb<T>(h, l + 1), s);
         prof_end(pr, s);
     }
     dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
@@ -1226,6 +1269,33 @@ const char* mg_strerror(mg_status s)
 }
 
 const char* mg_last_error(void) { return g_last_error.c_str(); }
+
+mg_status mg_convert_f64_to_f32(const double* x, float* y, size_t n, void* stream)
+{
+    if (n == 0) return MG_OK;
+    if (!x || !y) return fail(MG_ERR_INVALID_ARG, "null array");
+    vec_to_f32(y, x, n, (cudaStream_t)stream);
+    MG_CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status mg_convert_f32_to_f64(const float* x, double* y, size_t n, void* stream)
+{
+    if (n == 0) return MG_OK;
+    if (!x || !y) return fail(MG_ERR_INVALID_ARG, "null array");
+    vec_to_f64(y, x, n, (cudaStream_t)stream);
+    MG_CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status mg_reciprocal_f64(const double* x, double* y, size_t n, void* stream)
+{
+    if (n == 0) return MG_OK;
+    if (!x || !y) return fail(MG_ERR_INVALID_ARG, "null array");
+    vec_recip(y, x, n, (cudaStream_t)stream);
+    MG_CK(cudaGetLastError());
+    return MG_OK;
+}
 
 long long mg_launch_count(void) { return launch_count(); }
 

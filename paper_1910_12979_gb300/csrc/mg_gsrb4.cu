@@ -1,0 +1,244 @@
+// mg_gsrb4.cu -- one colour pass of red-black Gauss-Seidel, four cells per thread.
+//
+// A thread owns four consecutive cells of an x-row and updates the two of them
+// that have the pass's colour, in place.  Every operand comes in 16-byte loads
+// where the layout allows: the four cells, the rows above and below, the
+// planes in front and behind, b and the y- and z-face coefficients (x-faces
+// have n+1 per row, so those are four scalar loads); the one x-neighbour
+// outside the quad is a scalar load.  The quad is written back as one 16-byte
+// store; its two cells of the other colour are rewritten with the values read,
+// which nothing changes during the pass.  Warps cover 32 consecutive quads of
+// a row, so every access is coalesced, and the instruction count per cell is a
+// small fraction of a shared-memory tiled sweep's.  Levels whose x is the
+// fastest axis of at most a few hundred kilobytes per plane keep the
+// neighbouring planes in L2 between the rows that share them; b and the face
+// arrays are read once per pass with the streaming cache hint.
+//
+// The row arithmetic -- the order of the six face terms, the boundary cases and
+// the diagonal -- is that of k_gsrb (cell_row), so two passes of this kernel
+// equal two passes of k_gsrb bit for bit.  Requirements (checked by the
+// launcher): FP32, nx % 4 == 0.
+#include "mg_device.cuh"
+
+namespace mgp {
+
+namespace {
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld4s(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float el(const float4& v, int p) { return p == 0 ? v.x : p == 1 ? v.y : p == 2 ? v.z : v.w; }
+
+}  // namespace
+
+template <int DIM>
+__global__ void __launch_bounds__(256)
+k_gsrb_v4(CellLevel<float> L, float* __restrict__ x, const float* __restrict__ b, int color)
+{
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (4 * q >= nx || j >= ny) return;
+    const int i0 = 4 * q;
+    const size_t plane = (size_t)nx * ny;
+    const size_t row = (size_t)k * plane + (size_t)j * nx;
+    const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
+
+    const float4 xc = ld4(x + row + i0);
+    const float4 bb = ld4s(b + row + i0);
+    // neighbour rows / planes (present: inside, or wrapped on a periodic axis)
+    const bool hym = j > 0 || py, hyp = j < ny - 1 || py;
+    const bool hzm = DIM == 3 && (k > 0 || pz), hzp = DIM == 3 && (k < nz - 1 || pz);
+    const size_t rym = j > 0 ? row - nx : row + (size_t)(ny - 1) * nx;
+    const size_t ryp = j < ny - 1 ? row + nx : row - (size_t)(ny - 1) * nx;
+    const size_t rzm = k > 0 ? row - plane : row + (size_t)(nz - 1) * plane;
+    const size_t rzp = k < nz - 1 ? row + plane : row - (size_t)(nz - 1) * plane;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 xym = hym ? ld4(x + rym + i0) : zero4;
+    const float4 xyp = hyp ? ld4(x + ryp + i0) : zero4;
+    const float4 xzm = hzm ? ld4(x + rzm + i0) : zero4;
+    const float4 xzp = hzp ? ld4(x + rzp + i0) : zero4;
+    // the cells of this colour are p0 and p0 + 2 (i0 is even)
+    const int p0 = (color + j + k) & 1;
+    // x-neighbour outside the quad: left of cell 0 (p0 == 0) or right of cell 3 (p0 == 1)
+    float xout = 0.f;
+    if (p0 == 0) {
+        if (i0 > 0) xout = x[row + i0 - 1];
+        else if (px) xout = x[row + nx - 1];
+    } else {
+        if (i0 + 4 < nx) xout = x[row + i0 + 4];
+        else if (px) xout = x[row];
+    }
+    // face coefficients: x-faces i0+p0 .. i0+p0+3; y-faces of rows j, j+1; z-faces of planes k, k+1
+    const size_t fxb = ((size_t)k * ny + j) * (nx + 1) + i0 + p0;
+    const float fx0 = __ldcs(L.bx + fxb), fx1 = __ldcs(L.bx + fxb + 1), fx2 = __ldcs(L.bx + fxb + 2),
+                fx3 = __ldcs(L.bx + fxb + 3);
+    const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
+    const float4 fyl = ld4s(L.by + fyb), fyh = ld4s(L.by + fyb + nx);
+    float4 fzl = zero4, fzh = zero4;
+    if (DIM == 3) {
+        fzl = ld4s(L.bz + row + i0);
+        fzh = ld4s(L.bz + row + plane + i0);
+    }
+
+    auto update = [&](int p, float bxl, float bxh, float xl, float xh) -> float {
+        const int i = i0 + p;
+        float off = 0.f, dg = 0.f;
+        if (i > 0 || px) { off = fmadd(bxl, xl, off); dg += bxl; }
+        else if (L.bc.lo[0] == BCD) { dg += 2.f * bxl; }
+        if (i < nx - 1 || px) { off = fmadd(bxh, xh, off); dg += bxh; }
+        else if (L.bc.hi[0] == BCD) { dg += 2.f * bxh; }
+        const float byl = el(fyl, p), byh = el(fyh, p);
+        if (hym) { off = fmadd(byl, el(xym, p), off); dg += byl; }
+        else if (L.bc.lo[1] == BCD) { dg += 2.f * byl; }
+        if (hyp) { off = fmadd(byh, el(xyp, p), off); dg += byh; }
+        else if (L.bc.hi[1] == BCD) { dg += 2.f * byh; }
+        if (DIM == 3) {
+            const float bzl = el(fzl, p), bzh = el(fzh, p);
+            if (hzm) { off = fmadd(bzl, el(xzm, p), off); dg += bzl; }
+            else if (L.bc.lo[2] == BCD) { dg += 2.f * bzl; }
+            if (hzp) { off = fmadd(bzh, el(xzp, p), off); dg += bzh; }
+            else if (L.bc.hi[2] == BCD) { dg += 2.f * bzh; }
+        }
+        return (off - el(bb, p)) * recip(dg);
+    };
+    float4 out = xc;
+    if (p0 == 0) {
+        out.x = update(0, fx0, fx1, xout, xc.y);
+        out.z = update(2, fx2, fx3, xc.y, xc.w);
+    } else {
+        out.y = update(1, fx0, fx1, xc.x, xc.z);
+        out.w = update(3, fx2, fx3, xc.z, xout);
+    }
+    *reinterpret_cast<float4*>(x + row + i0) = out;
+}
+
+bool cell_gsrb_v4_ok(int dim, const CellLevel<float>& L, const float* x, const float* b)
+{
+    auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    return L.nx % 4 == 0 && L.nx >= 8 && L.invd == nullptr && a16(x) && a16(b) && a16(L.by) &&
+           (dim == 2 || a16(L.bz));
+}
+
+void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, int color, cudaStream_t s)
+{
+    const int nq = L.nx / 4;
+    const int bx = nq >= 32 ? 32 : nq >= 16 ? 16 : nq >= 8 ? 8 : nq >= 4 ? 4 : 2;
+    const dim3 block(bx, 256 / bx);
+    const dim3 grid((nq + bx - 1) / bx, (L.ny + block.y - 1) / block.y, dim == 3 ? L.nz : 1);
+    if (dim == 2) MGP_LAUNCH(k_gsrb_v4<2><<<grid, block, 0, s>>>(L, x, b, color));
+    else MGP_LAUNCH(k_gsrb_v4<3><<<grid, block, 0, s>>>(L, x, b, color));
+}
+
+}  // namespace mgp
+
+namespace mgp {
+
+// Residual r = b - L x of a 3-D FP32 level averaged over the 2 x 2 x 2 children
+// of each coarse cell, vectorised like k_gsrb_v4: lane pairs of a warp own one
+// quad of four x-cells in two consecutive rows, the even lane in plane 2ck and
+// the odd lane in plane 2ck + 1.  Each lane sums its residuals over x-pairs and
+// then over its two rows; one shuffle adds the two planes; the even lane
+// writes the two coarse cells.  The per-cell arithmetic and the order of the
+// sums (x pair, then y, then z) are those of k_resid_restrict_t, so the coarse
+// right-hand sides are identical.  Requirements: nx % 4 == 0, ny and nz even.
+__global__ void __launch_bounds__(256)
+k_resid_restrict_v4(CellLevel<float> F, const float* __restrict__ x, const float* __restrict__ b,
+                    float* __restrict__ bc)
+{
+    const int nx = F.nx, ny = F.ny, nz = F.nz;
+    const int lane = threadIdx.x;                      // 0..31
+    const int q = blockIdx.x * 16 + (lane >> 1);       // quad along x
+    const int cj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = 2 * blockIdx.z + (lane & 1);
+    const bool live = 4 * q < nx && 2 * cj < ny;
+    const int i0 = 4 * q;
+    const size_t plane = (size_t)nx * ny;
+    const bool px = F.bc.lo[0] == BCP, py = F.bc.lo[1] == BCP, pz = F.bc.lo[2] == BCP;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float s0 = 0.f, s1 = 0.f;   // this lane's sums for coarse x-cells 2q and 2q + 1
+    if (live) {
+        const bool hzm = k > 0 || pz, hzp = k < nz - 1 || pz;
+        float pair[2][2];
+#pragma unroll
+        for (int yy = 0; yy < 2; ++yy) {
+            const int j = 2 * cj + yy;
+            const size_t row = (size_t)k * plane + (size_t)j * nx;
+            const bool hym = j > 0 || py, hyp = j < ny - 1 || py;
+            const size_t rym = j > 0 ? row - nx : row + (size_t)(ny - 1) * nx;
+            const size_t ryp = j < ny - 1 ? row + nx : row - (size_t)(ny - 1) * nx;
+            const size_t rzm = k > 0 ? row - plane : row + (size_t)(nz - 1) * plane;
+            const size_t rzp = k < nz - 1 ? row + plane : row - (size_t)(nz - 1) * plane;
+            const float4 xc = ld4(x + row + i0);
+            const float4 bb = ld4s(b + row + i0);
+            const float4 xym = hym ? ld4(x + rym + i0) : zero4;
+            const float4 xyp = hyp ? ld4(x + ryp + i0) : zero4;
+            const float4 xzm = hzm ? ld4(x + rzm + i0) : zero4;
+            const float4 xzp = hzp ? ld4(x + rzp + i0) : zero4;
+            float xl = 0.f, xr = 0.f;
+            if (i0 > 0) xl = x[row + i0 - 1];
+            else if (px) xl = x[row + nx - 1];
+            if (i0 + 4 < nx) xr = x[row + i0 + 4];
+            else if (px) xr = x[row];
+            const size_t fxb = ((size_t)k * ny + j) * (nx + 1) + i0;
+            const float f0 = __ldcs(F.bx + fxb), f1 = __ldcs(F.bx + fxb + 1), f2 = __ldcs(F.bx + fxb + 2),
+                        f3 = __ldcs(F.bx + fxb + 3), f4 = __ldcs(F.bx + fxb + 4);
+            const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
+            const float4 fyl = ld4s(F.by + fyb), fyh = ld4s(F.by + fyb + nx);
+            const float4 fzl = ld4s(F.bz + row + i0), fzh = ld4s(F.bz + row + plane + i0);
+            const float fx[5] = {f0, f1, f2, f3, f4};
+            const float xs[6] = {xl, xc.x, xc.y, xc.z, xc.w, xr};
+            float r[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int i = i0 + p;
+                float off = 0.f, dg = 0.f;
+                const float bxl = fx[p], bxh = fx[p + 1];
+                if (i > 0 || px) { off = fmadd(bxl, xs[p], off); dg += bxl; }
+                else if (F.bc.lo[0] == BCD) { dg += 2.f * bxl; }
+                if (i < nx - 1 || px) { off = fmadd(bxh, xs[p + 2], off); dg += bxh; }
+                else if (F.bc.hi[0] == BCD) { dg += 2.f * bxh; }
+                const float byl = el(fyl, p), byh = el(fyh, p);
+                if (hym) { off = fmadd(byl, el(xym, p), off); dg += byl; }
+                else if (F.bc.lo[1] == BCD) { dg += 2.f * byl; }
+                if (hyp) { off = fmadd(byh, el(xyp, p), off); dg += byh; }
+                else if (F.bc.hi[1] == BCD) { dg += 2.f * byh; }
+                const float bzl = el(fzl, p), bzh = el(fzh, p);
+                if (hzm) { off = fmadd(bzl, el(xzm, p), off); dg += bzl; }
+                else if (F.bc.lo[2] == BCD) { dg += 2.f * bzl; }
+                if (hzp) { off = fmadd(bzh, el(xzp, p), off); dg += bzh; }
+                else if (F.bc.hi[2] == BCD) { dg += 2.f * bzh; }
+                r[p] = el(bb, p) - fmadd(-dg, xs[p + 1], off);
+            }
+            pair[yy][0] = r[0] + r[1];
+            pair[yy][1] = r[2] + r[3];
+        }
+        s0 = pair[0][0] + pair[1][0];
+        s1 = pair[0][1] + pair[1][1];
+    }
+    const float o0 = __shfl_xor_sync(0xffffffffu, s0, 1), o1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+    if (live && (lane & 1) == 0) {
+        const int cnx = nx / 2, cny = ny / 2;
+        float2 v;
+        v.x = (s0 + o0) * 0.125f;
+        v.y = (s1 + o1) * 0.125f;
+        *reinterpret_cast<float2*>(bc + ((size_t)blockIdx.z * cny + cj) * cnx + 2 * q) = v;
+    }
+}
+
+bool cell_resid_restrict_v4_ok(int dim, const CellLevel<float>& F, const float* x, const float* b, const float* bc)
+{
+    auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    return dim == 3 && F.nx % 4 == 0 && F.nx >= 8 && F.ny % 2 == 0 && F.nz % 2 == 0 && a16(x) && a16(b) &&
+           a16(F.by) && a16(F.bz) && ((uintptr_t)bc & 7) == 0;
+}
+
+void cell_resid_restrict_v4(const CellLevel<float>& F, const float* x, const float* b, float* bc, cudaStream_t s)
+{
+    const int nq = F.nx / 4, cny = F.ny / 2, cnz = F.nz / 2;
+    const dim3 block(32, 8);
+    const dim3 grid((nq + 15) / 16, (cny + 7) / 8, cnz);
+    MGP_LAUNCH(k_resid_restrict_v4<<<grid, block, 0, s>>>(F, x, b, bc));
+}
+
+}  // namespace mgp

@@ -92,6 +92,13 @@ void cell_gsrb(int dim, const CellLevel<T>& L, T* x, const T* b, int color, cuda
 // one full red-then-black sweep xin -> xout in a single launch (when ok)
 template <typename T>
 bool cell_gsrb_fused_ok(int dim, const CellLevel<T>& L);
+// one colour pass, four cells per thread with 16-byte accesses (FP32, nx % 4 == 0,
+// 16-byte aligned x, b and face arrays); same arithmetic as cell_gsrb
+bool cell_gsrb_v4_ok(int dim, const CellLevel<float>& L, const float* x, const float* b);
+void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, int color, cudaStream_t s);
+// 3-D residual + restriction, vectorised like cell_gsrb_v4; same results as cell_resid_restrict
+bool cell_resid_restrict_v4_ok(int dim, const CellLevel<float>& F, const float* x, const float* b, const float* bc);
+void cell_resid_restrict_v4(const CellLevel<float>& F, const float* x, const float* b, float* bc, cudaStream_t s);
 template <typename T>
 void cell_gsrb_sweep(int dim, const CellLevel<T>& L, const T* xin, T* xout, const T* b, cudaStream_t s);
 template <typename T>
@@ -127,8 +134,23 @@ template <typename T>
 void node_restrict(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, const T* rf, T* bc, cudaStream_t s);
 template <typename T>
 void node_prolong_add(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, T* xf, const T* xc, cudaStream_t s);
+// FP32 3-D levels with x periodic and nx % 4 == 0: Jacobi sweep / residual with
+// four nodes per thread (same results as the plain kernels)
+bool node_v4_ok(int dim, const NodeLevel<float>& L, const float* x, const float* out, const float* b);
+void node_v4(const NodeLevel<float>& L, const float* x, float* out, const float* b, float omega, bool resid,
+             cudaStream_t s);
 void node_resid64(int dim, const NodeLevel<double>& L, const double* x, const double* b, float* r32,
                   const double* scale, double* partials, cudaStream_t s);
+// Level-0 data of the sum-factorised FP64 nodal residual (3-D): per node the
+// sigma sums over the cells around its +x, +y and +z edges (w), and
+// dq = -(5/12) sum(sigma of its cells) / h^2 (0 at Dirichlet nodes).
+struct NodeEdges {
+    double* w[3];
+    double* dq;
+};
+void node_edges(const NodeLevel<double>& L, const NodeEdges& E, cudaStream_t s);
+void node_resid64_sf(const NodeLevel<double>& L, const NodeEdges& E, const double* x, const double* b, float* r32,
+                     const double* scale, double* partials, cudaStream_t s);
 void node_apply64(int dim, const NodeLevel<double>& L, const double* x, double* out, cudaStream_t s);
 void node_rhs(int dim, const NodeLevel<double>& L, double h, const double* const U[3], const double* b0,
               const double* S, double* f, double* partials, cudaStream_t s);
@@ -148,6 +170,8 @@ void vec_sum_sq(const double* v, size_t n, double* partials, cudaStream_t s);
 void vec_sub_mean(double* v, size_t n, const double* sum, double count, cudaStream_t s);
 void vec_copy_f64(double* dst, const double* src, size_t n, cudaStream_t s);
 void vec_to_f32(float* dst, const double* src, size_t n, cudaStream_t s);
+void vec_to_f64(double* dst, const float* src, size_t n, cudaStream_t s);
+void vec_recip(double* dst, const double* src, size_t n, cudaStream_t s);
 void vec_zero_f32(float* v, size_t n, cudaStream_t s);
 void vec_zero_f64(double* v, size_t n, cudaStream_t s);
 // phi += (*scale) * e

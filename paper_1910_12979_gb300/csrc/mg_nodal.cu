@@ -1,86 +1,9 @@
-// mg_nodal.cu -- nodal (Q1 finite element) projection kernels.
-//
-// phi lives on nodes, sigma = beta0/rho is constant per cell, U is cell-centred.
-// With equal spacing h the Q1 operator at node I, assembled on the fly from the
-// sigma of the 2^dim cells touching I (cells outside a non-periodic boundary
-// contribute nothing: the natural boundary condition), is
-//   3-D: h^2 (L phi)_I = sum_cells sigma_c [ -phi_I/3
-//            + (phi_{2 axes moved} x3 + phi_{opposite corner}) / 12 ]
-//        (face-adjacent corners have zero weight: 21 non-zeros at constant sigma)
-//   2-D: h^2 (L phi)_I = sum_cells sigma_c [ -2 phi_I/3 + (phi_x + phi_y)/6 + phi_diag/3 ]
-// written as (L phi)_I = off_I + diag_I phi_I.  Dirichlet nodes hold 0 and are not
-// unknowns; periodic node n_d is node 0.
-#include "mg_device.cuh"
+// mg_nodal.cu -- nodal (Q1 finite element) operator, smoother, transfers and FP64 residual.
+#include "mg_nodal.cuh"
+
+#include <type_traits>
 
 namespace mgp {
-
-__device__ __forceinline__ bool cell_ok(int c, int n, int bc, int& w)
-{
-    if (c >= 0 && c < n) { w = c; return true; }
-    if (bc != BCP) return false;
-    w = c < 0 ? c + n : c - n;
-    return true;
-}
-
-__device__ __forceinline__ int node_nb(int p, int N, int bc)  // periodic wrap of a node index
-{
-    return bc == BCP ? wrap(p, N) : p;
-}
-
-template <typename T>
-__device__ __forceinline__ bool node_dirichlet(const NodeLevel<T>& L, int i, int j, int k, int dim)
-{
-    if ((L.bc.lo[0] == BCD && i == 0) || (L.bc.hi[0] == BCD && i == L.nx)) return true;
-    if ((L.bc.lo[1] == BCD && j == 0) || (L.bc.hi[1] == BCD && j == L.ny)) return true;
-    if (dim == 3 && ((L.bc.lo[2] == BCD && k == 0) || (L.bc.hi[2] == BCD && k == L.nz))) return true;
-    return false;
-}
-
-template <int DIM, typename T, typename Phi>
-__device__ __forceinline__ void node_row(const NodeLevel<T>& L, int i, int j, int k, const Phi& phi, T& off, T& dg)
-{
-    T acc = T(0), ssum = T(0);
-    if (DIM == 3) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1, sz = (c & 4) ? 1 : -1;
-            int ci, cj, ck;
-            if (!cell_ok(sx > 0 ? i : i - 1, L.nx, L.bc.lo[0], ci)) continue;
-            if (!cell_ok(sy > 0 ? j : j - 1, L.ny, L.bc.lo[1], cj)) continue;
-            if (!cell_ok(sz > 0 ? k : k - 1, L.nz, L.bc.lo[2], ck)) continue;
-            const T sg = L.sigma[((size_t)ck * L.ny + cj) * L.nx + ci];
-            const int a = node_nb(i + sx, L.Nx, L.bc.lo[0]);
-            const int b = node_nb(j + sy, L.Ny, L.bc.lo[1]);
-            const int e = node_nb(k + sz, L.Nz, L.bc.lo[2]);
-            acc += sg * (phi(a, b, k) + phi(a, j, e) + phi(i, b, e) + phi(a, b, e));
-            ssum += sg;
-        }
-        off = acc * (L.ih2 / T(12));
-        dg = -ssum * (L.ih2 / T(3));
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1;
-            int ci, cj;
-            if (!cell_ok(sx > 0 ? i : i - 1, L.nx, L.bc.lo[0], ci)) continue;
-            if (!cell_ok(sy > 0 ? j : j - 1, L.ny, L.bc.lo[1], cj)) continue;
-            const T sg = L.sigma[(size_t)cj * L.nx + ci];
-            const int a = node_nb(i + sx, L.Nx, L.bc.lo[0]);
-            const int b = node_nb(j + sy, L.Ny, L.bc.lo[1]);
-            acc += sg * ((phi(a, j, 0) + phi(i, b, 0)) * T(0.5) + phi(a, b, 0));
-            ssum += sg;
-        }
-        off = acc * (L.ih2 / T(3));
-        dg = -ssum * (L.ih2 * T(2) / T(3));
-    }
-}
-
-template <typename T>
-struct NodePhi {
-    const T* p;
-    int Nx, Ny;
-    __device__ __forceinline__ T operator()(int i, int j, int k) const { return p[((size_t)k * Ny + j) * Nx + i]; }
-};
 
 // ----------------------------------------------------------------- setup
 
@@ -146,7 +69,7 @@ __global__ void k_jacobi(NodeLevel<T> L, const T* __restrict__ x, T* __restrict_
     node_row<DIM>(L, i, j, k, NodePhi<T>{x, L.Nx, L.Ny}, off, dg);
     const T xi = x[t];
     const T id = L.invd ? L.invd[t] : recip(dg);
-    xo[t] = xi + omega * (b[t] - (off + dg * xi)) * id;
+    xo[t] = fmadd(omega * (b[t] - fmadd(dg, xi, off)), id, xi);
 }
 
 template <int DIM, typename T>
@@ -160,7 +83,7 @@ __global__ void k_node_resid(NodeLevel<T> L, const T* __restrict__ x, const T* _
     if (node_dirichlet(L, i, j, k, DIM)) { r[t] = T(0); return; }
     T off, dg;
     node_row<DIM>(L, i, j, k, NodePhi<T>{x, L.Nx, L.Ny}, off, dg);
-    r[t] = b[t] - (off + dg * x[t]);
+    r[t] = b[t] - fmadd(dg, x[t], off);
 }
 
 // fine lattice position q on an axis: wrapped when periodic; false outside
@@ -241,7 +164,7 @@ __global__ void k_node_prolong(NodeLevel<T> F, NodeLevel<T> C, T* __restrict__ x
 // latency of later planes overlaps the arithmetic.  The cell loop visits the
 // cells in node_row's order; a missing cell adds 0 * (...), which leaves both
 // sums unchanged: the results equal k_jacobi's / k_node_resid's.  3-D only.
-constexpr int kNTX = 32, kNTY = 8, kNSlots = 4;
+constexpr int kNSlots = 4;
 
 template <typename T>
 struct NodePipeSlot {
@@ -250,25 +173,6 @@ struct NodePipeSlot {
     T bb[kNTY][kNTX];           // b of the tile
     T iv[kNTY][kNTX];           // 1/diagonal (FP64 levels)
 };
-
-__device__ __forceinline__ void cp_async_commit_n() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-__device__ __forceinline__ void ncp_async(void* smem, const void* gmem, bool valid, int bytes)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const int n = valid ? bytes : 0;
-    if (bytes == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
-}
-
-__device__ __forceinline__ int npos(int g, int n, bool periodic)
-{
-    if (g >= 0 && g < n) return g;
-    if (!periodic) return -1;
-    return g < 0 ? g + n : g - n;
-}
 
 template <typename T, bool RESID>
 __global__ void __launch_bounds__(kNTX * kNTY)
@@ -356,7 +260,7 @@ k_node_tiled(NodeLevel<T> L, const T* __restrict__ x, T* __restrict__ out, const
                     const NodePipeSlot<T>& Se = sz > 0 ? Sp : Sm;   // node plane k+sz
                     const T sg = Sc.ss[ly + (sy > 0 ? 0 : -1)][lx + (sx > 0 ? 0 : -1)];
                     const int a = lx + sx, bb2 = ly + sy;
-                    acc += sg * (Sk.xs[bb2][a] + Se.xs[ly][a] + Se.xs[bb2][lx] + Se.xs[bb2][a]);
+                    acc = fmadd(sg, ((Sk.xs[bb2][a] + Se.xs[ly][a]) + Se.xs[bb2][lx]) + Se.xs[bb2][a], acc);
                     ssum += sg;
                 }
                 const T off = acc * (L.ih2 / T(12));
@@ -364,10 +268,10 @@ k_node_tiled(NodeLevel<T> L, const T* __restrict__ x, T* __restrict__ out, const
                 const T xi = Sk.xs[ly][lx];
                 const T bv = Sk.bb[threadIdx.y][threadIdx.x];
                 if (RESID) {
-                    out[id] = bv - (off + dg * xi);
+                    out[id] = bv - fmadd(dg, xi, off);
                 } else {
                     const T inv = has_iv ? Sk.iv[threadIdx.y][threadIdx.x] : recip(dg);
-                    out[id] = xi + omega * (bv - (off + dg * xi)) * inv;
+                    out[id] = fmadd(omega * (bv - fmadd(dg, xi, off)), inv, xi);
                 }
             }
         }
@@ -396,7 +300,7 @@ __global__ void k_node_resid64(NodeLevel<double> L, const double* __restrict__ x
             double off, dg;
             node_row<DIM>(L, i, j, k, ph, off, dg);
             const double d = HAS_DIAG ? L.diag[t] : dg;
-            rs = (float)((b[t] - (off + d * x[t])) * inv);
+            rs = f64_to_f32_rn((b[t] - (off + d * x[t])) * inv);
         }
         acc = fmaf(rs, rs, acc);
         if (r32) r32[t] = rs;
@@ -430,159 +334,214 @@ __global__ void k_node_apply64(NodeLevel<double> L, const double* __restrict__ x
     out[t] = off + dg * x[t];
 }
 
-// ------------------------------------------------------ RHS / projection
+// ------------------------------------- sum-factorised FP64 residual (3-D)
+//
+// GB300 issues about two FP64 operations per SM per clock, so the FP64
+// residual is bound by its FP64 operation count, not by HBM.  With the cell
+// sum s_c = (sum of the 8 phi of cell c), the 3-D row of node_row regroups as
+//   h^2 (L phi)_I = (1/12) [ sum_c sigma_c s_c - sum_{6 nbrs n} W_In phi_n ]
+//                   - (5/12) phi_I sum_c sigma_c
+// (the 3 face-adjacent nodes of each cell carry weight 0 in the Q1 row, and
+// s_c = phi_I + (face-adjacent) + (the 4 weighted nodes)), where W_In is the
+// sum of sigma over the cells that contain the edge I-n.  W and the diagonal
+// part are coefficient data, built once per coefficient update (k_node_edges).
+// sum_c sigma_c s_c is formed with shared partial sums: per node plane the
+// 2x2 phi sums at every cell position, per cell Q = sigma (lower + upper 2x2
+// sums), per node the 2x2 sum of Q over each of the two cell planes.  About
+// 20 FP64 operations per node instead of about 40 for the direct row.
 
-struct CPtr3 {
-    const double* p[3];
-};
-struct MPtr3n {
-    double* p[3];
-};
-
-// f_I = D_N(beta0 U)_I - sum_c (beta0 S)_c / 2^dim; partials {sum f, sum lump^2, sum f^2}
-template <int DIM>
-__global__ void k_node_rhs(NodeLevel<double> L, double h, CPtr3 U, const double* __restrict__ b0,
-                           const double* __restrict__ S, double* __restrict__ f, double* __restrict__ partials)
+// per node: cells around the +x, +y, +z edges and the scaled diagonal part
+__global__ void k_node_edges(NodeLevel<double> L, NodeEdges E)
 {
     const int total = L.Nx * L.Ny * L.Nz;
-    const double wdiv = 1.0 / ((1 << (DIM - 1)) * h), wl = 1.0 / (1 << DIM);
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        int i, j, k;
-        unflat(t, L.Nx, L.Ny, i, j, k);
-        double v = 0.0, lump = 0.0;
-        if (!node_dirichlet(L, i, j, k, DIM)) {
-            for (int c = 0; c < (1 << DIM); ++c) {
-                const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1, sz = (c & 4) ? 1 : -1;
-                int ci, cj, ck = 0;
-                if (!cell_ok(sx > 0 ? i : i - 1, L.nx, L.bc.lo[0], ci)) continue;
-                if (!cell_ok(sy > 0 ? j : j - 1, L.ny, L.bc.lo[1], cj)) continue;
-                if (DIM == 3 && !cell_ok(sz > 0 ? k : k - 1, L.nz, L.bc.lo[2], ck)) continue;
-                const size_t id = ((size_t)ck * L.ny + cj) * L.nx + ci;
-                const double bb = b0[id];
-                double dv = sx * U.p[0][id] + sy * U.p[1][id];
-                if (DIM == 3) dv += sz * U.p[2][id];
-                v += bb * dv * wdiv;
-                lump += bb * S[id] * wl;
-            }
-            v -= lump;
-        }
-        if (f) f[t] = v;
-        acc[0] += v;
-        acc[1] += lump * lump;
-        acc[2] += v * v;
-    }
-    block_reduce_store<3>(acc, partials);
-}
-
-// Tiled 3-D version of k_node_rhs.  Per z-plane the cells around a 32 x 8 node
-// tile get W = beta0 U (3 components) and beta0 S computed once into shared
-// memory; each node then forms D_N from signed sums of its 8 cells (additions
-// only) and the lumped source from their sum.  Cells outside a non-periodic
-// boundary hold 0 (natural boundary condition).  The fixed kRedBlocks grid
-// strides over (tile, z-chunk) work items, so the reduction stays deterministic.
-struct NodeRhsShared {
-    double w[2][4][kNTY + 1][kNTX + 1];  // [plane ring][Wx, Wy, Wz, beta0 S][y][x]
-};
-
-__global__ void __launch_bounds__(kNTX * kNTY)
-k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restrict__ b0, const double* __restrict__ S,
-                 double* __restrict__ f, double* __restrict__ partials, int kz)
-{
-    constexpr int TX = kNTX, TY = kNTY;
-    __shared__ NodeRhsShared sh;
-    const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
-    const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
-    const int tx_n = (Nx + TX - 1) / TX, ty_n = (Ny + TY - 1) / TY, tz_n = (Nz + kz - 1) / kz;
-    const int items = tx_n * ty_n * tz_n;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    const double wdiv = 1.0 / (4.0 * h), wl = 1.0 / 8.0;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int it = blockIdx.x; it < items; it += gridDim.x) {
-        const int bx = it % tx_n, by = (it / tx_n) % ty_n, bz = it / (tx_n * ty_n);
-        const int x0 = bx * TX, y0 = by * TY, z0 = bz * kz, z1 = min(z0 + kz, Nz);
-        auto load = [&](int c) {  // cell plane c -> ring slot
-            int gz = c;
-            bool zok = true;
-            if (gz < 0 || gz >= nz) { if (pz) gz = gz < 0 ? gz + nz : gz - nz; else zok = false; }
-            const int slot = (c + 2) & 1;
-            for (int q = tid; q < (TX + 1) * (TY + 1); q += TX * TY) {
-                const int ly = q / (TX + 1), lx = q - ly * (TX + 1);
-                int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-                bool ok = zok;
-                if (gx < 0 || gx >= nx) { if (px) gx = gx < 0 ? gx + nx : gx - nx; else ok = false; }
-                if (gy < 0 || gy >= ny) { if (py) gy = gy < 0 ? gy + ny : gy - ny; else ok = false; }
-                if (gx >= nx || gy >= ny) ok = false;
-                double w0 = 0.0, w1 = 0.0, w2 = 0.0, ws = 0.0;
-                if (ok) {
-                    const size_t id = ((size_t)gz * ny + gy) * nx + gx;
-                    const double bb = b0[id];
-                    w0 = bb * U.p[0][id];
-                    w1 = bb * U.p[1][id];
-                    w2 = bb * U.p[2][id];
-                    ws = bb * S[id];
-                }
-                sh.w[slot][0][ly][lx] = w0;
-                sh.w[slot][1][ly][lx] = w1;
-                sh.w[slot][2][ly][lx] = w2;
-                sh.w[slot][3][ly][lx] = ws;
-            }
-        };
-        load(z0 - 1);
-        for (int k = z0; k < z1; ++k) {
-            load(k);
-            __syncthreads();
-            const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
-            if (i < Nx && j < Ny) {
-                const size_t id = ((size_t)k * Ny + j) * Nx + i;
-                double v = 0.0, lump = 0.0;
-                if (!node_dirichlet(L, i, j, k, 3)) {
-                    const int lx = threadIdx.x, ly = threadIdx.y;  // cell (i-1, j-1) is at (lx, ly)
-                    const int sp = (k + 2) & 1, sm = (k + 1) & 1;   // cell planes k and k-1
-                    auto W = [&](int s, int q, int a, int b) { return sh.w[s][q][ly + b][lx + a]; };
-                    const double dx = (W(sp, 0, 1, 1) + W(sp, 0, 1, 0) + W(sm, 0, 1, 1) + W(sm, 0, 1, 0)) -
-                                      (W(sp, 0, 0, 1) + W(sp, 0, 0, 0) + W(sm, 0, 0, 1) + W(sm, 0, 0, 0));
-                    const double dy = (W(sp, 1, 1, 1) + W(sp, 1, 0, 1) + W(sm, 1, 1, 1) + W(sm, 1, 0, 1)) -
-                                      (W(sp, 1, 1, 0) + W(sp, 1, 0, 0) + W(sm, 1, 1, 0) + W(sm, 1, 0, 0));
-                    const double dz = (W(sp, 2, 1, 1) + W(sp, 2, 0, 1) + W(sp, 2, 1, 0) + W(sp, 2, 0, 0)) -
-                                      (W(sm, 2, 1, 1) + W(sm, 2, 0, 1) + W(sm, 2, 1, 0) + W(sm, 2, 0, 0));
-                    lump = ((W(sp, 3, 1, 1) + W(sp, 3, 0, 1)) + (W(sp, 3, 1, 0) + W(sp, 3, 0, 0)) +
-                            (W(sm, 3, 1, 1) + W(sm, 3, 0, 1)) + (W(sm, 3, 1, 0) + W(sm, 3, 0, 0))) * wl;
-                    v = (dx + dy + dz) * wdiv - lump;
-                }
-                if (f) f[id] = v;
-                acc[0] += v;
-                acc[1] += lump * lump;
-                acc[2] += v * v;
-            }
-            __syncthreads();
-        }
-    }
-    block_reduce_store<3>(acc, partials);
-}
-
-// U_c -= (sigma_c / beta0_c) G_N(phi)_c
-template <int DIM>
-__global__ void k_node_project(NodeLevel<double> L, double h, const double* __restrict__ phi,
-                               const double* __restrict__ b0, MPtr3n U)
-{
-    const int total = L.nx * L.ny * L.nz;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
     int i, j, k;
-    unflat(t, L.nx, L.ny, i, j, k);
-    double g[3] = {0.0, 0.0, 0.0};
-    for (int c = 0; c < (1 << DIM); ++c) {
-        const int a = node_nb(i + (c & 1), L.Nx, L.bc.lo[0]);
-        const int b = node_nb(j + ((c >> 1) & 1), L.Ny, L.bc.lo[1]);
-        const int e = DIM == 3 ? node_nb(k + ((c >> 2) & 1), L.Nz, L.bc.lo[2]) : 0;
-        const double v = phi[((size_t)e * L.Ny + b) * L.Nx + a];
-        g[0] += (c & 1) ? v : -v;
-        g[1] += (c & 2) ? v : -v;
-        if (DIM == 3) g[2] += (c & 4) ? v : -v;
+    unflat(t, L.Nx, L.Ny, i, j, k);
+    auto sg = [&](int a, int b, int c) -> double {
+        int ci, cj, ck;
+        if (!cell_ok(a, L.nx, L.bc.lo[0], ci) || !cell_ok(b, L.ny, L.bc.lo[1], cj) || !cell_ok(c, L.nz, L.bc.lo[2], ck))
+            return 0.0;
+        return L.sigma[((size_t)ck * L.ny + cj) * L.nx + ci];
+    };
+    const double s00 = sg(i - 1, j - 1, k - 1), s10 = sg(i, j - 1, k - 1), s01 = sg(i - 1, j, k - 1),
+                 s11 = sg(i, j, k - 1);
+    const double u00 = sg(i - 1, j - 1, k), u10 = sg(i, j - 1, k), u01 = sg(i - 1, j, k), u11 = sg(i, j, k);
+    E.w[0][t] = (s10 + s11) + (u10 + u11);   // x-edge (i, i+1): cells of column i
+    E.w[1][t] = (s01 + s11) + (u01 + u11);   // y-edge (j, j+1): cells of row j
+    E.w[2][t] = (u00 + u10) + (u01 + u11);   // z-edge (k, k+1): cells of plane k
+    const double S = ((s00 + s10) + (s01 + s11)) + ((u00 + u10) + (u01 + u11));
+    E.dq[t] = node_dirichlet(L, i, j, k, 3) ? 0.0 : -(5.0 / 12.0) * L.ih2 * S;
+}
+
+struct NodeSFShared {
+    double xs[4][kNTY + 2][kNTX + 2];  // phi node planes (ring), nodes x0-1 .. x0+32, y0-1 .. y0+8
+    double ss[2][kNTY + 1][kNTX + 1];  // sigma cell planes (ring), cells x0-1 .. x0+31, y0-1 .. y0+7
+    double q[kNTY + 1][kNTX + 1];      // Q of the current cell plane
+};
+
+// One fixed grid of kRedBlocks blocks; block b takes an equal contiguous share
+// of the (tile, node plane) sequence, tile-major, so the work is balanced to a
+// plane and the partial sums are deterministic.
+__global__ void __launch_bounds__(kNTX * kNTY, kRedBlocks / 152)
+k_node_resid64_sf(NodeLevel<double> L, NodeEdges E, const double* __restrict__ x, const double* __restrict__ b,
+                  float* __restrict__ r32, const double* __restrict__ scale, double* __restrict__ partials)
+{
+    constexpr int TX = kNTX, TY = kNTY, NT = TX * TY, QN = (TX + 1) * (TY + 1), XN = (TX + 2) * (TY + 2);
+    __shared__ NodeSFShared sh;
+    const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
+    const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
+    const int tx_n = (Nx + TX - 1) / TX, ty_n = (Ny + TY - 1) / TY;
+    const long long G = (long long)tx_n * ty_n * Nz;
+    const long long g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const double inv = 1.0 / *scale;
+    const double c12 = L.ih2 / 12.0;
+    const size_t nplane = (size_t)Nx * Ny, cplane = (size_t)nx * ny;
+    float acc = 0.f;
+
+    for (long long g = g0; g < g1;) {
+        const int tile = (int)(g / Nz);
+        const int z0 = (int)(g - (long long)tile * Nz);
+        const int z1 = (int)min((long long)Nz, (long long)z0 + (g1 - g));
+        g += z1 - z0;
+        const int x0 = (tile % tx_n) * TX, y0 = (tile / tx_n) * TY;
+
+        int ox[2], os[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int q = tid + e * NT;
+            ox[e] = -2;
+            if (q < XN) {
+                const int ly = q / (TX + 2), lx = q - ly * (TX + 2);
+                const int gx = npos(x0 - 1 + lx, Nx, px), gy = npos(y0 - 1 + ly, Ny, py);
+                ox[e] = (gx >= 0 && gy >= 0) ? gy * Nx + gx : -1;
+            }
+            os[e] = -2;
+            if (q < QN) {
+                const int ly = q / (TX + 1), lx = q - ly * (TX + 1);
+                const int gx = npos(x0 - 1 + lx, nx, px), gy = npos(y0 - 1 + ly, ny, py);
+                os[e] = (gx >= 0 && gy >= 0) ? gy * nx + gx : -1;
+            }
+        }
+        auto issue_node = [&](int p) {  // node plane p (wrapped when z is periodic, else 0 outside)
+            int pn = p;
+            bool ok = true;
+            if (pn < 0 || pn >= Nz) { if (pz) pn = pn < 0 ? pn + Nz : pn - Nz; else ok = false; }
+            const double* xp = x + (ok ? pn * nplane : 0);
+            double* dst = &sh.xs[(p + 4) & 3][0][0];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (ox[e] >= -1) ncp_async(dst + tid + e * NT, xp + (ox[e] < 0 ? 0 : ox[e]), ok && ox[e] >= 0, 8);
+        };
+        auto issue_cell = [&](int p) {  // cell plane p
+            int pc = p;
+            bool ok = true;
+            if (pc < 0 || pc >= nz) { if (pz) pc = pc < 0 ? pc + nz : pc - nz; else ok = false; }
+            const double* sp = L.sigma + (ok ? pc * cplane : 0);
+            double* dst = &sh.ss[(p + 2) & 1][0][0];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (os[e] >= -1) ncp_async(dst + tid + e * NT, sp + (os[e] < 0 ? 0 : os[e]), ok && os[e] >= 0, 8);
+        };
+        // 2x2 phi sum of node plane slot s at cell position q (x then y pairs)
+        auto bxy = [&](int s, int q) {
+            const int qy = q / (TX + 1), qx = q - qy * (TX + 1);
+            const double* r0 = &sh.xs[s][qy][qx];
+            const double* r1 = &sh.xs[s][qy + 1][qx];
+            return (r0[0] + r0[1]) + (r1[0] + r1[1]);
+        };
+        const int q0 = tid, q1 = tid + NT;  // owned cell positions (q1 valid when < QN)
+        double bp0, bp1 = 0.0;
+
+        // prologue: Q of cell plane z0-1 and its 2x2 sums
+        issue_node(z0 - 1);
+        issue_node(z0);
+        issue_cell(z0 - 1);
+        cp_async_commit_n();
+        cp_async_wait_n<0>();
+        __syncthreads();
+        issue_node(z0 + 1);
+        issue_cell(z0);
+        cp_async_commit_n();
+        {
+            const int sl = (z0 - 1 + 4) & 3, sc = (z0 + 4) & 3, sg = (z0 - 1 + 2) & 1;
+            const double a0 = bxy(sl, q0), c0 = bxy(sc, q0);
+            (&sh.q[0][0])[q0] = (&sh.ss[sg][0][0])[q0] * (a0 + c0);
+            bp0 = c0;
+            if (q1 < QN) {
+                const double a1 = bxy(sl, q1), c1 = bxy(sc, q1);
+                (&sh.q[0][0])[q1] = (&sh.ss[sg][0][0])[q1] * (a1 + c1);
+                bp1 = c1;
+            }
+        }
+        __syncthreads();
+        const int lx = threadIdx.x, ly = threadIdx.y;
+        double qb_prev = (sh.q[ly][lx] + sh.q[ly][lx + 1]) + (sh.q[ly + 1][lx] + sh.q[ly + 1][lx + 1]);
+        const int i = x0 + lx, j = y0 + ly;
+        const bool own = i < Nx && j < Ny;
+        // index of the -x / -y neighbour's edge weight (-1: no such edge)
+        const int im = i > 0 ? i - 1 : (px ? Nx - 1 : -1);
+        const int jm = j > 0 ? j - 1 : (py ? Ny - 1 : -1);
+        double wz_prev = 0.0;
+        if (own) {
+            const int km = z0 > 0 ? z0 - 1 : (pz ? Nz - 1 : -1);
+            if (km >= 0) wz_prev = E.w[2][(size_t)km * nplane + (size_t)j * Nx + i];
+        }
+
+        for (int k = z0; k < z1; ++k) {
+            cp_async_wait_n<0>();  // node plane k+1 and cell plane k have landed
+            __syncthreads();
+            if (k + 1 < z1) {
+                issue_node(k + 2);
+                issue_cell(k + 1);
+            }
+            cp_async_commit_n();
+            {
+                const int sn = (k + 1 + 4) & 3, sg = (k + 2) & 1;
+                const double c0 = bxy(sn, q0);
+                (&sh.q[0][0])[q0] = (&sh.ss[sg][0][0])[q0] * (bp0 + c0);
+                bp0 = c0;
+                if (q1 < QN) {
+                    const double c1 = bxy(sn, q1);
+                    (&sh.q[0][0])[q1] = (&sh.ss[sg][0][0])[q1] * (bp1 + c1);
+                    bp1 = c1;
+                }
+            }
+            __syncthreads();
+            const double qb = (sh.q[ly][lx] + sh.q[ly][lx + 1]) + (sh.q[ly + 1][lx] + sh.q[ly + 1][lx + 1]);
+            const double P = qb_prev + qb;
+            qb_prev = qb;
+            if (own) {
+                const size_t row = (size_t)k * nplane + (size_t)j * Nx;
+                const double wz = E.w[2][row + i];
+                float rs = 0.f;
+                if (!node_dirichlet(L, i, j, k, 3)) {
+                    const int sk = (k + 4) & 3, sm = (k + 3) & 3, sp = (k + 5) & 3;
+                    const double wxp = E.w[0][row + i];
+                    const double wxm = im >= 0 ? E.w[0][row + im] : 0.0;
+                    const double wyp = E.w[1][row + i];
+                    const double wym = jm >= 0 ? E.w[1][(size_t)k * nplane + (size_t)jm * Nx + i] : 0.0;
+                    const double xi = sh.xs[sk][ly + 1][lx + 1];
+                    double t = P;
+                    t = fmadd(-wxm, sh.xs[sk][ly + 1][lx], t);
+                    t = fmadd(-wxp, sh.xs[sk][ly + 1][lx + 2], t);
+                    t = fmadd(-wym, sh.xs[sk][ly][lx + 1], t);
+                    t = fmadd(-wyp, sh.xs[sk][ly + 2][lx + 1], t);
+                    t = fmadd(-wz_prev, sh.xs[sm][ly + 1][lx + 1], t);
+                    t = fmadd(-wz, sh.xs[sp][ly + 1][lx + 1], t);
+                    const double Lx = fmadd(E.dq[row + i], xi, t * c12);
+                    rs = f64_to_f32_rn((b[row + i] - Lx) * inv);
+                }
+                wz_prev = wz;
+                acc = fmaf(rs, rs, acc);
+                if (r32) r32[row + i] = rs;
+            }
+        }
+        __syncthreads();  // the next segment's prologue refills the rings
     }
-    const double w = L.sigma[t] / b0[t] / ((1 << (DIM - 1)) * h);
-    for (int d = 0; d < DIM; ++d) U.p[d][t] -= w * g[d];
+    double a[1] = {(double)acc};
+    block_reduce_store<1>(a, partials);
 }
 
 template <int DIM, typename T>
@@ -620,9 +579,6 @@ __global__ void k_node_zero_dirichlet(NodeLevel<T> L, T* __restrict__ x)
 
 // ================================================================ launchers
 
-static inline int nb(long long n) { return ceil_div(n, kThreads); }
-template <typename T>
-static inline long long nnod(const NodeLevel<T>& L) { return (long long)L.Nx * L.Ny * L.Nz; }
 
 void node_coarsen_sigma(int dim, const NodeLevel<double>& F, const NodeLevel<double>& C, double* sc, cudaStream_t s)
 {
@@ -669,6 +625,12 @@ static void launch_node_tiled(const NodeLevel<T>& L, const T* x, T* out, const T
 template <typename T>
 void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (tiled && node_v4_ok(dim, L, x, xo, b)) {
+            node_v4(L, x, xo, b, omega, false, s);
+            return;
+        }
+    }
     if (node_tiled_ok(dim, L, tiled)) {
         launch_node_tiled<T, false>(L, x, xo, b, omega, s);
     } else if (dim == 2) {
@@ -681,6 +643,12 @@ void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, 
 template <typename T>
 void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bool tiled, cudaStream_t s)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (tiled && node_v4_ok(dim, L, x, r, b)) {
+            node_v4(L, x, r, b, 0.f, true, s);
+            return;
+        }
+    }
     if (node_tiled_ok(dim, L, tiled)) {
         launch_node_tiled<T, true>(L, x, r, b, T(0), s);
     } else if (dim == 2) {
@@ -716,6 +684,17 @@ void node_resid64(int dim, const NodeLevel<double>& L, const double* x, const do
     }
 }
 
+void node_edges(const NodeLevel<double>& L, const NodeEdges& E, cudaStream_t s)
+{
+    MGP_LAUNCH(k_node_edges<<<nb(nnod(L)), kThreads, 0, s>>>(L, E));
+}
+
+void node_resid64_sf(const NodeLevel<double>& L, const NodeEdges& E, const double* x, const double* b, float* r32,
+                     const double* scale, double* partials, cudaStream_t s)
+{
+    MGP_LAUNCH(k_node_resid64_sf<<<kRedBlocks, dim3(kNTX, kNTY), 0, s>>>(L, E, x, b, r32, scale, partials));
+}
+
 void node_diag(int dim, const NodeLevel<double>& L, double* diag, cudaStream_t s)
 {
     if (dim == 2) MGP_LAUNCH(k_node_diag<2><<<nb(nnod(L)), kThreads, 0, s>>>(L, diag));
@@ -726,31 +705,6 @@ void node_apply64(int dim, const NodeLevel<double>& L, const double* x, double* 
 {
     if (dim == 2) MGP_LAUNCH(k_node_apply64<2><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, out));
     else MGP_LAUNCH(k_node_apply64<3><<<nb(nnod(L)), kThreads, 0, s>>>(L, x, out));
-}
-
-void node_rhs(int dim, const NodeLevel<double>& L, double h, const double* const U[3], const double* b0,
-              const double* S, double* f, double* partials, cudaStream_t s)
-{
-    CPtr3 u{{U[0], U[1], dim == 3 ? U[2] : nullptr}};
-    if (dim == 3 && L.Nx >= kNTX && L.Ny >= kNTY) {
-        // about 4 work items per block
-        const long long tiles = (long long)((L.Nx + kNTX - 1) / kNTX) * ((L.Ny + kNTY - 1) / kNTY);
-        int kz = (int)((tiles * L.Nz + kRedBlocks * 4 - 1) / (kRedBlocks * 4));
-        kz = kz < 4 ? 4 : kz;
-        MGP_LAUNCH(k_node_rhs_tiled<<<kRedBlocks, dim3(kNTX, kNTY), 0, s>>>(L, h, u, b0, S, f, partials, kz));
-        return;
-    }
-    if (dim == 2) MGP_LAUNCH(k_node_rhs<2><<<kRedBlocks, kThreads, 0, s>>>(L, h, u, b0, S, f, partials));
-    else MGP_LAUNCH(k_node_rhs<3><<<kRedBlocks, kThreads, 0, s>>>(L, h, u, b0, S, f, partials));
-}
-
-void node_project(int dim, const NodeLevel<double>& L, double h, const double* phi, const double* b0,
-                  double* const U[3], cudaStream_t s)
-{
-    MPtr3n u{{U[0], U[1], dim == 3 ? U[2] : nullptr}};
-    long long n = (long long)L.nx * L.ny * L.nz;
-    if (dim == 2) MGP_LAUNCH(k_node_project<2><<<nb(n), kThreads, 0, s>>>(L, h, phi, b0, u));
-    else MGP_LAUNCH(k_node_project<3><<<nb(n), kThreads, 0, s>>>(L, h, phi, b0, u));
 }
 
 template <typename T>

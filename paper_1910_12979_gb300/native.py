@@ -19,6 +19,7 @@ MG_LOC_CELL, MG_LOC_NODAL = 0, 1
 MG_PREC_FP64, MG_PREC_MIXED = 0, 1
 MG_FLAG_NO_FUSED = 1
 MG_FLAG_NO_GRAPH = 2
+MG_FLAG_SWEEP_PIPE = 4
 
 BC = {"periodic": MG_BC_PERIODIC, "neumann": MG_BC_NEUMANN, "dirichlet": MG_BC_DIRICHLET}
 
@@ -88,6 +89,9 @@ SIGNATURES = [
     ("mg_mac_constraint_noalloc", ctypes.c_int, [ctypes.POINTER(mg_geometry), ctypes.c_void_p * 3,
                                                  ctypes.POINTER(mg_beta0), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p]),
+    ("mg_convert_f64_to_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("mg_convert_f32_to_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("mg_reciprocal_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("mg_prof_enable", None, [ctypes.c_int]),
     ("mg_launch_count", ctypes.c_longlong, []),
     ("mg_prof_query", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
@@ -103,6 +107,7 @@ PROF_NAMES = {MG_PROF_CELL_SMOOTH_FINE: "cell_smooth_fine", MG_PROF_RESID64: "ce
 PROF_FP64_BOUND = {"cell_resid64", "node_resid64"}
 
 _lib = None
+_lib_gil = None   # the same library through ctypes.PyDLL: calls keep the GIL
 
 
 def library_path() -> str:
@@ -128,6 +133,10 @@ def load(build_if_needed: bool = True):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    global _lib_gil
+    _lib_gil = ctypes.PyDLL(path)
+    _lib_gil.mg_destroy.restype = None
+    _lib_gil.mg_destroy.argtypes = [ctypes.c_void_p]
     _lib = lib
     return lib
 
@@ -217,8 +226,12 @@ def mg_apply(h, phi_ptr, out_ptr):
     return check(load().mg_apply(h, ctypes.c_void_p(phi_ptr), ctypes.c_void_p(out_ptr)), "mg_apply")
 
 
-def mg_destroy(h):
-    load().mg_destroy(h)
+def mg_destroy(h, keep_gil=False):
+    """keep_gil: call without releasing the GIL.  Finalizers that run inside a
+    garbage collection must not release it: another thread could then start a
+    second collection over the same object lists."""
+    lib = load()
+    (_lib_gil if keep_gil else lib).mg_destroy(h)
 
 
 def mg_strerror(s):
@@ -227,6 +240,18 @@ def mg_strerror(s):
 
 def mg_last_error():
     return load().mg_last_error().decode()
+
+
+def mg_convert_f64_to_f32(x_ptr, y_ptr, n, stream=None):
+    check(load().mg_convert_f64_to_f32(x_ptr, y_ptr, n, stream), "mg_convert_f64_to_f32")
+
+
+def mg_convert_f32_to_f64(x_ptr, y_ptr, n, stream=None):
+    check(load().mg_convert_f32_to_f64(x_ptr, y_ptr, n, stream), "mg_convert_f32_to_f64")
+
+
+def mg_reciprocal_f64(x_ptr, y_ptr, n, stream=None):
+    check(load().mg_reciprocal_f64(x_ptr, y_ptr, n, stream), "mg_reciprocal_f64")
 
 
 def mg_launch_count():

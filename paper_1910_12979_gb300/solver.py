@@ -144,15 +144,15 @@ class ProjectionSolver:
         N.mg_apply(self.handle, _ptr(phi, "phi", self.vec_shape), _ptr(out, "out", self.vec_shape))
         return out
 
-    def close(self):
+    def close(self, _keep_gil=False):
         if self.handle is not None:
-            N.mg_destroy(self.handle)
+            N.mg_destroy(self.handle, keep_gil=_keep_gil)
             self.handle = None
         self.workspace = None
 
     def __del__(self):
         try:
-            self.close()
+            self.close(_keep_gil=True)   # may run inside a garbage collection on any thread
         except Exception:
             pass
 

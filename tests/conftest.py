@@ -18,3 +18,13 @@ def oracle():
     import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(autouse=True)
+def _collect_after_gpu_test(request):
+    """Finalise the solver handles a GPU test leaves behind on the main thread,
+    between tests, rather than inside a later test's worker threads."""
+    yield
+    if request.node.get_closest_marker("gpu") is not None:
+        import gc
+        gc.collect()

@@ -167,6 +167,36 @@ def test_nodal_projection_vs_oracle(oracle, prec):
     assert st["rel_constraint"] == pytest.approx(ref["constraint"], rel=1e-6)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,lo,hi", [((40, 24, 16), ("dirichlet",) * 3, ("dirichlet",) * 3),
+                                     ((36, 12, 8), ("periodic", "neumann", "neumann"),
+                                      ("periodic", "dirichlet", "neumann"))])
+def test_nodal_projection_ragged_tiles(oracle, prec, n, lo, hi):
+    """Nodal projection on grids whose node counts are not multiples of the
+    32 x 8 tiles (partial tiles, walls, Dirichlet faces and a periodic axis):
+    the tiled FP64 residual, right-hand side and update against the oracle."""
+    O = oracle
+    rng = np.random.default_rng(41)
+    geom = I.geometry(n, lo, hi)
+    geom["h"] = (1.0 / 40,) * 3
+    g = ogrid(O, geom)
+    sigma = np.exp(0.5 * rng.normal(size=g.cell_shape))
+    beta0 = np.exp(0.3 * rng.normal(size=g.cell_shape))
+    U = [rng.normal(size=g.cell_shape) for _ in range(3)]
+    S = rng.normal(size=g.cell_shape)
+    ref = O.nodal_project(g, sigma, beta0, U, S, tol=1e-14)
+    s = ProjectionSolver(geom, T(sigma), loc="nodal", prec=prec)
+    Ud = [T(u) for u in U]
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.project(Ud, T(beta0), T(S), phi=phi, tol=1e-12)
+    assert relerr(H(phi), ref["phi"]) <= TOL[prec]
+    for d in range(3):
+        assert relerr(H(Ud[d]), ref["U"][d]) <= TOL[prec]
+    assert np.all(H(phi)[g.dirichlet_node_mask()] == 0.0)
+    assert st["rel_constraint"] == pytest.approx(ref["constraint"], rel=1e-6)
+    s.close()
+
+
 def test_polytrope_dirichlet_projection(oracle):
     O = oracle
     p = I.polytrope_star(32, seed=5)
@@ -257,19 +287,25 @@ def test_not_converged_returns_best_phi():
     assert st["iters"] == 2 and st["rel_resid"] < 1e-2
 
 
-def test_fused_sweep_matches_two_pass():
-    """The fused one-launch red-black sweep and the two colour passes are the same
-    arithmetic: identical phi, bit for bit."""
-    p = I.stratified(64, seed=9, contrast=1e3, nodal=False)
+@pytest.mark.parametrize("bcs", [(("periodic", "periodic", "neumann"), ("periodic", "periodic", "dirichlet")),
+                                 (("neumann", "dirichlet", "periodic"), ("dirichlet", "neumann", "periodic"))])
+def test_fused_sweep_matches_two_pass(bcs):
+    """The vectorised colour passes, the pipelined one-launch sweep and the plain
+    colour passes are the same arithmetic: identical phi, bit for bit."""
+    p = I.stratified(64, seed=9, contrast=1e3, nodal=False, mac=False)
+    geom = I.geometry((64, 64, 64), bcs[0], bcs[1])
     f = T(np.random.default_rng(4).normal(size=(64, 64, 64)))
-    out = []
-    for flags in (0, N.MG_FLAG_NO_FUSED):
-        for prec in ("mixed", "fp64"):
-            s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec=prec, flags=flags)
+    if "dirichlet" not in bcs[0] + bcs[1]:
+        f -= f.mean()
+    for prec in ("mixed", "fp64"):
+        out = []
+        for flags in (0, N.MG_FLAG_SWEEP_PIPE, N.MG_FLAG_NO_FUSED):
+            s = ProjectionSolver(geom, T(p["sigma"]), loc="cell", prec=prec, flags=flags)
             phi = torch.zeros_like(f)
             s.solve(f, phi, tol=1e-11)
             out.append(phi)
-    assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[3])
+            s.close()
+        assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[2]), prec
 
 
 def test_tiled_nodal_matches_untiled():

@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--sweep", default="v4", choices=["v4", "pipe"],
                     help="FP32 cell smoother: two vectorised colour passes (v4) or the pipelined one-launch "
                          "sweep (pipe, MG_FLAG_SWEEP_PIPE)")
+    ap.add_argument("--inner-mac", type=int, default=0,
+                    help="FP32 V-cycles per FP64 refinement step of the MAC solve (0: the library's choice)")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed-precision step (no graph-path, FP64, e2e or CPU legs): the "
                          "command used for ncu captures")
@@ -229,7 +231,8 @@ def run_batch(args, dev, world, dist):
     with torch.cuda.stream(stream):
         for sp in specs:
             p = I.batch_problem(sp)
-            s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", stream=stream)
+            s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", stream=stream,
+                                 flags=N.MG_FLAG_AUTOTUNE)
             f = s.rhs([T(u) for u in p["U_mac"]], T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]])
             solvers.append(s)
             rhs.append(f)
@@ -237,6 +240,12 @@ def run_batch(args, dev, world, dist):
             cells += sp["n"] ** 3
     stream.synchronize()
     tols = [args.tol] * len(solvers)
+    kind_names = {0: "default", 1: "4-cell passes, 8 quads/row", 2: "4-cell passes, 16 quads/row",
+                  3: "4-cell passes, 32 quads/row", 4: "pipelined one-launch sweep"}
+    tuned = {}
+    for sp, s in zip(specs, solvers):
+        tuned.setdefault(f"{sp['n']}^3", [kind_names.get(N.mg_smoother_kind(s.handle, l), "?")
+                                          for l in range(8) if N.mg_smoother_kind(s.handle, l) >= 0])
 
     def step():
         with torch.cuda.stream(stream):
@@ -280,7 +289,8 @@ def run_batch(args, dev, world, dist):
             "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": {"workload": "batch of 64 MAC solves, n in {32,64,96,128} (seed 4), contrast log-uniform "
                                    "in [1e1,1e4], one graph launch per step", "cells": cells, "tol": args.tol,
-                       "l2": "aggregate inputs larger than L2"},
+                       "l2": "aggregate inputs larger than L2",
+                       "autotuned_smoother_per_level": tuned},
             "gpu_launches": launches,
             "iters": {"min": min(x["iters"] for x in st), "max": max(x["iters"] for x in st)},
             "worst_rel_resid": max(x["rel_resid"] for x in st),
@@ -509,7 +519,8 @@ def main():
 
     def make(prec):
         fl = N.MG_FLAG_SWEEP_PIPE if args.sweep == "pipe" else 0
-        mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream, flags=fl)
+        mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream, flags=fl,
+                               inner_cycles=args.inner_mac)
         nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream)
         phim = torch.zeros(mac.vec_shape, dtype=torch.float64, device=dev)
         phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)

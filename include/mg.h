@@ -146,6 +146,13 @@ typedef struct {
  * kernel (red and black of a sweep in one pass over memory) instead of two
  * vectorised colour passes (same arithmetic). */
 #define MG_FLAG_SWEEP_PIPE 4
+/* flags (mixed precision): at mg_setup, time the candidate smoother kernels of
+ * every FP32 level -- the vectorised passes with 8, 16 or 32 quads per block
+ * row and the shared-memory pipelined or tiled kernel -- and keep the fastest.
+ * All candidates compute the same arithmetic.  Choices are cached per grid and
+ * boundary kinds for the process; mg_smoother_kind reports them.  The timing
+ * synchronises the handle's stream during mg_setup. */
+#define MG_FLAG_AUTOTUNE 8
 
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
@@ -314,6 +321,11 @@ mg_status mg_convert_f32_to_f64(const float* x, double* y, size_t n, void* strea
  * coefficients, projection updates): Newton's method from a binary32 estimate,
  * within about one ulp of the quotient; arguments as above. */
 mg_status mg_reciprocal_f64(const double* x, double* y, size_t n, void* stream);
+
+/* The smoother kernel a level uses: 0 the default rule, 1..3 the vectorised
+ * passes with 8/16/32 quads per block row, 4 the shared-memory kernel;
+ * -1 for a null handle or a level out of range. */
+int mg_smoother_kind(const mg_handle* h, int level);
 
 void mg_prof_enable(int on);
 /* Total number of CUDA kernels this library has launched in the process. */

@@ -11,6 +11,8 @@
 // face) acting through the ghost value -phi_c.
 #include "mg_device.cuh"
 
+#include <type_traits>
+
 namespace mgp {
 
 // off and diag of row (i,j,k); phi(ii,jj,kk) returns the neighbour value.
@@ -247,36 +249,6 @@ __global__ void __launch_bounds__(128) k_resid_restrict_t(CellLevel<T> F, const 
         const int cnx = F.nx / 2, cny = F.ny / 2;
         bc[((size_t)blockIdx.z * cny + blockIdx.y) * cnx + (i >> 1)] = s2 * T(0.125);
     }
-}
-
-// coarse value seen from fine cell index i along one axis (linear interpolation):
-// parent P = i/2 with weight 3/4, the neighbour Q on the fine cell's side with 1/4;
-// beyond a boundary the neighbour is the periodic image, the mirror (Neumann) or
-// the odd reflection (Dirichlet).
-struct Lin1D {
-    int p, q;
-    float sq;  // sign applied to the value at q (+1, or -1 for the Dirichlet ghost)
-};
-
-__device__ __forceinline__ Lin1D lin1d(int i, int nc, int bclo, int bchi)
-{
-    Lin1D r;
-    r.p = i >> 1;
-    r.sq = 1.f;
-    if (i & 1) {
-        r.q = r.p + 1;
-        if (r.q >= nc) {
-            if (bchi == BCP) r.q = 0;
-            else { r.q = r.p; r.sq = (bchi == BCD) ? -1.f : 1.f; }
-        }
-    } else {
-        r.q = r.p - 1;
-        if (r.q < 0) {
-            if (bclo == BCP) r.q = nc - 1;
-            else { r.q = r.p; r.sq = (bclo == BCD) ? -1.f : 1.f; }
-        }
-    }
-    return r;
 }
 
 template <int DIM, typename T, int ORDER>
@@ -520,6 +492,12 @@ void cell_prolong_add(int dim, const CellLevel<T>& F, const CellLevel<T>& C, T* 
                       cudaStream_t s)
 {
     long long n = (long long)F.nx * F.ny * F.nz;
+    if constexpr (std::is_same<T, float>::value) {
+        if (order == 1 && cell_prolong_v4_ok(dim, F, xf)) {
+            cell_prolong_v4(F, C, xf, xc, s);
+            return;
+        }
+    }
     if (dim == 2) {
         if (order == 0) MGP_LAUNCH(k_prolong_add<2, T, 0><<<nb(n), kThreads, 0, s>>>(F, C, xf, xc));
         else MGP_LAUNCH(k_prolong_add<2, T, 1><<<nb(n), kThreads, 0, s>>>(F, C, xf, xc));

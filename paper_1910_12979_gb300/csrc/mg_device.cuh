@@ -118,4 +118,34 @@ __device__ __forceinline__ float recip<float>(float d) { return d != 0.f ? __fdi
 template <>
 __device__ __forceinline__ double recip<double>(double d) { return d != 0.0 ? 1.0 / d : 0.0; }
 
+// coarse value seen from fine cell index i along one axis (linear interpolation):
+// parent P = i/2 with weight 3/4, the neighbour Q on the fine cell's side with 1/4;
+// beyond a boundary the neighbour is the periodic image, the mirror (Neumann) or
+// the odd reflection (Dirichlet).
+struct Lin1D {
+    int p, q;
+    float sq;  // sign applied to the value at q (+1, or -1 for the Dirichlet ghost)
+};
+
+__device__ __forceinline__ Lin1D lin1d(int i, int nc, int bclo, int bchi)
+{
+    Lin1D r;
+    r.p = i >> 1;
+    r.sq = 1.f;
+    if (i & 1) {
+        r.q = r.p + 1;
+        if (r.q >= nc) {
+            if (bchi == BCP) r.q = 0;
+            else { r.q = r.p; r.sq = (bchi == BCD) ? -1.f : 1.f; }
+        }
+    } else {
+        r.q = r.p - 1;
+        if (r.q < 0) {
+            if (bclo == BCP) r.q = nc - 1;
+            else { r.q = r.p; r.sq = (bclo == BCD) ? -1.f : 1.f; }
+        }
+    }
+    return r;
+}
+
 }  // namespace mgp

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <chrono>
 #include <algorithm>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <type_traits>
@@ -115,6 +116,7 @@ struct Level {
     double* diag64;    // level 0: diagonal for the FP64 residual
     double* ew64[3];   // level 0, 3-D nodal: edge sigma sums of the sum-factorised residual
     double* dq64;      //   and its scaled diagonal part
+    int kind;          // smoother kernel chosen by the autotuner (0: the default rule)
     float* B32[3];
     double* sig64;
     float* sig32;
@@ -471,12 +473,14 @@ void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, i
     const double cells = (double)h->lev[l].ncell;
     T* t = lt<T>(h, l);
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    const int kind = h->lev[l].kind;   // 1..3: four-cell passes, 8/16/32 quads per block row; 4: pipelined
     if constexpr (std::is_same<T, float>::value) {
-        if (!(h->opt.flags & (MG_FLAG_NO_FUSED | MG_FLAG_SWEEP_PIPE)) && cell_gsrb_v4_ok(h->dim, V, x, b)) {
+        const bool pipe = kind == 4 || (kind == 0 && (h->opt.flags & MG_FLAG_SWEEP_PIPE));
+        if (!(h->opt.flags & MG_FLAG_NO_FUSED) && !pipe && cell_gsrb_v4_ok(h->dim, V, x, b)) {
             for (int k = 0; k < nu; ++k)
                 for (int color = 0; color < 2; ++color) {
                     const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * cells, s) : -1;
-                    cell_gsrb_v4(h->dim, V, x, b, color, s);
+                    cell_gsrb_v4(h->dim, V, x, b, color, s, kind >= 1 && kind <= 3 ? 4 << kind : 0);
                     prof_end(pr, s);
                 }
             return;
@@ -547,8 +551,8 @@ void node_smooth(mg_handle* h, int l, T* x, const T* b, int sweeps)
     for (int k = 0; k < sweeps; ++k) {
         const int pr = l == 0 ? prof_begin(MG_PROF_NODE_SMOOTH_FINE, 4.0 * sizeof(T) * h->lev[0].nvec, s) : -1;
         const bool tiled = !(h->opt.flags & MG_FLAG_NO_FUSED);
-        if (k % 2 == 0) node_jacobi<T>(h->dim, V, x, t, b, om, tiled, s);
-        else node_jacobi<T>(h->dim, V, t, x, b, om, tiled, s);
+        if (k % 2 == 0) node_jacobi<T>(h->dim, V, x, t, b, om, tiled, s, h->lev[l].kind);
+        else node_jacobi<T>(h->dim, V, t, x, b, om, tiled, s, h->lev[l].kind);
         prof_end(pr, s);
     }
     if (sweeps % 2 == 1) cudaMemcpyAsync(x, t, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
@@ -564,7 +568,8 @@ void vcycle_node(mg_handle* h, T* x0, const T* b0, bool zero_init)
     for (int l = 0; l < L - 1; ++l) {
         if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
         node_smooth<T>(h, l, X(l), Bv(l), h->opt.nu1);
-        node_resid<T>(dim, nview<T>(h, l), X(l), Bv(l), lr<T>(h, l), !(h->opt.flags & MG_FLAG_NO_FUSED), s);
+        node_resid<T>(dim, nview<T>(h, l), X(l), Bv(l), lr<T>(h, l), !(h->opt.flags & MG_FLAG_NO_FUSED), s,
+                      h->lev[l].kind);
         node_restrict<T>(dim, nview<T>(h, l), nview<T>(h, l + 1), lr<T>(h, l), lb<T>(h, l + 1), s);
     }
     dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
@@ -936,6 +941,95 @@ double now_ms()
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// ---- smoother kernel autotuner (MG_FLAG_AUTOTUNE)
+//
+// For every FP32 level but the coarsest, the candidate smoother kernels -- the
+// four-cell / four-node passes with 8, 16 or 32 quads per block row, and the
+// shared-memory pipelined (cells) or tiled (nodes) kernel where the level
+// allows it -- each run one sweep on the level's scratch vectors, timed with
+// CUDA events on the handle's stream (one untimed call, then the best of
+// three), and the fastest is kept in Level::kind.  All candidates compute the
+// same arithmetic, so the choice changes no result.  Choices are cached per
+// (location, dimension, grid, boundary kinds) for the process: handles of a
+// size already seen are not timed again.
+struct TuneKey {
+    int v[11];
+    bool operator<(const TuneKey& o) const { return std::lexicographical_compare(v, v + 11, o.v, o.v + 11); }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+mg_status autotune(mg_handle* h)
+{
+    if (h->prec != MG_PREC_MIXED || (h->opt.flags & MG_FLAG_NO_FUSED)) return MG_OK;
+    cudaStream_t s = h->stream;
+    const bool nodal = h->loc == MG_LOC_NODAL;
+    cudaEvent_t e0, e1;
+    MG_CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(MG_ERR_CUDA, "cudaEventCreate"); }
+    mg_status rc = MG_OK;
+    for (int l = 0; l < h->nlev - 1 && rc == MG_OK; ++l) {
+        Level& v = h->lev[l];
+        const TuneKey key{{h->loc, h->dim, v.n[0], v.n[1], v.n[2], h->bc.lo[0], h->bc.lo[1], h->bc.lo[2], h->bc.hi[0],
+                           h->bc.hi[1], h->bc.hi[2]}};
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) { v.kind = it->second; continue; }
+        }
+        float *x = v.x32, *t = v.t32, *b = v.b32;
+        if (!x || !t || !b) continue;
+        std::vector<int> cand;
+        if (nodal) {
+            if (node_v4_ok(h->dim, nview<float>(h, l), x, t, b))
+                for (int k = 1; k <= 3; ++k)
+                    if ((4 << k) <= v.N[0] / 4) cand.push_back(k);
+            if (h->dim == 3 && v.N[0] >= 32 && v.N[1] >= 8) cand.push_back(4);
+        } else {
+            const CellLevel<float> V = cview<float>(h, l);
+            if (cell_gsrb_v4_ok(h->dim, V, x, b))
+                for (int k = 1; k <= 3; ++k)
+                    if ((4 << k) <= v.n[0] / 4) cand.push_back(k);
+            if (cell_gsrb_fused_ok<float>(h->dim, V)) cand.push_back(4);
+        }
+        int best = 0;
+        if (cand.size() > 1) {
+            cudaMemsetAsync(x, 0, v.nvec * sizeof(float), s);
+            cudaMemsetAsync(b, 0, v.nvec * sizeof(float), s);
+            float best_ms = 1e30f;
+            for (int k : cand) {
+                v.kind = k;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 4 && rc == MG_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    if (nodal) node_smooth<float>(h, l, x, b, 1);
+                    else cell_smooth<float>(h, l, cview<float>(h, l), x, b, 1);
+                    cudaEventRecord(e1, s);
+                    float m = 0.f;
+                    const cudaError_t e = cudaEventSynchronize(e1);
+                    if (e != cudaSuccess || cudaEventElapsedTime(&m, e0, e1) != cudaSuccess) {
+                        rc = cuda_fail(e != cudaSuccess ? e : cudaErrorUnknown, "autotune timing");
+                        break;
+                    }
+                    if (rep > 0 && m < ms) ms = m;   // the first call is an untimed warm-up
+                }
+                if (ms < best_ms) { best_ms = ms; best = k; }
+            }
+            cudaMemsetAsync(x, 0, v.nvec * sizeof(float), s);
+            cudaMemsetAsync(b, 0, v.nvec * sizeof(float), s);
+            cudaMemsetAsync(t, 0, v.nvec * sizeof(float), s);
+        }
+        v.kind = rc == MG_OK ? best : 0;
+        if (rc == MG_OK) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = best;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -1027,6 +1121,7 @@ mg_status mg_setup(const mg_coeff* c, const mg_geometry* g, const mg_bc* bc, con
     // zero every work vector once (Dirichlet planes of nodal vectors stay 0)
     cudaMemsetAsync(h->ws, 0, need - 256, h->stream);
     rc = build_coefficients(h, c);
+    if (rc == MG_OK && (h->opt.flags & MG_FLAG_AUTOTUNE)) rc = autotune(h);
     if (rc != MG_OK) { mg_destroy(h); return rc; }
     *out = h;
     return MG_OK;
@@ -1295,6 +1390,12 @@ mg_status mg_reciprocal_f64(const double* x, double* y, size_t n, void* stream)
     vec_recip(y, x, n, (cudaStream_t)stream);
     MG_CK(cudaGetLastError());
     return MG_OK;
+}
+
+int mg_smoother_kind(const mg_handle* h, int level)
+{
+    if (!h || level < 0 || level >= h->nlev) return -1;
+    return h->lev[level].kind;
 }
 
 long long mg_launch_count(void) { return launch_count(); }

@@ -120,10 +120,10 @@ bool cell_gsrb_v4_ok(int dim, const CellLevel<float>& L, const float* x, const f
            (dim == 2 || a16(L.bz));
 }
 
-void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, int color, cudaStream_t s)
+void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, int color, cudaStream_t s, int bxw)
 {
     const int nq = L.nx / 4;
-    const int bx = nq >= 32 ? 32 : nq >= 16 ? 16 : nq >= 8 ? 8 : nq >= 4 ? 4 : 2;
+    const int bx = bxw > 0 ? bxw : nq >= 32 ? 32 : nq >= 16 ? 16 : nq >= 8 ? 8 : nq >= 4 ? 4 : 2;
     const dim3 block(bx, 256 / bx);
     const dim3 grid((nq + bx - 1) / bx, (L.ny + block.y - 1) / block.y, dim == 3 ? L.nz : 1);
     if (dim == 2) MGP_LAUNCH(k_gsrb_v4<2><<<grid, block, 0, s>>>(L, x, b, color));
@@ -135,10 +135,11 @@ void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, 
 namespace mgp {
 
 // Residual r = b - L x of a 3-D FP32 level averaged over the 2 x 2 x 2 children
-// of each coarse cell, vectorised like k_gsrb_v4: lane pairs of a warp own one
-// quad of four x-cells in two consecutive rows, the even lane in plane 2ck and
-// the odd lane in plane 2ck + 1.  Each lane sums its residuals over x-pairs and
-// then over its two rows; one shuffle adds the two planes; the even lane
+// of each coarse cell, vectorised like k_gsrb_v4.  A lane owns one quad of four
+// x-cells in one fine row and plane; the 32 lanes of a warp are 8 quads x 2
+// rows x 2 planes (lane bits: plane, row, quad), i.e. the children of 16
+// coarse cells.  A lane sums its residuals over x-pairs; one shuffle adds the
+// two rows, a second the two planes, and the lane of the lower row and plane
 // writes the two coarse cells.  The per-cell arithmetic and the order of the
 // sums (x pair, then y, then z) are those of k_resid_restrict_t, so the coarse
 // right-hand sides are identical.  Requirements: nx % 4 == 0, ny and nz even.
@@ -147,77 +148,74 @@ k_resid_restrict_v4(CellLevel<float> F, const float* __restrict__ x, const float
                     float* __restrict__ bc)
 {
     const int nx = F.nx, ny = F.ny, nz = F.nz;
-    const int lane = threadIdx.x;                      // 0..31
-    const int q = blockIdx.x * 16 + (lane >> 1);       // quad along x
-    const int cj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int lane = threadIdx.x;                              // 0..31
+    const int q = blockIdx.x * 8 + (lane >> 2);                // quad along x
+    const int cj = blockIdx.y * blockDim.y + threadIdx.y;      // coarse row
+    const int j = 2 * cj + ((lane >> 1) & 1);
     const int k = 2 * blockIdx.z + (lane & 1);
     const bool live = 4 * q < nx && 2 * cj < ny;
     const int i0 = 4 * q;
     const size_t plane = (size_t)nx * ny;
     const bool px = F.bc.lo[0] == BCP, py = F.bc.lo[1] == BCP, pz = F.bc.lo[2] == BCP;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float s0 = 0.f, s1 = 0.f;   // this lane's sums for coarse x-cells 2q and 2q + 1
+    float s0 = 0.f, s1 = 0.f;   // x-pair sums for coarse x-cells 2q and 2q + 1
     if (live) {
+        const size_t row = (size_t)k * plane + (size_t)j * nx;
+        const bool hym = j > 0 || py, hyp = j < ny - 1 || py;
         const bool hzm = k > 0 || pz, hzp = k < nz - 1 || pz;
-        float pair[2][2];
+        const size_t rym = j > 0 ? row - nx : row + (size_t)(ny - 1) * nx;
+        const size_t ryp = j < ny - 1 ? row + nx : row - (size_t)(ny - 1) * nx;
+        const size_t rzm = k > 0 ? row - plane : row + (size_t)(nz - 1) * plane;
+        const size_t rzp = k < nz - 1 ? row + plane : row - (size_t)(nz - 1) * plane;
+        const float4 xc = ld4(x + row + i0);
+        const float4 bb = ld4s(b + row + i0);
+        const float4 xym = hym ? ld4(x + rym + i0) : zero4;
+        const float4 xyp = hyp ? ld4(x + ryp + i0) : zero4;
+        const float4 xzm = hzm ? ld4(x + rzm + i0) : zero4;
+        const float4 xzp = hzp ? ld4(x + rzp + i0) : zero4;
+        float xl = 0.f, xr = 0.f;
+        if (i0 > 0) xl = x[row + i0 - 1];
+        else if (px) xl = x[row + nx - 1];
+        if (i0 + 4 < nx) xr = x[row + i0 + 4];
+        else if (px) xr = x[row];
+        const size_t fxb = ((size_t)k * ny + j) * (nx + 1) + i0;
+        const float fx[5] = {__ldcs(F.bx + fxb), __ldcs(F.bx + fxb + 1), __ldcs(F.bx + fxb + 2),
+                             __ldcs(F.bx + fxb + 3), __ldcs(F.bx + fxb + 4)};
+        const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
+        const float4 fyl = ld4s(F.by + fyb), fyh = ld4s(F.by + fyb + nx);
+        const float4 fzl = ld4s(F.bz + row + i0), fzh = ld4s(F.bz + row + plane + i0);
+        const float xs[6] = {xl, xc.x, xc.y, xc.z, xc.w, xr};
+        float r[4];
 #pragma unroll
-        for (int yy = 0; yy < 2; ++yy) {
-            const int j = 2 * cj + yy;
-            const size_t row = (size_t)k * plane + (size_t)j * nx;
-            const bool hym = j > 0 || py, hyp = j < ny - 1 || py;
-            const size_t rym = j > 0 ? row - nx : row + (size_t)(ny - 1) * nx;
-            const size_t ryp = j < ny - 1 ? row + nx : row - (size_t)(ny - 1) * nx;
-            const size_t rzm = k > 0 ? row - plane : row + (size_t)(nz - 1) * plane;
-            const size_t rzp = k < nz - 1 ? row + plane : row - (size_t)(nz - 1) * plane;
-            const float4 xc = ld4(x + row + i0);
-            const float4 bb = ld4s(b + row + i0);
-            const float4 xym = hym ? ld4(x + rym + i0) : zero4;
-            const float4 xyp = hyp ? ld4(x + ryp + i0) : zero4;
-            const float4 xzm = hzm ? ld4(x + rzm + i0) : zero4;
-            const float4 xzp = hzp ? ld4(x + rzp + i0) : zero4;
-            float xl = 0.f, xr = 0.f;
-            if (i0 > 0) xl = x[row + i0 - 1];
-            else if (px) xl = x[row + nx - 1];
-            if (i0 + 4 < nx) xr = x[row + i0 + 4];
-            else if (px) xr = x[row];
-            const size_t fxb = ((size_t)k * ny + j) * (nx + 1) + i0;
-            const float f0 = __ldcs(F.bx + fxb), f1 = __ldcs(F.bx + fxb + 1), f2 = __ldcs(F.bx + fxb + 2),
-                        f3 = __ldcs(F.bx + fxb + 3), f4 = __ldcs(F.bx + fxb + 4);
-            const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
-            const float4 fyl = ld4s(F.by + fyb), fyh = ld4s(F.by + fyb + nx);
-            const float4 fzl = ld4s(F.bz + row + i0), fzh = ld4s(F.bz + row + plane + i0);
-            const float fx[5] = {f0, f1, f2, f3, f4};
-            const float xs[6] = {xl, xc.x, xc.y, xc.z, xc.w, xr};
-            float r[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int i = i0 + p;
-                float off = 0.f, dg = 0.f;
-                const float bxl = fx[p], bxh = fx[p + 1];
-                if (i > 0 || px) { off = fmadd(bxl, xs[p], off); dg += bxl; }
-                else if (F.bc.lo[0] == BCD) { dg += 2.f * bxl; }
-                if (i < nx - 1 || px) { off = fmadd(bxh, xs[p + 2], off); dg += bxh; }
-                else if (F.bc.hi[0] == BCD) { dg += 2.f * bxh; }
-                const float byl = el(fyl, p), byh = el(fyh, p);
-                if (hym) { off = fmadd(byl, el(xym, p), off); dg += byl; }
-                else if (F.bc.lo[1] == BCD) { dg += 2.f * byl; }
-                if (hyp) { off = fmadd(byh, el(xyp, p), off); dg += byh; }
-                else if (F.bc.hi[1] == BCD) { dg += 2.f * byh; }
-                const float bzl = el(fzl, p), bzh = el(fzh, p);
-                if (hzm) { off = fmadd(bzl, el(xzm, p), off); dg += bzl; }
-                else if (F.bc.lo[2] == BCD) { dg += 2.f * bzl; }
-                if (hzp) { off = fmadd(bzh, el(xzp, p), off); dg += bzh; }
-                else if (F.bc.hi[2] == BCD) { dg += 2.f * bzh; }
-                r[p] = el(bb, p) - fmadd(-dg, xs[p + 1], off);
-            }
-            pair[yy][0] = r[0] + r[1];
-            pair[yy][1] = r[2] + r[3];
+        for (int p = 0; p < 4; ++p) {
+            const int i = i0 + p;
+            float off = 0.f, dg = 0.f;
+            const float bxl = fx[p], bxh = fx[p + 1];
+            if (i > 0 || px) { off = fmadd(bxl, xs[p], off); dg += bxl; }
+            else if (F.bc.lo[0] == BCD) { dg += 2.f * bxl; }
+            if (i < nx - 1 || px) { off = fmadd(bxh, xs[p + 2], off); dg += bxh; }
+            else if (F.bc.hi[0] == BCD) { dg += 2.f * bxh; }
+            const float byl = el(fyl, p), byh = el(fyh, p);
+            if (hym) { off = fmadd(byl, el(xym, p), off); dg += byl; }
+            else if (F.bc.lo[1] == BCD) { dg += 2.f * byl; }
+            if (hyp) { off = fmadd(byh, el(xyp, p), off); dg += byh; }
+            else if (F.bc.hi[1] == BCD) { dg += 2.f * byh; }
+            const float bzl = el(fzl, p), bzh = el(fzh, p);
+            if (hzm) { off = fmadd(bzl, el(xzm, p), off); dg += bzl; }
+            else if (F.bc.lo[2] == BCD) { dg += 2.f * bzl; }
+            if (hzp) { off = fmadd(bzh, el(xzp, p), off); dg += bzh; }
+            else if (F.bc.hi[2] == BCD) { dg += 2.f * bzh; }
+            r[p] = el(bb, p) - fmadd(-dg, xs[p + 1], off);
         }
-        s0 = pair[0][0] + pair[1][0];
-        s1 = pair[0][1] + pair[1][1];
+        s0 = r[0] + r[1];
+        s1 = r[2] + r[3];
     }
+    // rows: the lane of row 2cj adds its partner's (row 2cj + 1) sums
+    s0 = s0 + __shfl_xor_sync(0xffffffffu, s0, 2);
+    s1 = s1 + __shfl_xor_sync(0xffffffffu, s1, 2);
+    // planes
     const float o0 = __shfl_xor_sync(0xffffffffu, s0, 1), o1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-    if (live && (lane & 1) == 0) {
+    if (live && (lane & 3) == 0) {
         const int cnx = nx / 2, cny = ny / 2;
         float2 v;
         v.x = (s0 + o0) * 0.125f;
@@ -237,8 +235,62 @@ void cell_resid_restrict_v4(const CellLevel<float>& F, const float* x, const flo
 {
     const int nq = F.nx / 4, cny = F.ny / 2, cnz = F.nz / 2;
     const dim3 block(32, 8);
-    const dim3 grid((nq + 15) / 16, (cny + 7) / 8, cnz);
+    const dim3 grid((nq + 7) / 8, (cny + 7) / 8, cnz);
     MGP_LAUNCH(k_resid_restrict_v4<<<grid, block, 0, s>>>(F, x, b, bc));
+}
+
+}  // namespace mgp
+
+namespace mgp {
+
+// Linear prolongation and correction, x_f += P x_c, four fine cells of a row per
+// thread (one 16-byte read-modify-write); the coarse values come through L1.
+// Same weights and order of operations as k_prolong_add<3, float, 1>.
+__global__ void __launch_bounds__(256)
+k_prolong_add_v4(CellLevel<float> F, CellLevel<float> C, float* __restrict__ xf, const float* __restrict__ xc)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (4 * q >= F.nx || j >= F.ny) return;
+    const int i0 = 4 * q;
+    const Lin1D ly = lin1d(j, C.ny, F.bc.lo[1], F.bc.hi[1]);
+    const Lin1D lz = lin1d(k, C.nz, F.bc.lo[2], F.bc.hi[2]);
+    const size_t cpl = (size_t)C.nx * C.ny;
+    const float* rpp = xc + lz.p * cpl + (size_t)ly.p * C.nx;   // (y p, z p)
+    const float* rqp = xc + lz.p * cpl + (size_t)ly.q * C.nx;   // (y q, z p)
+    const float* rpq = xc + lz.q * cpl + (size_t)ly.p * C.nx;   // (y p, z q)
+    const float* rqq = xc + lz.q * cpl + (size_t)ly.q * C.nx;   // (y q, z q)
+    const float w1 = 0.75f, w2 = 0.25f;
+    float4 v = *reinterpret_cast<const float4*>(xf + ((size_t)k * F.ny + j) * F.nx + i0);
+    float add[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const Lin1D lx = lin1d(i0 + p, C.nx, F.bc.lo[0], F.bc.hi[0]);
+        auto plane = [&](const float* ra, const float* rb) {
+            return w1 * (w1 * ra[lx.p] + w2 * lx.sq * ra[lx.q]) + w2 * ly.sq * (w1 * rb[lx.p] + w2 * lx.sq * rb[lx.q]);
+        };
+        add[p] = w1 * plane(rpp, rqp) + w2 * lz.sq * plane(rpq, rqq);
+    }
+    v.x += add[0];
+    v.y += add[1];
+    v.z += add[2];
+    v.w += add[3];
+    *reinterpret_cast<float4*>(xf + ((size_t)k * F.ny + j) * F.nx + i0) = v;
+}
+
+bool cell_prolong_v4_ok(int dim, const CellLevel<float>& F, const float* xf)
+{
+    return dim == 3 && F.nx % 4 == 0 && F.nx >= 8 && ((uintptr_t)xf & 15) == 0;
+}
+
+void cell_prolong_v4(const CellLevel<float>& F, const CellLevel<float>& C, float* xf, const float* xc, cudaStream_t s)
+{
+    const int nq = F.nx / 4;
+    const int bx = nq >= 32 ? 32 : nq >= 16 ? 16 : nq >= 8 ? 8 : nq >= 4 ? 4 : 2;
+    const dim3 block(bx, 256 / bx);
+    const dim3 grid((nq + bx - 1) / bx, (F.ny + block.y - 1) / block.y, F.nz);
+    MGP_LAUNCH(k_prolong_add_v4<<<grid, block, 0, s>>>(F, C, xf, xc));
 }
 
 }  // namespace mgp

@@ -95,10 +95,15 @@ bool cell_gsrb_fused_ok(int dim, const CellLevel<T>& L);
 // one colour pass, four cells per thread with 16-byte accesses (FP32, nx % 4 == 0,
 // 16-byte aligned x, b and face arrays); same arithmetic as cell_gsrb
 bool cell_gsrb_v4_ok(int dim, const CellLevel<float>& L, const float* x, const float* b);
-void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, int color, cudaStream_t s);
+// bxw: quads per block row (8, 16 or 32; 0 picks by the level's width)
+void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, int color, cudaStream_t s,
+                  int bxw = 0);
 // 3-D residual + restriction, vectorised like cell_gsrb_v4; same results as cell_resid_restrict
 bool cell_resid_restrict_v4_ok(int dim, const CellLevel<float>& F, const float* x, const float* b, const float* bc);
 void cell_resid_restrict_v4(const CellLevel<float>& F, const float* x, const float* b, float* bc, cudaStream_t s);
+// 3-D linear prolongation and correction, four fine cells per thread
+bool cell_prolong_v4_ok(int dim, const CellLevel<float>& F, const float* xf);
+void cell_prolong_v4(const CellLevel<float>& F, const CellLevel<float>& C, float* xf, const float* xc, cudaStream_t s);
 template <typename T>
 void cell_gsrb_sweep(int dim, const CellLevel<T>& L, const T* xin, T* xout, const T* b, cudaStream_t s);
 template <typename T>
@@ -126,10 +131,14 @@ void node_coarsen_sigma(int dim, const NodeLevel<double>& F, const NodeLevel<dou
 void node_invdiag(int dim, const NodeLevel<double>& L, double* invd, cudaStream_t s);
 void node_diag(int dim, const NodeLevel<double>& L, double* diag, cudaStream_t s);
 // tiled: allow the shared-memory tiled kernel (3-D levels of at least 32 x 8 nodes)
+// kind: 0 the default choice; 1..3 the four-node kernel with 8/16/32 quads per
+// block row; 4 the shared-memory tiled kernel (when the level allows each)
 template <typename T>
-void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s);
+void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s,
+                 int kind = 0);
 template <typename T>
-void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bool tiled, cudaStream_t s);
+void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bool tiled, cudaStream_t s,
+                int kind = 0);
 template <typename T>
 void node_restrict(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, const T* rf, T* bc, cudaStream_t s);
 template <typename T>
@@ -138,7 +147,9 @@ void node_prolong_add(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, T* 
 // four nodes per thread (same results as the plain kernels)
 bool node_v4_ok(int dim, const NodeLevel<float>& L, const float* x, const float* out, const float* b);
 void node_v4(const NodeLevel<float>& L, const float* x, float* out, const float* b, float omega, bool resid,
-             cudaStream_t s);
+             cudaStream_t s, int bxw = 0);
+bool node_prolong_v4_ok(int dim, const NodeLevel<float>& F, const float* xf);
+void node_prolong_v4(const NodeLevel<float>& F, const NodeLevel<float>& C, float* xf, const float* xc, cudaStream_t s);
 void node_resid64(int dim, const NodeLevel<double>& L, const double* x, const double* b, float* r32,
                   const double* scale, double* partials, cudaStream_t s);
 // Level-0 data of the sum-factorised FP64 nodal residual (3-D): per node the

@@ -623,11 +623,12 @@ static void launch_node_tiled(const NodeLevel<T>& L, const T* x, T* out, const T
 }
 
 template <typename T>
-void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s)
+void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s,
+                 int kind)
 {
     if constexpr (std::is_same<T, float>::value) {
-        if (tiled && node_v4_ok(dim, L, x, xo, b)) {
-            node_v4(L, x, xo, b, omega, false, s);
+        if (tiled && kind != 4 && node_v4_ok(dim, L, x, xo, b)) {
+            node_v4(L, x, xo, b, omega, false, s, kind >= 1 && kind <= 3 ? 4 << kind : 0);
             return;
         }
     }
@@ -641,11 +642,11 @@ void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, 
 }
 
 template <typename T>
-void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bool tiled, cudaStream_t s)
+void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bool tiled, cudaStream_t s, int kind)
 {
     if constexpr (std::is_same<T, float>::value) {
-        if (tiled && node_v4_ok(dim, L, x, r, b)) {
-            node_v4(L, x, r, b, 0.f, true, s);
+        if (tiled && kind != 4 && node_v4_ok(dim, L, x, r, b)) {
+            node_v4(L, x, r, b, 0.f, true, s, kind >= 1 && kind <= 3 ? 4 << kind : 0);
             return;
         }
     }
@@ -668,6 +669,12 @@ void node_restrict(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, const 
 template <typename T>
 void node_prolong_add(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, T* xf, const T* xc, cudaStream_t s)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (node_prolong_v4_ok(dim, F, xf)) {
+            node_prolong_v4(F, C, xf, xc, s);
+            return;
+        }
+    }
     if (dim == 2) MGP_LAUNCH(k_node_prolong<2, T><<<nb(nnod(F)), kThreads, 0, s>>>(F, C, xf, xc));
     else MGP_LAUNCH(k_node_prolong<3, T><<<nb(nnod(F)), kThreads, 0, s>>>(F, C, xf, xc));
 }
@@ -723,12 +730,13 @@ void node_zero_dirichlet(int dim, const NodeLevel<T>& L, T* x, cudaStream_t s)
 }
 
 template void node_jacobi<float>(int, const NodeLevel<float>&, const float*, float*, const float*, float, bool,
-                                 cudaStream_t);
+                                 cudaStream_t, int);
 template void node_jacobi<double>(int, const NodeLevel<double>&, const double*, double*, const double*, double, bool,
-                                  cudaStream_t);
-template void node_resid<float>(int, const NodeLevel<float>&, const float*, const float*, float*, bool, cudaStream_t);
+                                  cudaStream_t, int);
+template void node_resid<float>(int, const NodeLevel<float>&, const float*, const float*, float*, bool, cudaStream_t,
+                                int);
 template void node_resid<double>(int, const NodeLevel<double>&, const double*, const double*, double*, bool,
-                                 cudaStream_t);
+                                 cudaStream_t, int);
 template void node_restrict<float>(int, const NodeLevel<float>&, const NodeLevel<float>&, const float*, float*,
                                    cudaStream_t);
 template void node_restrict<double>(int, const NodeLevel<double>&, const NodeLevel<double>&, const double*, double*,

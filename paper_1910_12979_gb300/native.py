@@ -20,6 +20,7 @@ MG_PREC_FP64, MG_PREC_MIXED = 0, 1
 MG_FLAG_NO_FUSED = 1
 MG_FLAG_NO_GRAPH = 2
 MG_FLAG_SWEEP_PIPE = 4
+MG_FLAG_AUTOTUNE = 8
 
 BC = {"periodic": MG_BC_PERIODIC, "neumann": MG_BC_NEUMANN, "dirichlet": MG_BC_DIRICHLET}
 
@@ -92,6 +93,7 @@ SIGNATURES = [
     ("mg_convert_f64_to_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("mg_convert_f32_to_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("mg_reciprocal_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("mg_smoother_kind", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mg_prof_enable", None, [ctypes.c_int]),
     ("mg_launch_count", ctypes.c_longlong, []),
     ("mg_prof_query", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
@@ -252,6 +254,10 @@ def mg_convert_f32_to_f64(x_ptr, y_ptr, n, stream=None):
 
 def mg_reciprocal_f64(x_ptr, y_ptr, n, stream=None):
     check(load().mg_reciprocal_f64(x_ptr, y_ptr, n, stream), "mg_reciprocal_f64")
+
+
+def mg_smoother_kind(h, level):
+    return int(load().mg_smoother_kind(h, level))
 
 
 def mg_launch_count():

@@ -64,6 +64,8 @@ def parse():
                          "sweep (pipe, MG_FLAG_SWEEP_PIPE)")
     ap.add_argument("--inner-mac", type=int, default=0,
                     help="FP32 V-cycles per FP64 refinement step of the MAC solve (0: the library's choice)")
+    ap.add_argument("--coarsest", type=int, default=0,
+                    help="largest coarsest-level size handed to the dense solve (0: the library's default)")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed-precision step (no graph-path, FP64, e2e or CPU legs): the "
                          "command used for ncu captures")
@@ -232,7 +234,7 @@ def run_batch(args, dev, world, dist):
         for sp in specs:
             p = I.batch_problem(sp)
             s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", stream=stream,
-                                 flags=N.MG_FLAG_AUTOTUNE)
+                                 flags=N.MG_FLAG_AUTOTUNE | N.MG_FLAG_ZERO_GUESS)
             f = s.rhs([T(u) for u in p["U_mac"]], T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]])
             solvers.append(s)
             rhs.append(f)
@@ -379,7 +381,8 @@ def run_config1(args, dev):
     res = {}
     for prec in ("fp64", "mixed"):
         with torch.cuda.stream(stream):
-            s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec=prec, stream=stream)
+            s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec=prec, stream=stream,
+                                 flags=N.MG_FLAG_ZERO_GUESS)
             f = T(p["f"])
             phi = torch.zeros_like(f)
 
@@ -421,8 +424,8 @@ def run_config2(args, dev):
         Um, Uc = [u.clone() for u in U0m], [u.clone() for u in U0c]
         out = {}
         for prec in ("fp64", "mixed"):
-            mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream)
-            nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream)
+            mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream, flags=N.MG_FLAG_ZERO_GUESS)
+            nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream, flags=N.MG_FLAG_ZERO_GUESS)
             phim = torch.zeros_like(sigma)
             phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)
 
@@ -432,8 +435,6 @@ def run_config2(args, dev):
                     nod.update_coeff(sigma)
                     for a, b in zip(Um + Uc, U0m + U0c):
                         a.copy_(b)
-                    phim.zero_()
-                    phin.zero_()
                     a = mac.project(Um, beta0, S, beta0_face=b0f, phi=phim, tol=args.tol, allow_not_converged=True)
                     b = nod.project(Uc, beta0, S, phi=phin, tol=args.tol, allow_not_converged=True)
                     return a, b
@@ -518,10 +519,13 @@ def main():
     stream.synchronize()
 
     def make(prec):
-        fl = N.MG_FLAG_SWEEP_PIPE if args.sweep == "pipe" else 0
+        # every step starts the solves from phi = 0 (the step zeroes phi anyway)
+        fl = N.MG_FLAG_ZERO_GUESS | (N.MG_FLAG_SWEEP_PIPE if args.sweep == "pipe" else 0)
+        cm = {"coarsest_max": args.coarsest} if args.coarsest > 0 else {}
         mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream, flags=fl,
-                               inner_cycles=args.inner_mac)
-        nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream)
+                               inner_cycles=args.inner_mac, **cm)
+        nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream, flags=N.MG_FLAG_ZERO_GUESS,
+                               **cm)
         phim = torch.zeros(mac.vec_shape, dtype=torch.float64, device=dev)
         phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)
         return mac, nod, phim, phin
@@ -537,8 +541,6 @@ def main():
                 a.copy_(b)
             for a, b in zip(Uc, U0c):
                 a.copy_(b)
-            phim.zero_()
-            phin.zero_()
             stats["mac"] = mac.project(Um, beta0, S, beta0_face=b0f, phi=phim, tol=args.tol,
                                        allow_not_converged=True)
             stats["nodal"] = nod.project(Uc, beta0, S, phi=phin, tol=args.tol, allow_not_converged=True)

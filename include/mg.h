@@ -115,13 +115,13 @@ typedef struct {
  *   nu1, nu2      pre/post smoothing sweeps (red-black Gauss-Seidel for cells,
  *                 damped Jacobi for nodes)
  *   max_iters     cap on V-cycles (FP64) or refinement steps (mixed)
- *   coarsest_max  stop coarsening once a level has at most this many cells
+ *   coarsest_max  stop coarsening once a level has at most this many cells (default 8)
  *   interp_order  cell prolongation: 0 piecewise constant, 1 linear
  *   omega         nodal Jacobi damping
  *   stream        cudaStream_t (NULL: the legacy default stream)
  *   flags         MG_FLAG_* bits (0 by default)
  *   inner_cycles  mixed precision: FP32 V-cycles per FP64 refinement step
- *                 (0: automatic, 1 for cells and 2 for nodes) */
+ *                 (0: automatic, 2) */
 typedef struct {
     int prec;
     int nu1;
@@ -153,6 +153,10 @@ typedef struct {
  * boundary kinds for the process; mg_smoother_kind reports them.  The timing
  * synchronises the handle's stream during mg_setup. */
 #define MG_FLAG_AUTOTUNE 8
+/* flags: solves ignore phi's input and start from phi = 0; the first residual
+ * is then f itself and costs no operator application (one FP64 residual fewer
+ * per solve).  phi is still written with the solution. */
+#define MG_FLAG_ZERO_GUESS 16
 
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||

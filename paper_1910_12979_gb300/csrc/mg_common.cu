@@ -66,23 +66,78 @@ __global__ void k_copy64(double* __restrict__ d, const double* __restrict__ a, s
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
         d[t] = a[t];
 }
+// V: four elements per step with 16-byte accesses (all pointers 16-byte aligned), then the tail
+template <bool V>
 __global__ void k_to32(float* __restrict__ d, const double* __restrict__ a, size_t n)
 {
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-        d[t] = f64_to_f32_rn(a[t]);
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+    size_t done = 0;
+    if (V) {
+        const size_t n4 = n / 4;
+        for (size_t t = t0; t < n4; t += st) {
+            const double2 p = reinterpret_cast<const double2*>(a)[2 * t];
+            const double2 q = reinterpret_cast<const double2*>(a)[2 * t + 1];
+            reinterpret_cast<float4*>(d)[t] =
+                make_float4(f64_to_f32_rn(p.x), f64_to_f32_rn(p.y), f64_to_f32_rn(q.x), f64_to_f32_rn(q.y));
+        }
+        done = 4 * n4;
+    }
+    for (size_t t = done + t0; t < n; t += st) d[t] = f64_to_f32_rn(a[t]);
 }
+template <bool V>
 __global__ void k_axpy32(double* __restrict__ phi, const float* __restrict__ e, const double* __restrict__ scale,
                          size_t n)
 {
     const double s = *scale;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-        phi[t] = fmadd(s, f32_to_f64(e[t]), phi[t]);
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+    size_t done = 0;
+    if (V) {
+        const size_t n4 = n / 4;
+        for (size_t t = t0; t < n4; t += st) {
+            const float4 ev = reinterpret_cast<const float4*>(e)[t];
+            double2* pp = reinterpret_cast<double2*>(phi) + 2 * t;
+            double2 p = pp[0], q = pp[1];
+            p.x = fmadd(s, f32_to_f64(ev.x), p.x);
+            p.y = fmadd(s, f32_to_f64(ev.y), p.y);
+            q.x = fmadd(s, f32_to_f64(ev.z), q.x);
+            q.y = fmadd(s, f32_to_f64(ev.w), q.y);
+            pp[0] = p;
+            pp[1] = q;
+        }
+        done = 4 * n4;
+    }
+    for (size_t t = done + t0; t < n; t += st) phi[t] = fmadd(s, f32_to_f64(e[t]), phi[t]);
 }
+static inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 __global__ void k_to64(double* __restrict__ d, const float* __restrict__ a, size_t n)
 {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
         d[t] = f32_to_f64(a[t]);
+}
+
+// Residual of a zero initial guess: r = f, so the FP32 copy r / scale and its
+// squared norm need no operator application.  Same traversal, grid and
+// accumulation order as the cell FP64 residual kernel, whose result it equals
+// bit for bit when x = 0.
+__global__ void k_init_zero_guess(const double* __restrict__ f, float* __restrict__ r32,
+                                  const double* __restrict__ scale, double* __restrict__ partials, int n)
+{
+    const double inv = 1.0 / *scale;
+    float acc = 0.f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const float rs = f64_to_f32_rn(f[t] * inv);
+        acc = fmaf(rs, rs, acc);
+        if (r32) r32[t] = rs;
+    }
+    double a[1] = {(double)acc};
+    block_reduce_store<1>(a, partials);
+}
+
+void vec_init_zero_guess(const double* f, float* r32, const double* scale, double* partials, size_t n,
+                         cudaStream_t s)
+{
+    MGP_LAUNCH(k_init_zero_guess<<<kRedBlocks, kThreads, 0, s>>>(f, r32, scale, partials, (int)n));
 }
 
 __global__ void k_recip(double* __restrict__ d, const double* __restrict__ a, size_t n)
@@ -107,13 +162,15 @@ void vec_copy_f64(double* dst, const double* src, size_t n, cudaStream_t s)
 }
 void vec_to_f32(float* dst, const double* src, size_t n, cudaStream_t s)
 {
-    MGP_LAUNCH(k_to32<<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
+    if (al16(dst) && al16(src)) MGP_LAUNCH(k_to32<true><<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
+    else MGP_LAUNCH(k_to32<false><<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
 }
 void vec_zero_f32(float* v, size_t n, cudaStream_t s) { cudaMemsetAsync(v, 0, n * sizeof(float), s); }
 void vec_zero_f64(double* v, size_t n, cudaStream_t s) { cudaMemsetAsync(v, 0, n * sizeof(double), s); }
 void vec_axpy_f32(double* phi, const float* e, const double* scale, size_t n, cudaStream_t s)
 {
-    MGP_LAUNCH(k_axpy32<<<kRedBlocks, kThreads, 0, s>>>(phi, e, scale, n));
+    if (al16(phi) && al16(e)) MGP_LAUNCH(k_axpy32<true><<<kRedBlocks, kThreads, 0, s>>>(phi, e, scale, n));
+    else MGP_LAUNCH(k_axpy32<false><<<kRedBlocks, kThreads, 0, s>>>(phi, e, scale, n));
 }
 
 __global__ void k_fscale(DevScalars* d)

@@ -201,7 +201,7 @@ mg_status plan(mg_handle* h, Bump& B)
     int n[3] = {h->geo.n[0], h->geo.n[1], dim == 3 ? h->geo.n[2] : 1};
     double hh[3] = {h->geo.h[0], h->geo.h[1], dim == 3 ? h->geo.h[2] : 1.0};
     int L = 0;
-    const long long cmax = h->opt.coarsest_max > 0 ? h->opt.coarsest_max : 64;
+    const long long cmax = h->opt.coarsest_max > 0 ? h->opt.coarsest_max : 8;
     for (;;) {
         if (L >= kMaxLevels) return fail(MG_ERR_UNSUPPORTED, "too many levels");
         Level& v = h->lev[L];
@@ -430,6 +430,19 @@ void residual64(mg_handle* h, const double* phi, float* r32)
     reduce_finalize(h->partials, 1, &h->d->rnorm2, s);
 }
 
+// The first residual when the solve starts from phi = 0 (MG_FLAG_ZERO_GUESS):
+// phi is cleared and r = f needs no operator application.
+void init_zero_guess(mg_handle* h, double* phi, float* r32)
+{
+    cudaStream_t s = h->stream;
+    const size_t n = h->lev[0].nvec;
+    cudaMemsetAsync(phi, 0, n * sizeof(double), s);
+    vec_init_zero_guess(h->f64, r32, &h->d->fscale, h->partials, n, s);
+    reduce_finalize(h->partials, 1, &h->d->rnorm2, s);
+}
+
+bool zero_guess(const mg_handle* h) { return (h->opt.flags & MG_FLAG_ZERO_GUESS) != 0; }
+
 template <typename T>
 T* lx(mg_handle* h, int l);
 template <>
@@ -592,7 +605,7 @@ void gauge(mg_handle* h, double* phi)
 int inner_cycles(const mg_handle* h)
 {
     if (h->opt.inner_cycles > 0) return h->opt.inner_cycles;
-    return h->loc == MG_LOC_NODAL ? 2 : 1;
+    return 2;
 }
 
 // Mixed refinement step: a few FP32 V-cycles on A e = r / ||f|| from e = 0,
@@ -614,9 +627,13 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
     cudaStream_t s = h->stream;
     const bool mixed = h->prec == MG_PREC_MIXED;
     const bool nodal = h->loc == MG_LOC_NODAL;
-    if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), phi, s);
     float* r32 = mixed ? h->lev[0].b32 : nullptr;
-    residual64(h, phi, r32);
+    if (zero_guess(h)) {
+        init_zero_guess(h, phi, r32);
+    } else {
+        if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), phi, s);
+        residual64(h, phi, r32);
+    }
     mg_status rc = readback(h);
     if (rc != MG_OK) return rc;
     if (h->hs->info != 0)
@@ -774,9 +791,13 @@ mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream
         reduce_finalize(h->partials, 2, h->d->red, s);
         finish_rhs(h, 1, -1);
     }
-    MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(phi, h->d, n, 1));
-    if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), phi, s);
-    residual64(h, phi, r32);
+    if (zero_guess(h)) {
+        init_zero_guess(h, phi, r32);
+    } else {
+        MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(phi, h->d, n, 1));
+        if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), phi, s);
+        residual64(h, phi, r32);
+    }
     cudaGraph_t g;
     std::vector<cudaGraphNode_t> deps;
     mg_status rc = capture_deps(s, &g, deps);
@@ -1043,7 +1064,7 @@ void mg_default_options(mg_options* o)
     o->nu1 = 2;
     o->nu2 = 2;
     o->max_iters = 100;
-    o->coarsest_max = 64;
+    o->coarsest_max = 8;
     o->interp_order = 1;
     o->omega = 0.9;
     o->stream = nullptr;

@@ -183,6 +183,9 @@ void vec_copy_f64(double* dst, const double* src, size_t n, cudaStream_t s);
 void vec_to_f32(float* dst, const double* src, size_t n, cudaStream_t s);
 void vec_to_f64(double* dst, const float* src, size_t n, cudaStream_t s);
 void vec_recip(double* dst, const double* src, size_t n, cudaStream_t s);
+// r32 = f / scale and partials of its squared norm: the residual of x = 0
+void vec_init_zero_guess(const double* f, float* r32, const double* scale, double* partials, size_t n,
+                         cudaStream_t s);
 void vec_zero_f32(float* v, size_t n, cudaStream_t s);
 void vec_zero_f64(double* v, size_t n, cudaStream_t s);
 // phi += (*scale) * e

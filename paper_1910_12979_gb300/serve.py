@@ -222,7 +222,8 @@ class GpuBackend:
         p0 = self.problems[n][0]
         stream = torch.cuda.Stream(device=self.device)
         with torch.cuda.stream(stream):
-            solver = self.ProjectionSolver(p0["geom"], p0["sigma"], loc="cell", prec=self.prec, stream=stream)
+            solver = self.ProjectionSolver(p0["geom"], p0["sigma"], loc="cell", prec=self.prec, stream=stream,
+                                           flags=self.N.MG_FLAG_ZERO_GUESS | self.N.MG_FLAG_AUTOTUNE)
             U = [torch.empty_like(u) for u in p0["U"]]
             phi = torch.empty_like(p0["sigma"])
         stream.synchronize()
@@ -240,7 +241,6 @@ class GpuBackend:
             s.update_coeff(p["sigma"])
             for a, b in zip(state["U"], p["U"]):
                 a.copy_(b)
-            state["phi"].zero_()
             st = s.project(state["U"], p["beta0"], p["S"], beta0_face=p["beta0_face"], phi=state["phi"],
                            tol=self.tol, allow_not_converged=True)
             out = [u.clone() for u in state["U"]] if req.keep else None

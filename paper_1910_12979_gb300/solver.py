@@ -31,7 +31,7 @@ class ProjectionSolver:
     """
 
     def __init__(self, geom, sigma, loc="cell", prec="mixed", faces=None, nu1=2, nu2=2, max_iters=100,
-                 coarsest_max=64, interp_order=1, omega=0.9, stream=None, flags=0, inner_cycles=0):
+                 coarsest_max=8, interp_order=1, omega=0.9, stream=None, flags=0, inner_cycles=0):
         N.load()
         self.dim = int(geom["dim"])
         n = list(geom["n"]) + [1] * (3 - len(geom["n"]))

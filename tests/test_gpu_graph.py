@@ -105,3 +105,22 @@ def test_graph_zero_rhs_and_warm_start():
     s.solve(f, phi, tol=1e-10)
     st2 = s.solve(f, phi, tol=1e-10)   # warm start at the solution: no iteration needed
     assert st2["iters"] == 0
+
+
+@pytest.mark.parametrize("loc", ["cell", "nodal"])
+def test_zero_guess_flag(loc):
+    """MG_FLAG_ZERO_GUESS ignores phi's input and skips the operator in the first
+    residual; the FP32 residual it feeds the V-cycles is the same, so the solve
+    returns the same phi as a solve started from an explicit zero, on the graph
+    path and on the host-driven loop."""
+    p = I.stratified(32, seed=23, contrast=1e3, mac=False, nodal=False)
+    res = []
+    for flags in (0, N.MG_FLAG_ZERO_GUESS, N.MG_FLAG_ZERO_GUESS | N.MG_FLAG_NO_GRAPH):
+        s = ProjectionSolver(p["geom"], T(p["sigma"]), loc=loc, prec="mixed", flags=flags)
+        f = T(np.random.default_rng(9).normal(size=s.vec_shape))
+        phi = torch.zeros_like(f) if flags == 0 else torch.full_like(f, 7.0)
+        st = s.solve(f, phi, tol=1e-11)
+        res.append((phi, st["iters"]))
+        s.close()
+    for phi, it in res[1:]:
+        assert it == res[0][1] and torch.equal(phi, res[0][0])

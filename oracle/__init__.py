@@ -66,7 +66,7 @@ def _L():
                      "orc_mac_solve_dense", "orc_mac_solve_mg", "orc_mac_project", "orc_nodal_apply",
                      "orc_nodal_div", "orc_nodal_lump", "orc_nodal_grad", "orc_nodal_rhs",
                      "orc_nodal_solve_dense", "orc_nodal_solve_mg", "orc_nodal_project", "orc_beta0_eq5",
-                     "orc_map_radial"):
+                     "orc_map_radial", "orc_rotation_forces"):
             getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -357,3 +357,17 @@ def map_radial(g: Grid, spherical, center, r0, dr, beta0_r, rho0_r):
                         ctypes.c_double(dr), ctypes.c_int(len(b)), _p(b), _p(rho), _p(sigma), _p(bc),
                         _arr3(_ptr3(bf)))
     return sigma, bc, bf
+
+
+def rotation_forces(g: Grid, omega, center, U, F=None, alpha=1.0, centrifugal=True):
+    """F += alpha (-2 omega x U - omega x (omega x r)) at cell centres (S5); returns F."""
+    U = [_f64(u) for u in U]
+    if F is None:
+        F = [np.zeros(g.cell_shape) for _ in range(g.dim)]
+    else:
+        F = [np.array(f, dtype=np.float64, order="C", copy=True) for f in F]
+    om = (ctypes.c_double * 3)(*(list(omega) + [0.0] * (3 - len(omega))))
+    c = (ctypes.c_double * 3)(*(list(center) + [0.0] * (3 - len(center))))
+    _L().orc_rotation_forces(ctypes.byref(g.c()), om, c, ctypes.c_int(1 if centrifugal else 0),
+                             ctypes.c_double(alpha), _arr3(_ptr3(U)), _arr3(_ptr3(F)))
+    return F

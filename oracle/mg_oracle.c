@@ -1373,3 +1373,47 @@ int orc_map_radial(const orc_grid* g, int spherical, const double* center, doubl
     }
     return 0;
 }
+
+/* ======================================================================== */
+/* Rotation: Coriolis and centrifugal accelerations (S5, the rotating form  */
+/* of the momentum equation)                                                 */
+/* ======================================================================== */
+
+/* For cell-centred velocity components U[d] (d < dim; the missing component of
+ * a 2-D grid is 0) and angular velocity omega (3 components), at every cell
+ * centre x with r = x - center:
+ *     a = -2 omega x U  -  [centrifugal] omega x (omega x r)
+ * and F[d] += alpha a_d.  The cross products are written out component by
+ * component.  F may alias U (each cell is read in full before it is written). */
+static void cross3(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+int orc_rotation_forces(const orc_grid* g, const double* omega, const double* center, int centrifugal,
+                        double alpha, const double* const U[3], double* const F[3])
+{
+    int c[3];
+    for (c[2] = 0; c[2] < g->n[2]; ++c[2])
+        for (c[1] = 0; c[1] < g->n[1]; ++c[1])
+            for (c[0] = 0; c[0] < g->n[0]; ++c[0]) {
+                size_t id = ((size_t)c[2] * g->n[1] + c[1]) * g->n[0] + c[0];
+                double u[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0}, w[3], a[3];
+                for (int d = 0; d < g->dim; ++d) {
+                    u[d] = U[d][id];
+                    r[d] = (c[d] + 0.5) * g->h[d] - center[d];
+                }
+                cross3(omega, u, w);
+                for (int d = 0; d < 3; ++d) a[d] = -2.0 * w[d];
+                if (centrifugal) {
+                    double wr[3], wwr[3];
+                    cross3(omega, r, wr);
+                    cross3(omega, wr, wwr);
+                    for (int d = 0; d < 3; ++d) a[d] -= wwr[d];
+                }
+                for (int d = 0; d < g->dim; ++d) F[d][id] += alpha * a[d];
+            }
+    return 0;
+}

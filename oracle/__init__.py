@@ -66,7 +66,7 @@ def _L():
                      "orc_mac_solve_dense", "orc_mac_solve_mg", "orc_mac_project", "orc_nodal_apply",
                      "orc_nodal_div", "orc_nodal_lump", "orc_nodal_grad", "orc_nodal_rhs",
                      "orc_nodal_solve_dense", "orc_nodal_solve_mg", "orc_nodal_project", "orc_beta0_eq5",
-                     "orc_map_radial", "orc_rotation_forces"):
+                     "orc_map_radial", "orc_rotation_forces", "orc_face_average", "orc_advect"):
             getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -371,3 +371,37 @@ def rotation_forces(g: Grid, omega, center, U, F=None, alpha=1.0, centrifugal=Tr
     _L().orc_rotation_forces(ctypes.byref(g.c()), om, c, ctypes.c_int(1 if centrifugal else 0),
                              ctypes.c_double(alpha), _arr3(_ptr3(U)), _arr3(_ptr3(F)))
     return F
+
+
+def face_average(g: Grid, U):
+    """MAC face velocities from cell-centred U (mean of the two cells; walls 0; outflow: interior value)."""
+    U = [_f64(u) for u in U]
+    Uf = [np.zeros(g.face_shape(d)) for d in range(g.dim)]
+    _L().orc_face_average(ctypes.byref(g.c()), _arr3(_ptr3(U)), _arr3(_ptr3(Uf)))
+    return Uf
+
+
+def advect(g: Grid, Uf, q):
+    """Upwind advective derivative (U_adv . grad) q at cell centres."""
+    Uf = [_f64(u) for u in Uf]
+    q = _f64(q)
+    A = np.zeros(g.cell_shape)
+    _L().orc_advect(ctypes.byref(g.c()), _arr3(_ptr3(Uf)), _p(q), _p(A))
+    return A
+
+
+def time_step(g: Grid, sigma, beta0_cell, beta0_face, U, S, dt, omega=None, center=None, centrifugal=True,
+              tol=1e-14):
+    """One step around the two projections (S2-S3), in the order of the method:
+    face velocities from U^n, MAC projection of them, advection of U^n by the
+    projected face velocities (plus the rotation accelerations when omega is
+    given), nodal projection of the result.  Returns the new cell velocities, the
+    projected face velocities and the two projections' results."""
+    Uf = face_average(g, U)
+    mac = mac_project(g, sigma, beta0_cell, beta0_face, Uf, S, tol=tol)
+    Uadv = mac["U"]
+    Ustar = [np.asarray(U[d], dtype=np.float64) - dt * advect(g, Uadv, U[d]) for d in range(g.dim)]
+    if omega is not None:
+        Ustar = rotation_forces(g, omega, center, U, F=Ustar, alpha=dt, centrifugal=centrifugal)
+    nod = nodal_project(g, sigma, beta0_cell, Ustar, S, tol=tol)
+    return {"U": nod["U"], "Uadv": Uadv, "mac": mac, "nodal": nod}

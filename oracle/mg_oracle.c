@@ -1417,3 +1417,78 @@ int orc_rotation_forces(const orc_grid* g, const double* omega, const double* ce
             }
     return 0;
 }
+
+/* ======================================================================== */
+/* One time step around the two projections (S2-S3): face velocities,        */
+/* advection of the cell-centred velocity                                    */
+/* ======================================================================== */
+
+/* cell c moved by s along d: 1 and the (wrapped) index when it exists */
+static int cell_shift(const orc_grid* g, const int c[3], int d, int s, int out[3])
+{
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2];
+    out[d] += s;
+    if (out[d] >= 0 && out[d] < g->n[d]) return 1;
+    if (g->bclo[d] != BC_PERIODIC) return 0;
+    out[d] = out[d] < 0 ? out[d] + g->n[d] : out[d] - g->n[d];
+    return 1;
+}
+
+/* Face velocities from cell-centred U: on every face of direction d the mean of
+ * U_d in the two cells beside it; a periodic face takes its wrap neighbour; a
+ * wall (Neumann) face carries 0; an outflow (Dirichlet) face the value of its
+ * interior cell. */
+int orc_face_average(const orc_grid* g, const double* const U[3], double* const Uf[3])
+{
+    for (int d = 0; d < g->dim; ++d) {
+        int m[3] = { g->n[0], g->n[1], g->n[2] };
+        m[d] += 1;
+        int f[3];
+        for (f[2] = 0; f[2] < m[2]; ++f[2])
+            for (f[1] = 0; f[1] < m[1]; ++f[1])
+                for (f[0] = 0; f[0] < m[0]; ++f[0]) {
+                    int hi[3] = { f[0], f[1], f[2] }, lo[3];
+                    int has_hi = hi[d] < g->n[d];
+                    int has_lo = cell_shift(g, hi, d, -1, lo);
+                    if (!has_hi && g->bclo[d] == BC_PERIODIC) { hi[d] = 0; has_hi = 1; }
+                    double v;
+                    if (has_hi && has_lo) {
+                        v = 0.5 * (U[d][cell_index(g, lo)] + U[d][cell_index(g, hi)]);
+                    } else {
+                        int bc = has_hi ? g->bclo[d] : g->bchi[d];
+                        v = bc == BC_NEUMANN ? 0.0 : U[d][cell_index(g, has_hi ? hi : lo)];
+                    }
+                    Uf[d][face_index(g, d, f)] = v;
+                }
+    }
+    return 0;
+}
+
+/* Upwind advective derivative (U_adv . grad) q at cell centres, from face
+ * velocities U_adv and a cell field q:
+ *   A_c = sum_d (1/h_d) [ u_{d,+} (q~_{d,+} - q_c) - u_{d,-} (q~_{d,-} - q_c) ]
+ * with q~ on a face the value of the upwind cell (the lower cell when u >= 0);
+ * an upwind cell outside a non-periodic boundary takes q_c (zero gradient). */
+int orc_advect(const orc_grid* g, const double* const Uf[3], const double* q, double* A)
+{
+    int c[3];
+    for (c[2] = 0; c[2] < g->n[2]; ++c[2])
+        for (c[1] = 0; c[1] < g->n[1]; ++c[1])
+            for (c[0] = 0; c[0] < g->n[0]; ++c[0]) {
+                long id = cell_index(g, c);
+                double qc = q[id], a = 0.0;
+                for (int d = 0; d < g->dim; ++d) {
+                    int fl[3] = { c[0], c[1], c[2] }, fh[3] = { c[0], c[1], c[2] };
+                    fh[d] += 1;
+                    double ul = Uf[d][face_index(g, d, fl)], uh = Uf[d][face_index(g, d, fh)];
+                    int nb[3];
+                    double qlo = cell_shift(g, c, d, -1, nb) ? q[cell_index(g, nb)] : qc;
+                    double qhi = cell_shift(g, c, d, +1, nb) ? q[cell_index(g, nb)] : qc;
+                    double qt_hi = uh >= 0.0 ? qc : qhi;   /* upwind value on the high face */
+                    double qt_lo = ul >= 0.0 ? qlo : qc;   /* and on the low face */
+                    a += (uh * (qt_hi - qc) - ul * (qt_lo - qc)) / g->h[d];
+                }
+                A[id] = a;
+            }
+    return 0;
+}

@@ -50,10 +50,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="stratified", choices=["stratified", "batch", "serve", "config1", "config2"],
+    ap.add_argument("--workload", default="stratified", choices=["stratified", "batch", "serve", "config1", "config2", "step"],
                     help="stratified: the default 256^3 MAC + nodal mixed step; batch: 64 uneven MAC solves in "
                          "one graph launch; serve: Poisson stream of polytrope-star projections (p50/p99); "
-                         "config1: 2-D 64^2 manufactured solve; config2: 128^3 FP64 MAC + nodal step")
+                         "config1: 2-D 64^2 manufactured solve; config2: 128^3 FP64 MAC + nodal step; "
+                         "step: the time step around the two projections (face velocities, MAC projection, "
+                         "advection with rotation, nodal projection), mixed, on the stratified workload")
     ap.add_argument("--parity", action="store_true",
                     help="also solve the MAC system of the workload with the CPU oracle and report rel-L2 of phi")
     ap.add_argument("--budget-gb", type=float, default=24.0, help="serve: device-memory budget of the slots")
@@ -406,6 +408,69 @@ def run_config1(args, dev):
             "fp64": res["fp64"], "mixed": res["mixed"]}
 
 
+def run_step(args, dev, world, dist):
+    """Time steps around the two projections (mg_step) on the stratified workload, mixed precision."""
+    import numpy as np
+    import torch
+
+    import inputs as I
+    from paper_1910_12979_gb300 import ProjectionSolver
+    from paper_1910_12979_gb300 import native as N
+    from paper_1910_12979_gb300.solver import time_step
+
+    n = args.n
+    p = I.stratified(n, seed=3, contrast=1e3, mac=False)
+    stream = torch.cuda.Stream(device=dev)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    with torch.cuda.stream(stream):
+        sigma, beta0, S = T(p["sigma"]), T(p["beta0"]), T(p["S"])
+        b0f = [T(b) for b in p["beta0_face"]]
+        U0 = [T(u) for u in p["U_cell"]]
+        fl = N.MG_FLAG_ZERO_GUESS
+        mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec="mixed", stream=stream, flags=fl)
+        nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec="mixed", stream=stream, flags=fl)
+        Un = [torch.empty_like(u) for u in U0]
+        Ua = [torch.empty(mac.face_shape(d), dtype=torch.float64, device=dev) for d in range(3)]
+    stream.synchronize()
+    dt, omega, centre = 0.01, (0.0, 0.0, 2.0), (0.5, 0.5, 0.5)
+
+    def step():
+        with torch.cuda.stream(stream):
+            mac.update_coeff(sigma)
+            nod.update_coeff(sigma)
+            return time_step(mac, nod, U0, Un, Ua, beta0, b0f, S, dt, omega=omega, center=centre, centrifugal=True,
+                             tol=args.tol, allow_not_converged=True)
+
+    for _ in range(args.warmup):
+        st = step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = N.mg_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = N.mg_launch_count() - l0
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return {"metric": "time steps/s around the two projections", "value": args.steps * world / (ms / 1e3),
+            "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (mixed)", "data": "synthetic",
+            "config": {"workload": f"stratified atmosphere {n}^3: face velocities, MAC projection, upwind advection "
+                                   f"with Coriolis and centrifugal terms (Omega = {omega}), nodal projection",
+                       "dt": dt, "tol": args.tol, "coefficient_update_per_step": True},
+            "gpu_launches": launches,
+            "solver": {"mac": {k: st[0][k] for k in ("iters", "rel_resid", "rel_constraint")},
+                       "nodal": {k: st[1][k] for k in ("iters", "rel_resid", "rel_constraint")}}}
+
+
 def run_config2(args, dev):
     """128^3 stratified MAC + nodal step in FP64 (and the MAC rel-L2 against the oracle)."""
     import numpy as np
@@ -497,6 +562,8 @@ def main():
             line = run_serve(args, dev, rank, world, dist)
         elif args.workload == "config1":
             line = run_config1(args, dev)
+        elif args.workload == "step":
+            line = run_step(args, dev, world, dist)
         else:
             line = run_config2(args, dev)
         if rank == 0:

@@ -311,6 +311,47 @@ typedef enum {
 mg_status mg_mac_constraint_noalloc(const mg_geometry* geom, const double* const U[3], const mg_beta0* beta0,
                                     const double* S, double* out, void* stream);
 
+/* One time step around the two projections (S2-S3; NEXT to the projection
+ * path), in the order of the method:
+ *   1. face velocities Uadv from the cell velocities U (mean of the two cells
+ *      beside a face; periodic faces wrap; wall faces 0; outflow faces the
+ *      interior cell's value),
+ *   2. MAC projection of Uadv (mg_project on mac, phi internal),
+ *   3. Unew = U - dt (Uadv . grad) U with upwind face values (zero gradient
+ *      where the upwind cell is outside a boundary), plus dt times the rotation
+ *      accelerations of mg_rotation_forces when omega is not NULL,
+ *   4. nodal projection of Unew (mg_project on nodal, phi internal).
+ *   mac, nodal  handles of the same grid, boundary kinds and stream (loc
+ *               MG_LOC_CELL and MG_LOC_NODAL)
+ *   U           device, cell-centred components of U^n (not modified)
+ *   Unew        device, cell-centred output U^{n+1}; must not alias U
+ *   Uadv        device, face arrays: scratch, and on return the projected face
+ *               velocities
+ *   beta0       cell and face values (both required); S: cells
+ *   dt >= 0; omega (3 doubles, host) or NULL; center (host) when centrifugal
+ *   tol         for both projections; stats: NULL or 2 entries (MAC, nodal)
+ * Returns the first failing status (MG_ERR_NOT_CONVERGED still completes the
+ * step with the best phi); synchronises the handles' stream. */
+mg_status mg_step(mg_handle* mac, mg_handle* nodal, const double* const U[3], double* const Unew[3],
+                  double* const Uadv[3], const mg_beta0* beta0, const double* S, double dt, const double omega[3],
+                  const double center[3], int centrifugal, double tol, mg_stats stats[2]);
+
+/* Rotation (S5, the rotating form of the velocity equation): at every cell
+ * centre x, with r = x - center, accumulate the Coriolis and (if centrifugal
+ * is nonzero) centrifugal accelerations
+ *     F[d] += alpha * ( -2 Omega x U  -  Omega x (Omega x r) )_d ,   d < dim.
+ *   geom     cell grid (its loc is ignored); 2-D grids use the in-plane
+ *            components (U_z = 0, r_z = 0)
+ *   omega    host, 3 doubles: the angular velocity
+ *   center   host, 3 doubles: the rotation axis passes through it (may be NULL
+ *            when centrifugal is 0)
+ *   alpha    scale (1: the acceleration; dt: the explicit velocity update)
+ *   U, F     device, cell-centred components, x-fastest; F may alias U
+ *   stream   cudaStream_t (NULL: legacy default stream); asynchronous
+ * MG_ERR_INVALID_ARG for null or missing arguments. */
+mg_status mg_rotation_forces(const mg_geometry* geom, const double omega[3], const double center[3], int centrifugal,
+                             double alpha, const double* const U[3], double* const F[3], void* stream);
+
 /* Precision conversions of the mixed-precision path, exposed so that they can
  * be checked against the hardware conversions.  The paper has no counterpart.
  * mg_convert_f64_to_f32 rounds to nearest, ties to even; mg_convert_f32_to_f64

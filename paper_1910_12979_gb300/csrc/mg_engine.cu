@@ -154,6 +154,13 @@ struct mg_handle {
     long long g_fixed[2], g_body[2];  // kernel launches outside the loop / per iteration
 };
 
+void mgp::handle_info(const mg_handle* h, mg_geometry* g, mg_bc* bc, cudaStream_t* s)
+{
+    if (g) *g = h->geo;
+    if (bc) *bc = h->bcin;
+    if (s) *s = h->stream;
+}
+
 namespace {
 
 bool valid_bc(int v) { return v == MG_BC_PERIODIC || v == MG_BC_NEUMANN || v == MG_BC_DIRICHLET; }

@@ -10,6 +10,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/mg.h"
+
 namespace mgp {
 
 enum { BCP = 0, BCN = 1, BCD = 2 };
@@ -72,6 +74,8 @@ struct DevScalars {
 // (mg_launch_count reports the total).
 // sets the message mg_last_error() returns on this thread
 void set_last_error(const char* msg);
+// geometry, boundary kinds and stream of a handle (for entry points outside the engine)
+void handle_info(const mg_handle* h, mg_geometry* g, mg_bc* bc, cudaStream_t* s);
 void note_launch();
 void add_launches(long long n);
 long long launch_count();

@@ -91,6 +91,13 @@ SIGNATURES = [
     ("mg_mac_constraint_noalloc", ctypes.c_int, [ctypes.POINTER(mg_geometry), ctypes.c_void_p * 3,
                                                  ctypes.POINTER(mg_beta0), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p]),
+    ("mg_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p * 3, ctypes.c_void_p * 3,
+                               ctypes.c_void_p * 3, ctypes.POINTER(mg_beta0), ctypes.c_void_p, ctypes.c_double,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                               ctypes.c_double, ctypes.POINTER(mg_stats)]),
+    ("mg_rotation_forces", ctypes.c_int, [ctypes.POINTER(mg_geometry), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_void_p * 3, ctypes.c_void_p * 3, ctypes.c_void_p]),
     ("mg_convert_f64_to_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("mg_convert_f32_to_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("mg_reciprocal_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -243,6 +250,27 @@ def mg_strerror(s):
 
 def mg_last_error():
     return load().mg_last_error().decode()
+
+
+def mg_step(mac, nodal, U_ptrs, Unew_ptrs, Uadv_ptrs, beta0, S_ptr, dt, omega=None, center=None, centrifugal=False,
+            tol=1e-10, allow=(MG_OK,)):
+    arr = lambda p: (ctypes.c_void_p * 3)(*(list(p) + [None] * (3 - len(p))))
+    om = (ctypes.c_double * 3)(*omega) if omega is not None else None
+    c = (ctypes.c_double * 3)(*center) if center is not None else None
+    st = (mg_stats * 2)()
+    check(load().mg_step(mac, nodal, arr(U_ptrs), arr(Unew_ptrs), arr(Uadv_ptrs), ctypes.byref(beta0),
+                         ctypes.c_void_p(S_ptr), float(dt), om, c, 1 if centrifugal else 0, float(tol), st),
+          "mg_step", allow)
+    return st[0], st[1]
+
+
+def mg_rotation_forces(geom, omega, center, centrifugal, alpha, U_ptrs, F_ptrs, stream=None):
+    om = (ctypes.c_double * 3)(*omega)
+    c = (ctypes.c_double * 3)(*center) if center is not None else None
+    u = (ctypes.c_void_p * 3)(*(list(U_ptrs) + [None] * (3 - len(U_ptrs))))
+    f = (ctypes.c_void_p * 3)(*(list(F_ptrs) + [None] * (3 - len(F_ptrs))))
+    return check(load().mg_rotation_forces(ctypes.byref(geom), om, c, 1 if centrifugal else 0, float(alpha), u, f,
+                                           stream), "mg_rotation_forces")
 
 
 def mg_convert_f64_to_f32(x_ptr, y_ptr, n, stream=None):

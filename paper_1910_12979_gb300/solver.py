@@ -163,3 +163,22 @@ def solve_batch(solvers, rhs, phi, tols, allow_not_converged=False):
     st = N.mg_solve_batch([s.handle for s in solvers], [_ptr(r, "rhs") for r in rhs], [_ptr(p, "phi") for p in phi],
                           list(tols), allow)
     return [s.as_dict() for s in st]
+
+
+def time_step(mac, nodal, U, Unew, Uadv, beta0_cell, beta0_face, S, dt, omega=None, center=None, centrifugal=False,
+              tol=1e-10, allow_not_converged=False):
+    """mg_step: face velocities, MAC projection, advection (+ rotation), nodal
+    projection.  mac / nodal: ProjectionSolver objects of the same grid;
+    U: cell components of U^n; Unew: output cell components; Uadv: face arrays
+    (scratch; the projected face velocities on return).  Returns the two
+    projections' statistics."""
+    b0 = N.mg_beta0()
+    b0.cell = _ptr(beta0_cell, "beta0_cell", mac.cell_shape)
+    for d in range(mac.dim):
+        b0.face[d] = _ptr(beta0_face[d], f"beta0_face[{d}]", mac.face_shape(d))
+    allow = (N.MG_OK, N.MG_ERR_NOT_CONVERGED) if allow_not_converged else (N.MG_OK,)
+    a, b = N.mg_step(mac.handle, nodal.handle, [_ptr(u, "U", mac.cell_shape) for u in U],
+                     [_ptr(u, "Unew", mac.cell_shape) for u in Unew],
+                     [_ptr(u, "Uadv", mac.face_shape(d)) for d, u in enumerate(Uadv)], b0,
+                     _ptr(S, "S", mac.cell_shape), dt, omega, center, centrifugal, tol, allow)
+    return a.as_dict(), b.as_dict()

@@ -190,8 +190,9 @@ class Clocks:
 
 
 # the source files whose change invalidates a kernel class's ncu counters
-PROF_SOURCES = {"cell_smooth_fine": ["mg_sweep.cu"], "node_smooth_fine": ["mg_nodal.cu", "mg_nodal.cuh"],
-                "cell_restrict_fine": ["mg_cell.cu"], "cell_resid64": ["mg_cell.cu"],
+PROF_SOURCES = {"cell_smooth_fine": ["mg_gsrb4.cu", "mg_sweep.cu", "mg_cell.cu"],
+                "node_smooth_fine": ["mg_nodal4.cu", "mg_nodal.cu", "mg_nodal.cuh"],
+                "cell_restrict_fine": ["mg_gsrb4.cu", "mg_cell.cu"], "cell_resid64": ["mg_cell.cu"],
                 "node_resid64": ["mg_nodal.cu", "mg_nodal.cuh"]}
 
 
@@ -373,6 +374,7 @@ def run_config1(args, dev):
     import inputs as I
     import oracle as O
     from paper_1910_12979_gb300 import ProjectionSolver
+    from paper_1910_12979_gb300 import native as N
 
     p = I.manufactured_2d(64)
     g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
@@ -478,6 +480,7 @@ def run_config2(args, dev):
 
     import inputs as I
     from paper_1910_12979_gb300 import ProjectionSolver
+    from paper_1910_12979_gb300 import native as N
 
     p = I.stratified(128, seed=2, contrast=1e3)
     stream = torch.cuda.Stream(device=dev)

@@ -721,38 +721,73 @@ def main():
         for s in f64[:2]:
             s.close()
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies its inputs from pinned
+    # host memory and reads its projected velocities back.  Two device input sets and a copy stream
+    # let the copies of step k+1 (and the read-back of step k) overlap the solves of step k.
     if not args.no_e2e:
         mac, nod, phim, phin = mixed
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         h_in = [pin(p["sigma"]), pin(p["beta0"]), pin(p["S"])] + [pin(b) for b in p["beta0_face"]] + \
                [pin(u) for u in p["U_mac"]] + [pin(u) for u in p["U_cell"]]
-        d_in = [sigma, beta0, S] + b0f + U0m + U0c
-        h_out = [torch.empty_like(u, device="cpu").pin_memory() for u in Um + Uc]
         h2d = sum(t.numel() * t.element_size() for t in h_in)
-        d2h = sum(t.numel() * t.element_size() for t in h_out)
+        cstream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(stream):
+            d_sets = [[torch.empty_like(sigma) for _ in range(3)] + [torch.empty_like(b) for b in b0f] +
+                      [torch.empty_like(u) for u in U0m] + [torch.empty_like(u) for u in U0c] for _ in range(2)]
+            w_sets = [[torch.empty_like(u) for u in Um + Uc] for _ in range(2)]
+        h_out = [[torch.empty_like(u, device="cpu").pin_memory() for u in Um + Uc] for _ in range(2)]
+        d2h = sum(t.numel() * t.element_size() for t in h_out[0])
+        h2d_done = [torch.cuda.Event() for _ in range(2)]
+        comp_done = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_step():
-            with torch.cuda.stream(stream):
-                for d, hsrc in zip(d_in, h_in):
+        def upload(i):
+            with torch.cuda.stream(cstream):
+                for d, hsrc in zip(d_sets[i], h_in):
                     d.copy_(hsrc, non_blocking=True)
-            step(mixed)
+                h2d_done[i].record(cstream)
+
+        def compute(i):
+            sg, b0, Sv = d_sets[i][0], d_sets[i][1], d_sets[i][2]
+            bf, u0m, u0c = d_sets[i][3:6], d_sets[i][6:9], d_sets[i][9:12]
+            um, uc = w_sets[i][:3], w_sets[i][3:]
+            stream.wait_event(h2d_done[i])
             with torch.cuda.stream(stream):
-                for hd, d in zip(h_out, Um + Uc):
+                mac.update_coeff(sg)
+                nod.update_coeff(sg)
+                for a_, b_ in zip(um + uc, u0m + u0c):
+                    a_.copy_(b_)
+                mac.project(um, b0, Sv, beta0_face=bf, phi=phim, tol=args.tol, allow_not_converged=True)
+                nod.project(uc, b0, Sv, phi=phin, tol=args.tol, allow_not_converged=True)
+                comp_done[i].record(stream)
+
+        def download(i):
+            cstream.wait_event(comp_done[i])
+            with torch.cuda.stream(cstream):
+                for hd, d in zip(h_out[i], w_sets[i]):
                     hd.copy_(d, non_blocking=True)
+
+        def run(K):
+            upload(0)
+            if K > 1:
+                upload(1)
+            for k in range(K):
+                compute(k % 2)
+                download(k % 2)
+                if k + 2 < K:
+                    upload(k % 2)   # after this step's read-back (same stream) and its solves (event)
+            cstream.synchronize()
             stream.synchronize()
 
-        e2e_step()
-        Ke = max(1, min(args.steps, 5))
+        run(2)
+        Ke = max(2, min(args.steps, 6))
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(Ke):
-            e2e_step()
-        e1.record(stream)
+        e0.record(cstream)
+        run(Ke)
+        e1.record(cstream)
         e1.synchronize()
         mse = e0.elapsed_time(e1)
         if dist is not None:
@@ -760,7 +795,9 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             mse = float(t.item())
         line["e2e"] = {"value": 2.0 * Ke * world / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": mse / Ke}
+                       "d2h_bytes_per_step": d2h, "ms_per_step": mse / Ke,
+                       "note": "pinned host inputs copied and results read back every step on a copy stream, "
+                               "overlapping the solves of the neighbouring step (double-buffered device inputs)"}
 
     if args.parity and rank == 0:
         import oracle as O

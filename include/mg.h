@@ -121,7 +121,9 @@ typedef struct {
  *   stream        cudaStream_t (NULL: the legacy default stream)
  *   flags         MG_FLAG_* bits (0 by default)
  *   inner_cycles  mixed precision: FP32 V-cycles per FP64 refinement step
- *                 (0: automatic, 2) */
+ *                 (0: automatic -- two, or one when the last step's rate per
+ *                 V-cycle brings the residual below half the tolerance in one;
+ *                 the graph path decides this on the device with the same rule) */
 typedef struct {
     int prec;
     int nu1;
@@ -199,9 +201,13 @@ mg_status mg_update_coeff(mg_handle* h, const mg_coeff* coeff);
 mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_stats* stats);
 
 /* Projection (steps a2-a10): f = D(beta0 U) - beta0 S, solve to tol, update U
- * in place, report the constraint.  MAC: U[d] face arrays, beta0->face required.
- * Nodal: U[d] cell arrays.  phi: optional device output (and initial guess) of
- * the solution; NULL uses an internal buffer started from zero. */
+ * in place, report the constraint.  MAC: U[d] face arrays, beta0->face required;
+ * the constraint after the update equals the solver residual, and the solve
+ * stops when ||f - L phi|| <= tol * min(||f||, ||beta0 S||), so that
+ * ||D(beta0 U) - beta0 S|| <= tol ||beta0 S|| holds as well.  Nodal: U[d] cell
+ * arrays (approximate projection: the constraint is reported only).  phi:
+ * optional device output (and initial guess) of the solution; NULL uses an
+ * internal buffer started from zero. */
 mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* beta0, const double* S, double* phi,
                      double tol, mg_stats* stats);
 

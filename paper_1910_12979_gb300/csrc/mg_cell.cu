@@ -9,72 +9,11 @@
 //   diag = sum over interior/periodic faces of Bt + 2 Bt on Dirichlet faces,
 // Neumann faces contributing nothing and a Dirichlet face (phi = 0 on the
 // face) acting through the ghost value -phi_c.
-#include "mg_device.cuh"
+#include "mg_cellops.cuh"
 
 #include <type_traits>
 
 namespace mgp {
-
-// off and diag of row (i,j,k); phi(ii,jj,kk) returns the neighbour value.
-template <int DIM, typename T, typename Phi>
-__device__ __forceinline__ void cell_row(const CellLevel<T>& L, int i, int j, int k, const Phi& phi, T& off, T& dg)
-{
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
-    off = T(0);
-    dg = T(0);
-    {
-        const size_t r = ((size_t)k * ny + j) * (nx + 1) + i;
-        const T bl = L.bx[r], bh = L.bx[r + 1];
-        if (i > 0) { off = fmadd(bl, phi(i - 1, j, k), off); dg += bl; }
-        else if (L.bc.lo[0] == BCP) { off = fmadd(bl, phi(nx - 1, j, k), off); dg += bl; }
-        else if (L.bc.lo[0] == BCD) { dg += T(2) * bl; }
-        if (i < nx - 1) { off = fmadd(bh, phi(i + 1, j, k), off); dg += bh; }
-        else if (L.bc.hi[0] == BCP) { off = fmadd(bh, phi(0, j, k), off); dg += bh; }
-        else if (L.bc.hi[0] == BCD) { dg += T(2) * bh; }
-    }
-    {
-        const size_t r = ((size_t)k * (ny + 1) + j) * nx + i;
-        const T bl = L.by[r], bh = L.by[r + nx];
-        if (j > 0) { off = fmadd(bl, phi(i, j - 1, k), off); dg += bl; }
-        else if (L.bc.lo[1] == BCP) { off = fmadd(bl, phi(i, ny - 1, k), off); dg += bl; }
-        else if (L.bc.lo[1] == BCD) { dg += T(2) * bl; }
-        if (j < ny - 1) { off = fmadd(bh, phi(i, j + 1, k), off); dg += bh; }
-        else if (L.bc.hi[1] == BCP) { off = fmadd(bh, phi(i, 0, k), off); dg += bh; }
-        else if (L.bc.hi[1] == BCD) { dg += T(2) * bh; }
-    }
-    if (DIM == 3) {
-        const size_t r = ((size_t)k * ny + j) * nx + i;
-        const size_t pl = (size_t)nx * ny;
-        const T bl = L.bz[r], bh = L.bz[r + pl];
-        if (k > 0) { off = fmadd(bl, phi(i, j, k - 1), off); dg += bl; }
-        else if (L.bc.lo[2] == BCP) { off = fmadd(bl, phi(i, j, nz - 1), off); dg += bl; }
-        else if (L.bc.lo[2] == BCD) { dg += T(2) * bl; }
-        if (k < nz - 1) { off = fmadd(bh, phi(i, j, k + 1), off); dg += bh; }
-        else if (L.bc.hi[2] == BCP) { off = fmadd(bh, phi(i, j, 0), off); dg += bh; }
-        else if (L.bc.hi[2] == BCD) { dg += T(2) * bh; }
-    }
-}
-
-template <typename T>
-struct GlobalPhi {
-    const T* p;
-    int nx, ny;
-    __device__ __forceinline__ T operator()(int i, int j, int k) const { return p[((size_t)k * ny + j) * nx + i]; }
-};
-
-struct UnitPhi {  // phi = e_col
-    int col, nx, ny;
-    __device__ __forceinline__ double operator()(int i, int j, int k) const
-    {
-        return (((k * ny + j) * nx + i) == col) ? 1.0 : 0.0;
-    }
-};
-
-template <typename T>
-__device__ __forceinline__ T inv_diag(const CellLevel<T>& L, int idx, T dg)
-{
-    return L.invd ? L.invd[idx] : recip(dg);
-}
 
 // ------------------------------------------------------------------ setup
 
@@ -195,9 +134,7 @@ __global__ void k_gsrb(CellLevel<T> L, T* __restrict__ x, const T* __restrict__ 
     int i, j, k;
     unflat(t, L.nx, L.ny, i, j, k);
     if (((i + j + k) & 1) != color) return;
-    T off, dg;
-    cell_row<DIM>(L, i, j, k, GlobalPhi<T>{x, L.nx, L.ny}, off, dg);
-    x[t] = (off - b[t]) * inv_diag(L, t, dg);
+    x[t] = gs_value<DIM>(L, x, b, i, j, k);
 }
 
 // r = b - L x on the fine level, averaged over the 2^dim children of each coarse cell.
@@ -210,20 +147,7 @@ __global__ void k_resid_restrict(CellLevel<T> F, const T* __restrict__ x, const 
     if (t >= total) return;
     int ci, cj, ck;
     unflat(t, cnx, cny, ci, cj, ck);
-    const GlobalPhi<T> ph{x, F.nx, F.ny};
-    T r[1 << DIM];
-#pragma unroll
-    for (int q = 0; q < (1 << DIM); ++q) {
-        const int i = 2 * ci + (q & 1), j = 2 * cj + ((q >> 1) & 1), k = DIM == 3 ? 2 * ck + ((q >> 2) & 1) : 0;
-        T off, dg;
-        cell_row<DIM>(F, i, j, k, ph, off, dg);
-        const size_t id = ((size_t)k * F.ny + j) * F.nx + i;
-        r[q] = b[id] - fmadd(-dg, x[id], off);
-    }
-    // x pairs, then y, then z: the order of the tiled and vectorised variants
-    T s = (r[0] + r[1]) + (r[2] + r[3]);
-    if (DIM == 3) s = s + ((r[4] + r[5]) + (r[6] + r[7]));
-    bc[t] = s * (T(1) / T(1 << DIM));
+    bc[t] = restrict_value<DIM>(F, x, b, ci, cj, ck);
 }
 
 // 3-D residual + restriction with one thread per fine cell: a (32, 2, 2) block
@@ -259,26 +183,7 @@ __global__ void k_prolong_add(CellLevel<T> F, CellLevel<T> C, T* __restrict__ xf
     if (t >= total) return;
     int i, j, k;
     unflat(t, F.nx, F.ny, i, j, k);
-    auto X = [&](int a, int b2, int c) { return xc[((size_t)c * C.ny + b2) * C.nx + a]; };
-    if (ORDER == 0) {
-        xf[t] += X(i >> 1, j >> 1, DIM == 3 ? (k >> 1) : 0);
-        return;
-    }
-    const Lin1D lx = lin1d(i, C.nx, F.bc.lo[0], F.bc.hi[0]);
-    const Lin1D ly = lin1d(j, C.ny, F.bc.lo[1], F.bc.hi[1]);
-    const T w1 = T(0.75), w2 = T(0.25);
-    if (DIM == 2) {
-        const T v = w1 * (w1 * X(lx.p, ly.p, 0) + w2 * T(lx.sq) * X(lx.q, ly.p, 0)) +
-                    w2 * T(ly.sq) * (w1 * X(lx.p, ly.q, 0) + w2 * T(lx.sq) * X(lx.q, ly.q, 0));
-        xf[t] += v;
-    } else {
-        const Lin1D lz = lin1d(k, C.nz, F.bc.lo[2], F.bc.hi[2]);
-        auto plane = [&](int c) {
-            return w1 * (w1 * X(lx.p, ly.p, c) + w2 * T(lx.sq) * X(lx.q, ly.p, c)) +
-                   w2 * T(ly.sq) * (w1 * X(lx.p, ly.q, c) + w2 * T(lx.sq) * X(lx.q, ly.q, c));
-        };
-        xf[t] += w1 * plane(lz.p) + w2 * T(lz.sq) * plane(lz.q);
-    }
+    xf[t] += prolong_value<DIM>(F, C, xc, i, j, k, ORDER);
 }
 
 // -------------------------------------------------------- FP64 residuals

@@ -374,10 +374,8 @@ __global__ void k_dense_apply(const double* __restrict__ Minv, int N, const T* _
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int r = warp; r < N; r += nw) {
-        double s = 0.0;
-        for (int c = lane; c < N; c += 32) s += Minv[(size_t)r * N + c] * (double)b[c];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) x[r] = (T)s;
+        const double s = dense_row(Minv, N, b, r, lane);
+        if (lane == 0) x[r] = from_f64<T>(s);
     }
 }
 

@@ -109,6 +109,28 @@ __device__ __forceinline__ double recip_nr(double d)
     return y;
 }
 
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+template <typename T>
+__device__ __forceinline__ T from_f64(double v);
+template <>
+__device__ __forceinline__ float from_f64<float>(double v) { return f64_to_f32_rn(v); }
+template <>
+__device__ __forceinline__ double from_f64<double>(double v) { return v; }
+
+// Row r of x = Minv b (dense coarsest solve), summed by the 32 lanes of a warp:
+// lane-strided partial sums, then a shuffle-down tree; every lane must call it.
+template <typename T>
+__device__ __forceinline__ double dense_row(const double* __restrict__ Minv, int N, const T* __restrict__ b, int r,
+                                            int lane)
+{
+    double s = 0.0;
+    for (int c = lane; c < N; c += 32) s = fmadd(Minv[(size_t)r * N + c], to_f64(b[c]), s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
 template <typename T>
 __device__ __forceinline__ T recip(T d);
 // FP32 levels only precondition the FP64 refinement: the fast reciprocal

@@ -151,7 +151,7 @@ struct mg_handle {
     std::atomic<int> busy;
     // graph-resident solve loops: [0] rhs taken from the caller, [1] rhs already in f64
     cudaGraphExec_t gx[2];
-    long long g_fixed[2], g_body[2];  // kernel launches outside the loop / per iteration
+    long long g_fixed[2], g_body[2], g_if[2];  // kernel launches outside the loop / per iteration / per IF
 };
 
 void mgp::handle_info(const mg_handle* h, mg_geometry* g, mg_bc* bc, cudaStream_t* s)
@@ -536,7 +536,14 @@ void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
     const int dim = h->dim, L = h->nlev;
     auto X = [&](int l) { return l == 0 ? x0 : lx<T>(h, l); };
     auto Bv = [&](int l) { return l == 0 ? b0 : (const T*)lb<T>(h, l); };
-    for (int l = 0; l < L - 1; ++l) {
+    // levels lc .. L-1 (at most kCoarseCells cells each) run as one launch
+    int lc = L;
+    if (!(h->opt.flags & MG_FLAG_NO_FUSED)) {
+        lc = L - 1;
+        while (lc > 0 && h->lev[lc - 1].ncell <= (size_t)kCoarseCells && L - (lc - 1) <= kCoarseMaxLevels) --lc;
+        if (lc == L - 1) lc = L;   // a single level: nothing to fuse
+    }
+    for (int l = 0; l < lc && l < L - 1; ++l) {
         if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
         const CellLevel<T> V = cview<T>(h, l);
         cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu1);
@@ -553,8 +560,21 @@ void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
         if (!done) cell_resid_restrict<T>(dim, V, X(l), Bv(l), lb<T>(h, l + 1), s);
         prof_end(pr, s);
     }
-    dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
-    for (int l = L - 2; l >= 0; --l) {
+    if (lc < L) {
+        CellLevel<T> Ls[kCoarseMaxLevels];
+        T* xs[kCoarseMaxLevels];
+        T* bs[kCoarseMaxLevels];
+        for (int l = lc; l < L; ++l) {
+            Ls[l - lc] = cview<T>(h, l);
+            xs[l - lc] = X(l);
+            bs[l - lc] = const_cast<T*>(Bv(l));
+        }
+        coarse_cycle<T>(dim, L - lc, Ls, xs, bs, h->Minv, h->Nd, h->opt.nu1, h->opt.nu2, h->opt.interp_order,
+                        lc > 0 || zero_init, s);
+    } else {
+        dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
+    }
+    for (int l = (lc < L ? lc : L - 1) - 1; l >= 0; --l) {
         const CellLevel<T> V = cview<T>(h, l);
         cell_prolong_add<T>(dim, V, cview<T>(h, l + 1), X(l), X(l + 1), h->opt.interp_order, s);
         cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu2);
@@ -617,19 +637,33 @@ int inner_cycles(const mg_handle* h)
 
 // Mixed refinement step: a few FP32 V-cycles on A e = r / ||f|| from e = 0,
 // then phi += ||f|| e in FP64.
-void mixed_correction(mg_handle* h, double* phi)
+void mixed_correction(mg_handle* h, double* phi, int cycles)
 {
     float* e = h->lev[0].x32;
-    const int m = inner_cycles(h);
-    for (int j = 0; j < m; ++j) {
+    for (int j = 0; j < cycles; ++j) {
         if (h->loc == MG_LOC_NODAL) vcycle_node<float>(h, e, h->lev[0].b32, j == 0);
         else vcycle_cell<float>(h, e, h->lev[0].b32, j == 0);
     }
     vec_axpy_f32(phi, e, &h->d->fscale, h->lev[0].nvec, h->stream);
 }
 
+bool adaptive_cycles(const mg_handle* h) { return h->prec == MG_PREC_MIXED && h->opt.inner_cycles == 0; }
+
+// Automatic inner cycles of mixed refinement: after a step, one V-cycle is
+// enough for the next step when the last step's rate per V-cycle, applied once
+// to the current relative residual, lands below half the tolerance; otherwise
+// two.  The first step runs two.  Host loop and graph use this same function.
+__host__ __device__ inline int next_two(bool first, bool last_two, double prev_rel, double rel, double tol)
+{
+    if (first || !(prev_rel > 0.0) || !(rel > 0.0)) return 1;
+    double rho = rel / prev_rel;
+    if (last_two) rho = sqrt(rho);
+    return rel * rho > 0.5 * tol ? 1 : 0;
+}
+
+
 // Iterate on L phi = f64 (rhs and ||f|| already prepared on the device).
-mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
+mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st, bool constraint_tol = false)
 {
     cudaStream_t s = h->stream;
     const bool mixed = h->prec == MG_PREC_MIXED;
@@ -646,6 +680,10 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
     if (h->hs->info != 0)
         return fail(MG_ERR_UNSUPPORTED, "the coarsest-level operator is singular");
     const double fn2 = h->hs->fnorm2;
+    if (constraint_tol && fn2 > 0.0 && h->hs->src2 > 0.0) {   // as k_constraint_tol
+        const double c = tol * sqrt(h->hs->src2 / fn2);
+        if (c < tol) tol = c;
+    }
     if (st) { st->rhs_norm = sqrt(fn2); st->iters = 0; st->rel_resid = 0.0; }
     if (fn2 == 0.0) {
         zero(phi, h->lev[0].nvec, s);
@@ -656,10 +694,13 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
     double best = rel;
     int stall = 0, it = 0;
     mg_status status = MG_OK;
+    const bool adaptive = adaptive_cycles(h);
+    int two = next_two(true, true, 0.0, rel, tol);
+    double prev = rel;
     while (rel > tol) {
         if (it >= h->opt.max_iters) { status = MG_ERR_NOT_CONVERGED; break; }
         if (mixed) {
-            mixed_correction(h, phi);
+            mixed_correction(h, phi, adaptive ? (two ? 2 : 1) : inner_cycles(h));
         } else {
             if (nodal) vcycle_node<double>(h, phi, h->f64, false);
             else vcycle_cell<double>(h, phi, h->f64, false);
@@ -673,6 +714,8 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st)
         if (rel < 0.9 * best) { best = rel; stall = 0; }
         else if (++stall >= 4) { status = rel <= tol ? MG_OK : MG_ERR_NOT_CONVERGED; break; }
         if (rel < best) best = rel;
+        two = next_two(false, two != 0, prev, rel, tol);   // as k_check
+        prev = rel;
     }
     if (h->singular) gauge(h, phi);
     if (st) { st->iters = it; st->rel_resid = rel; }
@@ -704,6 +747,20 @@ __global__ void k_set_io(DevScalars* d, const double* rhs, double* phi, double t
     d->phi_io = phi;
     d->tol = tol;
     d->maxit = maxit;
+    d->two = 1;
+    d->n_two = 0;
+}
+
+// MAC projection: the constraint after the update equals the solver residual
+// (L = D B G), so ||D(beta0 U) - beta0 S|| <= tol ||beta0 S|| needs
+// ||f - L phi|| <= tol ||beta0 S||.  The stopping tolerance on ||r||/||f|| becomes
+// tol * min(1, ||beta0 S|| / ||f||); solve_core computes the same value on the host.
+__global__ void k_constraint_tol(DevScalars* d)
+{
+    if (d->fnorm2 > 0.0 && d->src2 > 0.0) {
+        const double c = d->tol * sqrt(d->src2 / d->fnorm2);
+        if (c < d->tol) d->tol = c;
+    }
 }
 
 // dir 0: dst <- rhs_in; 1: dst <- phi_io; 2: phi_io <- dst.  No-op when aliased.
@@ -754,21 +811,76 @@ __global__ void k_check(DevScalars* d, cudaGraphConditionalHandle c, int first)
         if (!stop && rel > d->tol && d->iters >= d->maxit) { st = MG_ERR_NOT_CONVERGED; stop = 1; }
         d->status = st;
         cont = (!stop && rel > d->tol) ? 1u : 0u;
+        const int two = next_two(first != 0, d->two != 0, d->prev_rel, rel, d->tol);
+        if (first) d->n_two = 0;
+        d->two = two;
+        d->prev_rel = rel;
     }
     cudaGraphSetConditional(c, cont);
 }
 
+// the IF node of the second V-cycle of a refinement step
+__global__ void k_set_two(DevScalars* d, cudaGraphConditionalHandle c)
+{
+    if (threadIdx.x != 0) return;
+    if (d->two) d->n_two += 1;
+    cudaGraphSetConditional(c, d->two ? 1u : 0u);
+}
+
 // One refinement iteration (mixed) or V-cycle (FP64) on phi, then the residual.
-void iterate_once(mg_handle* h, double* phi, float* r32)
+mg_status capture_deps(cudaStream_t s, cudaGraph_t* g, std::vector<cudaGraphNode_t>& deps);
+
+// One refinement step inside the graph's WHILE body (h->stream is capturing).
+// With automatic inner cycles the second V-cycle sits in an IF node whose
+// condition k_set_two takes from the scalar block (set by k_check); its
+// launches are counted into if_launches.
+mg_status iterate_once(mg_handle* h, double* phi, float* r32, cudaStream_t if_stream, long long& if_launches)
 {
     const bool nodal = h->loc == MG_LOC_NODAL;
+    if_launches = 0;
+    if (h->prec == MG_PREC_MIXED && adaptive_cycles(h)) {
+        cudaStream_t s = h->stream;
+        float* e = h->lev[0].x32;
+        if (nodal) vcycle_node<float>(h, e, h->lev[0].b32, true);
+        else vcycle_cell<float>(h, e, h->lev[0].b32, true);
+        cudaGraph_t g;
+        std::vector<cudaGraphNode_t> deps;
+        mg_status rc = capture_deps(s, &g, deps);
+        if (rc != MG_OK) return rc;
+        cudaGraphConditionalHandle ifh;
+        MG_CK(cudaGraphConditionalHandleCreate(&ifh, g, 0, 0));
+        MGP_LAUNCH(k_set_two<<<1, 32, 0, s>>>(h->d, ifh));
+        rc = capture_deps(s, &g, deps);
+        if (rc != MG_OK) return rc;
+        cudaGraphNodeParams prm = {};
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = ifh;
+        prm.conditional.type = cudaGraphCondTypeIf;
+        prm.conditional.size = 1;
+        cudaGraphNode_t ifnode;
+        MG_CK(cudaGraphAddNode(&ifnode, g, deps.data(), nullptr, deps.size(), &prm));
+        MG_CK(cudaStreamUpdateCaptureDependencies(s, &ifnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        cudaGraph_t ifg = prm.conditional.phGraph_out[0];
+        MG_CK(cudaStreamBeginCaptureToGraph(if_stream, ifg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        const long long c0 = launch_count();
+        h->stream = if_stream;
+        if (nodal) vcycle_node<float>(h, e, h->lev[0].b32, false);
+        else vcycle_cell<float>(h, e, h->lev[0].b32, false);
+        h->stream = s;
+        if_launches = launch_count() - c0;
+        MG_CK(cudaStreamEndCapture(if_stream, &ifg));
+        vec_axpy_f32(phi, e, &h->d->fscale, h->lev[0].nvec, s);
+        residual64(h, phi, r32);
+        return MG_OK;
+    }
     if (h->prec == MG_PREC_MIXED) {
-        mixed_correction(h, phi);
+        mixed_correction(h, phi, inner_cycles(h));
     } else {
         if (nodal) vcycle_node<double>(h, phi, h->f64, false);
         else vcycle_cell<double>(h, phi, h->f64, false);
     }
     residual64(h, phi, r32);
+    return MG_OK;
 }
 
 mg_status capture_deps(cudaStream_t s, cudaGraph_t* g, std::vector<cudaGraphNode_t>& deps)
@@ -783,7 +895,8 @@ mg_status capture_deps(cudaStream_t s, cudaGraph_t* g, std::vector<cudaGraphNode
 }
 
 // Enqueue one whole solve of L phi_int = f64 on h->stream, which is capturing.
-mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream, long long& fixed, long long& body)
+mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream, cudaStream_t if_stream,
+                        long long& fixed, long long& body, long long& if_body)
 {
     cudaStream_t s = h->stream;
     const size_t n = h->lev[0].nvec;
@@ -826,7 +939,8 @@ mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream
     cudaGraph_t bodyg = prm.conditional.phGraph_out[0];
     MG_CK(cudaStreamBeginCaptureToGraph(body_stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     h->stream = body_stream;
-    iterate_once(h, phi, r32);
+    rc = iterate_once(h, phi, r32, if_stream, if_body);
+    if (rc != MG_OK) { h->stream = s; cudaStreamEndCapture(body_stream, &bodyg); return rc; }
     MGP_LAUNCH(k_check<<<1, 32, 0, body_stream>>>(h->d, cond, 0));
     h->stream = s;
     MG_CK(cudaStreamEndCapture(body_stream, &bodyg));
@@ -837,35 +951,38 @@ mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream
     MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     const long long c3 = launch_count();
     fixed = (c1 - c0) + (c3 - c2);
-    body = c2 - c1;
+    body = (c2 - c1) - if_body;
     MG_CK(cudaGetLastError());
     return MG_OK;
 }
 
 struct CaptureStreams {
-    cudaStream_t main = nullptr, body = nullptr;
+    cudaStream_t main = nullptr, body = nullptr, inner = nullptr;
     ~CaptureStreams()
     {
         if (main) cudaStreamDestroy(main);
         if (body) cudaStreamDestroy(body);
+        if (inner) cudaStreamDestroy(inner);
     }
     mg_status make()
     {
         MG_CK(cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking));
         MG_CK(cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking));
+        MG_CK(cudaStreamCreateWithFlags(&inner, cudaStreamNonBlocking));
         return MG_OK;
     }
 };
 
 // Capture the handles' solves as independent branches of one graph.
 mg_status build_graph(mg_handle* const* hs, int count, bool rhs_from_io, cudaGraphExec_t* exec,
-                      std::vector<long long>& fixed, std::vector<long long>& body)
+                      std::vector<long long>& fixed, std::vector<long long>& body, std::vector<long long>& ifb)
 {
     CaptureStreams cs;
     mg_status rc = cs.make();
     if (rc != MG_OK) return rc;
     fixed.assign(count, 0);
     body.assign(count, 0);
+    ifb.assign(count, 0);
     MG_CK(cudaStreamBeginCapture(cs.main, cudaStreamCaptureModeRelaxed));
     std::vector<cudaGraphNode_t> join;
     for (int i = 0; i < count && rc == MG_OK; ++i) {
@@ -873,7 +990,7 @@ mg_status build_graph(mg_handle* const* hs, int count, bool rhs_from_io, cudaGra
         cudaStreamUpdateCaptureDependencies(cs.main, nullptr, nullptr, 0, cudaStreamSetCaptureDependencies);
         cudaStream_t saved = hs[i]->stream;
         hs[i]->stream = cs.main;
-        rc = capture_solve(hs[i], rhs_from_io, cs.body, fixed[i], body[i]);
+        rc = capture_solve(hs[i], rhs_from_io, cs.body, cs.inner, fixed[i], body[i], ifb[i]);
         hs[i]->stream = saved;
         cudaGraph_t g;
         std::vector<cudaGraphNode_t> sinks;
@@ -885,7 +1002,7 @@ mg_status build_graph(mg_handle* const* hs, int count, bool rhs_from_io, cudaGra
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs.main, &graph);
     long long captured = 0;
-    for (int i = 0; i < count; ++i) captured += fixed[i] + body[i];
+    for (int i = 0; i < count; ++i) captured += fixed[i] + body[i] + ifb[i];
     add_launches(-captured);  // capture enqueues nothing; replays are counted after each run
     if (rc != MG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -900,19 +1017,20 @@ bool use_graph(const mg_handle* h) { return !(h->opt.flags & MG_FLAG_NO_GRAPH) &
 mg_status ensure_graph(mg_handle* h, int which)
 {
     if (h->gx[which]) return MG_OK;
-    std::vector<long long> f, b;
-    mg_status rc = build_graph(&h, 1, which == 0, &h->gx[which], f, b);
+    std::vector<long long> f, b, fi;
+    mg_status rc = build_graph(&h, 1, which == 0, &h->gx[which], f, b, fi);
     if (rc != MG_OK) return rc;
     h->g_fixed[which] = f[0];
     h->g_body[which] = b[0];
+    h->g_if[which] = fi[0];
     return MG_OK;
 }
 
 // Result of a finished graph solve (the scalar block is in h->hs).
-mg_status graph_result(mg_handle* h, long long fixed, long long body, mg_stats* st)
+mg_status graph_result(mg_handle* h, long long fixed, long long body, long long ifb, mg_stats* st)
 {
     const DevScalars& r = *h->hs;
-    add_launches(fixed + body * r.iters);
+    add_launches(fixed + body * r.iters + ifb * r.n_two);
     if (r.info != 0) return fail(MG_ERR_UNSUPPORTED, "the coarsest-level operator is singular");
     if (st) {
         st->iters = r.iters;
@@ -932,7 +1050,7 @@ mg_status graph_result(mg_handle* h, long long fixed, long long body, mg_stats* 
 struct BatchGraph {
     std::vector<mg_handle*> hs;
     cudaGraphExec_t exec = nullptr;
-    std::vector<long long> fixed, body;
+    std::vector<long long> fixed, body, ifb;
 };
 std::mutex g_batch_mu;
 std::vector<BatchGraph*> g_batches;
@@ -1189,7 +1307,7 @@ mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_
         MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(h->d, rhs, phi, tol, h->opt.max_iters));
         MG_CK(cudaGraphLaunch(h->gx[0], s));
         MG_CK(cudaStreamSynchronize(s));
-        rc = graph_result(h, h->g_fixed[0], h->g_body[0], &local);
+        rc = graph_result(h, h->g_fixed[0], h->g_body[0], h->g_if[0], &local);
     } else {
         vec_copy_f64(h->f64, rhs, n, s);
         if (h->loc == MG_LOC_NODAL) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), h->f64, s);
@@ -1239,11 +1357,12 @@ mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* b0, const
         rc = ensure_graph(h, 1);
         if (rc != MG_OK) return rc;
         MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(h->d, nullptr, phi, tol, h->opt.max_iters));
+        if (h->loc == MG_LOC_CELL) MGP_LAUNCH(k_constraint_tol<<<1, 1, 0, s>>>(h->d));
         MG_CK(cudaGraphLaunch(h->gx[1], s));
         MG_CK(cudaStreamSynchronize(s));
-        rc = graph_result(h, h->g_fixed[1], h->g_body[1], &local);
+        rc = graph_result(h, h->g_fixed[1], h->g_body[1], h->g_if[1], &local);
     } else {
-        rc = solve_core(h, phi, tol, &local);
+        rc = solve_core(h, phi, tol, &local, h->loc == MG_LOC_CELL);
     }
     if (rc == MG_OK || rc == MG_ERR_NOT_CONVERGED) {
         // a9: projection update; a10: constraint
@@ -1327,7 +1446,7 @@ mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double*
     if (!bg) {
         std::unique_ptr<BatchGraph> nb(new BatchGraph());
         nb->hs.assign(hs, hs + count);
-        mg_status rc = build_graph(hs, count, true, &nb->exec, nb->fixed, nb->body);
+        mg_status rc = build_graph(hs, count, true, &nb->exec, nb->fixed, nb->body, nb->ifb);
         if (rc != MG_OK) return rc;
         std::lock_guard<std::mutex> lk(g_batch_mu);
         bg = nb.release();
@@ -1342,7 +1461,7 @@ mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double*
     for (int i = 0; i < count; ++i) {
         mg_stats local;
         memset(&local, 0, sizeof local);
-        mg_status rc = graph_result(hs[i], bg->fixed[i], bg->body[i], &local);
+        mg_status rc = graph_result(hs[i], bg->fixed[i], bg->body[i], bg->ifb[i], &local);
         local.ms = ms;
         local.status = rc;
         if (st) st[i] = local;

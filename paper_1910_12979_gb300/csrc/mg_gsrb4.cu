@@ -18,7 +18,7 @@
 // the diagonal -- is that of k_gsrb (cell_row), so two passes of this kernel
 // equal two passes of k_gsrb bit for bit.  Requirements (checked by the
 // launcher): FP32, nx % 4 == 0.
-#include "mg_device.cuh"
+#include "mg_cellops.cuh"
 
 namespace mgp {
 
@@ -245,7 +245,7 @@ namespace mgp {
 
 // Linear prolongation and correction, x_f += P x_c, four fine cells of a row per
 // thread (one 16-byte read-modify-write); the coarse values come through L1.
-// Same weights and order of operations as k_prolong_add<3, float, 1>.
+// The arithmetic is prolong_value's, as in k_prolong_add.
 __global__ void __launch_bounds__(256)
 k_prolong_add_v4(CellLevel<float> F, CellLevel<float> C, float* __restrict__ xf, const float* __restrict__ xc)
 {
@@ -254,24 +254,10 @@ k_prolong_add_v4(CellLevel<float> F, CellLevel<float> C, float* __restrict__ xf,
     const int k = blockIdx.z;
     if (4 * q >= F.nx || j >= F.ny) return;
     const int i0 = 4 * q;
-    const Lin1D ly = lin1d(j, C.ny, F.bc.lo[1], F.bc.hi[1]);
-    const Lin1D lz = lin1d(k, C.nz, F.bc.lo[2], F.bc.hi[2]);
-    const size_t cpl = (size_t)C.nx * C.ny;
-    const float* rpp = xc + lz.p * cpl + (size_t)ly.p * C.nx;   // (y p, z p)
-    const float* rqp = xc + lz.p * cpl + (size_t)ly.q * C.nx;   // (y q, z p)
-    const float* rpq = xc + lz.q * cpl + (size_t)ly.p * C.nx;   // (y p, z q)
-    const float* rqq = xc + lz.q * cpl + (size_t)ly.q * C.nx;   // (y q, z q)
-    const float w1 = 0.75f, w2 = 0.25f;
     float4 v = *reinterpret_cast<const float4*>(xf + ((size_t)k * F.ny + j) * F.nx + i0);
     float add[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const Lin1D lx = lin1d(i0 + p, C.nx, F.bc.lo[0], F.bc.hi[0]);
-        auto plane = [&](const float* ra, const float* rb) {
-            return w1 * (w1 * ra[lx.p] + w2 * lx.sq * ra[lx.q]) + w2 * ly.sq * (w1 * rb[lx.p] + w2 * lx.sq * rb[lx.q]);
-        };
-        add[p] = w1 * plane(rpp, rqp) + w2 * lz.sq * plane(rpq, rqq);
-    }
+    for (int p = 0; p < 4; ++p) add[p] = prolong_value<3>(F, C, xc, i0 + p, j, k, 1);
     v.x += add[0];
     v.y += add[1];
     v.z += add[2];

@@ -65,9 +65,12 @@ struct DevScalars {
     int info;                  // dense coarsest factorisation: 0 ok, k > 0 zero pivot
     int iters, stall, status;  // iteration count, stalled iterations, mg_status
     int maxit;
-    int pad_i;
+    int adaptive;              // mixed, automatic inner cycles: one or two V-cycles per step
     const double* rhs_in;      // caller rhs of the current call (graph mode)
     double* phi_io;            // caller phi of the current call (graph mode)
+    double prev_rel;           // relative residual before the last refinement step
+    int two;                   // the next refinement step runs a second V-cycle
+    int n_two;                 // refinement steps that ran a second V-cycle (launch accounting)
 };
 
 // Every kernel launch of the library goes through MGP_LAUNCH, which counts it
@@ -128,6 +131,16 @@ void cell_project(int dim, const CellLevel<double>& L, const double* h, const do
                   const double* const b0f[3], double* const U[3], cudaStream_t s);
 template <typename T>
 void cell_dense_assemble(int dim, const CellLevel<T>& L, double* A, int lda, cudaStream_t s);
+
+// The coarse end of a cell V-cycle in one CTA (levels of at most kCoarseCells
+// cells, at most kCoarseMaxLevels of them): zero (all but the first level
+// unless zero_first), nu1 colour sweeps, residual restriction, dense bottom
+// solve, prolongation, nu2 sweeps; same arithmetic as the launched kernels.
+constexpr int kCoarseCells = 512;
+constexpr int kCoarseMaxLevels = 8;
+template <typename T>
+void coarse_cycle(int dim, int nlev, const CellLevel<T>* L, T* const* x, T* const* b, const double* Minv, int Nd,
+                  int nu1, int nu2, int order, bool zero_first, cudaStream_t s);
 
 // Nodal system.
 void node_coarsen_sigma(int dim, const NodeLevel<double>& F, const NodeLevel<double>& C, double* sc,

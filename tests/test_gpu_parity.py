@@ -197,6 +197,39 @@ def test_nodal_projection_ragged_tiles(oracle, prec, n, lo, hi):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,lo,hi", [((40, 24, 16), ("dirichlet",) * 3, ("dirichlet",) * 3),
+                                     ((36, 20, 12), ("periodic", "neumann", "dirichlet"),
+                                      ("periodic", "dirichlet", "neumann")),
+                                     ((30, 18, 10), ("neumann", "periodic", "neumann"),
+                                      ("dirichlet", "periodic", "neumann"))])
+def test_mac_projection_ragged_grids(oracle, prec, n, lo, hi):
+    """MAC projection on grids whose widths are not multiples of the vectorised
+    kernels' quads or tiles on some levels (36 -> 18 -> 9, 30 -> 15), with walls,
+    outflow faces and periodic axes, against the oracle."""
+    O = oracle
+    rng = np.random.default_rng(43)
+    geom = I.geometry(n, lo, hi)
+    geom["h"] = (1.0 / 40,) * 3
+    g = ogrid(O, geom)
+    sigma = np.exp(0.5 * rng.normal(size=g.cell_shape))
+    beta0 = np.exp(0.3 * rng.normal(size=g.cell_shape))
+    b0f = [np.exp(0.3 * rng.normal(size=g.face_shape(d))) for d in range(3)]
+    U = [rng.normal(size=g.face_shape(d)) for d in range(3)]
+    S = rng.normal(size=g.cell_shape)
+    ref = O.mac_project(g, sigma, beta0, b0f, U, S, tol=1e-14)
+    s = ProjectionSolver(geom, T(sigma), loc="cell", prec=prec)
+    Ud = [T(u) for u in U]
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.project(Ud, T(beta0), T(S), beta0_face=[T(b) for b in b0f], phi=phi, tol=1e-10)
+    assert relerr(gauge(H(phi), g.singular), gauge(ref["phi"], g.singular)) <= TOL[prec]
+    for d in range(3):
+        assert relerr(H(Ud[d]), ref["U"][d]) <= TOL[prec]
+    # the MAC stopping rule also bounds the constraint by tol (relative to ||beta0 S||)
+    assert st["rel_constraint"] <= 1e-10 * 1.01
+    s.close()
+
+
 def test_polytrope_dirichlet_projection(oracle):
     O = oracle
     p = I.polytrope_star(32, seed=5)
@@ -252,7 +285,7 @@ def test_config3_256_properties(oracle):
     B = O.mac_faces(g, p["sigma"])
     f = O.mac_rhs(g, p["beta0"], p["beta0_face"], p["U_mac"], p["S"])
     rel = np.linalg.norm(f - O.mac_apply(g, B, ph)) / np.linalg.norm(f)
-    assert rel <= 1e-10 * 1.01 and abs(rel - st["rel_resid"]) <= 1e-3 * rel
+    assert rel <= 1e-10 * 1.01 and abs(rel - st["rel_resid"]) <= max(1e-3 * rel, 1e-15)
     div = O.mac_rhs(g, p["beta0"], p["beta0_face"], [H(u) for u in U], p["S"])
     src = np.linalg.norm(p["beta0"] * p["S"])
     assert np.linalg.norm(div) / src == pytest.approx(st["rel_constraint"], rel=1e-3)

@@ -163,7 +163,8 @@ typedef struct {
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
  * over cells, nodal ||D_N(beta0 U) - S_N||/||S_N|| over unknown nodes (a
- * diagnostic: the nodal projection is approximate).  ms: wall time of the call. */
+ * diagnostic: the nodal projection is approximate).  ms: wall time of the call.
+ * iters: refinement steps (mixed) or V-cycles (FP64); vcycles: V-cycles run. */
 typedef struct {
     int iters;
     double rel_resid;
@@ -172,6 +173,7 @@ typedef struct {
     double src_norm;
     double ms;
     int status;
+    int vcycles;
 } mg_stats;
 
 typedef struct mg_handle mg_handle;

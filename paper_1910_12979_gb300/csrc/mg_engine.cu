@@ -695,13 +695,16 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st, bool c
     int stall = 0, it = 0;
     mg_status status = MG_OK;
     const bool adaptive = adaptive_cycles(h);
-    int two = next_two(true, true, 0.0, rel, tol);
+    int two = next_two(true, true, 0.0, rel, tol), vcyc = 0;
     double prev = rel;
     while (rel > tol) {
         if (it >= h->opt.max_iters) { status = MG_ERR_NOT_CONVERGED; break; }
         if (mixed) {
-            mixed_correction(h, phi, adaptive ? (two ? 2 : 1) : inner_cycles(h));
+            const int m = adaptive ? (two ? 2 : 1) : inner_cycles(h);
+            mixed_correction(h, phi, m);
+            vcyc += m;
         } else {
+            vcyc += 1;
             if (nodal) vcycle_node<double>(h, phi, h->f64, false);
             else vcycle_cell<double>(h, phi, h->f64, false);
         }
@@ -718,7 +721,7 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st, bool c
         prev = rel;
     }
     if (h->singular) gauge(h, phi);
-    if (st) { st->iters = it; st->rel_resid = rel; }
+    if (st) { st->iters = it; st->rel_resid = rel; st->vcycles = vcyc; }
     if (status != MG_OK) {
         char buf[160];
         snprintf(buf, sizeof buf, "stopped after %d iterations at relative residual %.3e (tol %.3e)", it, rel, tol);
@@ -1036,6 +1039,9 @@ mg_status graph_result(mg_handle* h, long long fixed, long long body, long long 
         st->iters = r.iters;
         st->rel_resid = r.rel;
         st->rhs_norm = sqrt(r.fnorm2);
+        st->vcycles = h->prec == MG_PREC_MIXED
+                          ? (adaptive_cycles(h) ? r.iters + r.n_two : r.iters * inner_cycles(h))
+                          : r.iters;
     }
     if (r.status != MG_OK) {
         char buf[160];

@@ -53,7 +53,7 @@ class mg_options(ctypes.Structure):
 class mg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_resid", ctypes.c_double), ("rel_constraint", ctypes.c_double),
                 ("rhs_norm", ctypes.c_double), ("src_norm", ctypes.c_double), ("ms", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("vcycles", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

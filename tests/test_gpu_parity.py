@@ -230,6 +230,37 @@ def test_mac_projection_ragged_grids(oracle, prec, n, lo, hi):
     s.close()
 
 
+@pytest.mark.parametrize("loc", ["cell", "nodal"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_two_dimensional_projection(oracle, loc, prec):
+    """2-D projections (periodic x, wall below, outflow above) against the oracle."""
+    O = oracle
+    rng = np.random.default_rng(44)
+    geom = I.geometry((48, 32), ("periodic", "neumann"), ("periodic", "dirichlet"))
+    geom["h"] = (1.0 / 48,) * 2
+    g = ogrid(O, geom)
+    sigma = np.exp(0.5 * rng.normal(size=g.cell_shape))
+    beta0 = np.exp(0.3 * rng.normal(size=g.cell_shape))
+    S = rng.normal(size=g.cell_shape)
+    s = ProjectionSolver(geom, T(sigma), loc=loc, prec=prec)
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    if loc == "cell":
+        b0f = [np.exp(0.3 * rng.normal(size=g.face_shape(d))) for d in range(2)]
+        U = [rng.normal(size=g.face_shape(d)) for d in range(2)]
+        ref = O.mac_project(g, sigma, beta0, b0f, U, S, tol=1e-14)
+        Ud = [T(u) for u in U]
+        s.project(Ud, T(beta0), T(S), beta0_face=[T(b) for b in b0f], phi=phi, tol=1e-11)
+    else:
+        U = [rng.normal(size=g.cell_shape) for _ in range(2)]
+        ref = O.nodal_project(g, sigma, beta0, U, S, tol=1e-14)
+        Ud = [T(u) for u in U]
+        s.project(Ud, T(beta0), T(S), phi=phi, tol=1e-11)
+    assert relerr(H(phi), ref["phi"].reshape(H(phi).shape)) <= TOL[prec]
+    for d in range(2):
+        assert relerr(H(Ud[d]), ref["U"][d].reshape(H(Ud[d]).shape)) <= TOL[prec]
+    s.close()
+
+
 def test_polytrope_dirichlet_projection(oracle):
     O = oracle
     p = I.polytrope_star(32, seed=5)

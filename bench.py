@@ -246,7 +246,9 @@ def run_batch(args, dev, world, dist):
     stream.synchronize()
     tols = [args.tol] * len(solvers)
     kind_names = {0: "default", 1: "4-cell passes, 8 quads/row", 2: "4-cell passes, 16 quads/row",
-                  3: "4-cell passes, 32 quads/row", 4: "pipelined one-launch sweep"}
+                  3: "4-cell passes, 32 quads/row", 4: "pipelined one-launch sweep",
+                  5: "4-node passes, 8 quads/row, 4 planes/thread", 6: "4-node passes, 16 quads/row, 4 planes/thread",
+                  7: "4-node passes, 32 quads/row, 4 planes/thread"}
     tuned = {}
     for sp, s in zip(specs, solvers):
         tuned.setdefault(f"{sp['n']}^3", [kind_names.get(N.mg_smoother_kind(s.handle, l), "?")

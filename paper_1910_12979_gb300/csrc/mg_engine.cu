@@ -1096,9 +1096,11 @@ double now_ms()
 // ---- smoother kernel autotuner (MG_FLAG_AUTOTUNE)
 //
 // For every FP32 level but the coarsest, the candidate smoother kernels -- the
-// four-cell / four-node passes with 8, 16 or 32 quads per block row, and the
+// four-cell / four-node passes with 8, 16 or 32 quads per block row (for nodes
+// also marching four planes per thread), and the
 // shared-memory pipelined (cells) or tiled (nodes) kernel where the level
-// allows it -- each run one sweep on the level's scratch vectors, timed with
+// allows it -- each run two sweeps (the default smoothing count, so that a
+// ping-ponging kernel ends in place) on the level's scratch vectors, timed with
 // CUDA events on the handle's stream (one untimed call, then the best of
 // three), and the fastest is kept in Level::kind.  All candidates compute the
 // same arithmetic, so the choice changes no result.  Choices are cached per
@@ -1135,7 +1137,10 @@ mg_status autotune(mg_handle* h)
         if (nodal) {
             if (node_v4_ok(h->dim, nview<float>(h, l), x, t, b))
                 for (int k = 1; k <= 3; ++k)
-                    if ((4 << k) <= v.N[0] / 4) cand.push_back(k);
+                    if ((4 << k) <= v.N[0] / 4) {
+                        cand.push_back(k);
+                        cand.push_back(k + 4);   // the same shape marching four planes
+                    }
             if (h->dim == 3 && v.N[0] >= 32 && v.N[1] >= 8) cand.push_back(4);
         } else {
             const CellLevel<float> V = cview<float>(h, l);
@@ -1154,8 +1159,8 @@ mg_status autotune(mg_handle* h)
                 float ms = 1e30f;
                 for (int rep = 0; rep < 4 && rc == MG_OK; ++rep) {
                     cudaEventRecord(e0, s);
-                    if (nodal) node_smooth<float>(h, l, x, b, 1);
-                    else cell_smooth<float>(h, l, cview<float>(h, l), x, b, 1);
+                    if (nodal) node_smooth<float>(h, l, x, b, 2);
+                    else cell_smooth<float>(h, l, cview<float>(h, l), x, b, 2);
                     cudaEventRecord(e1, s);
                     float m = 0.f;
                     const cudaError_t e = cudaEventSynchronize(e1);

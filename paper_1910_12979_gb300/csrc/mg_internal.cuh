@@ -16,6 +16,7 @@ namespace mgp {
 
 enum { BCP = 0, BCN = 1, BCD = 2 };
 
+constexpr int kNumSMs = 152;        // SMs of a GB300 (two dies of 76)
 constexpr int kRedBlocks = 608;     // 4 x 152 SMs: fixed grid of every reduction kernel
 constexpr int kRedSlots = 4;        // quantities one reduction pass may accumulate
 constexpr int kMaxLevels = 16;
@@ -149,7 +150,9 @@ void node_invdiag(int dim, const NodeLevel<double>& L, double* invd, cudaStream_
 void node_diag(int dim, const NodeLevel<double>& L, double* diag, cudaStream_t s);
 // tiled: allow the shared-memory tiled kernel (3-D levels of at least 32 x 8 nodes)
 // kind: 0 the default choice; 1..3 the four-node kernel with 8/16/32 quads per
-// block row; 4 the shared-memory tiled kernel (when the level allows each)
+// block row, one plane per thread; 4 the shared-memory tiled kernel; 5..7 the
+// four-node kernel with 8/16/32 quads per block row marching four planes (when
+// the level allows each)
 template <typename T>
 void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s,
                  int kind = 0);
@@ -161,10 +164,12 @@ void node_restrict(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, const 
 template <typename T>
 void node_prolong_add(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, T* xf, const T* xc, cudaStream_t s);
 // FP32 3-D levels with x periodic and nx % 4 == 0: Jacobi sweep / residual with
-// four nodes per thread (same results as the plain kernels)
+// four nodes per thread (same results as the plain kernels); bxw quads per
+// block row (0: by the row length), kz node planes marched per thread (1 or 4;
+// 0: by the level size)
 bool node_v4_ok(int dim, const NodeLevel<float>& L, const float* x, const float* out, const float* b);
 void node_v4(const NodeLevel<float>& L, const float* x, float* out, const float* b, float omega, bool resid,
-             cudaStream_t s, int bxw = 0);
+             cudaStream_t s, int bxw = 0, int kz = 0);
 bool node_prolong_v4_ok(int dim, const NodeLevel<float>& F, const float* xf);
 void node_prolong_v4(const NodeLevel<float>& F, const NodeLevel<float>& C, float* xf, const float* xc, cudaStream_t s);
 void node_resid64(int dim, const NodeLevel<double>& L, const double* x, const double* b, float* r32,

@@ -622,13 +622,17 @@ static void launch_node_tiled(const NodeLevel<T>& L, const T* x, T* out, const T
     MGP_LAUNCH(k_node_tiled<T, RESID><<<g, dim3(kNTX, kNTY), smem, s>>>(L, x, out, b, omega, kz));
 }
 
+// quads per block row and planes per thread of the four-node kernel for a smoother kind
+static int v4_width(int kind) { return kind >= 1 && kind <= 3 ? 4 << kind : kind >= 5 && kind <= 7 ? 4 << (kind - 4) : 0; }
+static int v4_planes(int kind) { return kind >= 1 && kind <= 3 ? 1 : kind >= 5 && kind <= 7 ? 4 : 0; }
+
 template <typename T>
 void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s,
                  int kind)
 {
     if constexpr (std::is_same<T, float>::value) {
         if (tiled && kind != 4 && node_v4_ok(dim, L, x, xo, b)) {
-            node_v4(L, x, xo, b, omega, false, s, kind >= 1 && kind <= 3 ? 4 << kind : 0);
+            node_v4(L, x, xo, b, omega, false, s, v4_width(kind), v4_planes(kind));
             return;
         }
     }
@@ -646,7 +650,7 @@ void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bo
 {
     if constexpr (std::is_same<T, float>::value) {
         if (tiled && kind != 4 && node_v4_ok(dim, L, x, r, b)) {
-            node_v4(L, x, r, b, 0.f, true, s, kind >= 1 && kind <= 3 ? 4 << kind : 0);
+            node_v4(L, x, r, b, 0.f, true, s, v4_width(kind), v4_planes(kind));
             return;
         }
     }

@@ -5,7 +5,12 @@
 // need -- phi on the 3 x 3 rows/planes around them (16-byte loads plus the two
 // x-neighbours), sigma of the 2 x 2 cell rows/planes (16-byte loads plus the
 // cell left of the quad) and b -- instead of staging tiles in shared memory;
-// warps cover 32 consecutive quads, so every access is coalesced.  Cells
+// warps cover 32 consecutive quads, so every access is coalesced.  With KZ > 1
+// a thread marches up KZ node planes and keeps a rolling window of three phi
+// planes and two sigma planes, so each plane costs 3 phi rows, 2 sigma rows and
+// b (14 loads) instead of 9 + 4 + 1 (36), with the row and boundary index work
+// done once per thread (the one-plane kernel is bound by instruction issue,
+// not bytes), and the loads of a step are issued a step ahead of their use.  Cells
 // outside a non-periodic boundary read sigma 0 and add 0 * (...), which leaves
 // the sums unchanged.  The row arithmetic -- cells in node_row's order, the four
 // phi of a cell summed left to right, the fused multiply-adds -- is that of
@@ -22,49 +27,64 @@ __device__ __forceinline__ float4 nld4(const float* p) { return *reinterpret_cas
 
 }  // namespace
 
-template <bool RESID>
-__global__ void __launch_bounds__(256, 4)
+template <bool RESID, int KZ>
+__global__ void __launch_bounds__(256, KZ > 1 ? 2 : 4)
 k_node_jacobi_v4(NodeLevel<float> L, const float* __restrict__ x, float* __restrict__ out,
                  const float* __restrict__ b, float omega)
 {
     const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+    const int k0 = blockIdx.z * KZ;
     if (4 * q >= Nx || j >= Ny) return;
     const int i0 = 4 * q;
-    const bool py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
+    const bool pz = L.bc.lo[2] == BCP;
     const size_t nplane = (size_t)Nx * Ny, cplane = (size_t)nx * ny;
-
-    // one node plane k + dz of phi: rows j - 1 .. j + 1, columns i0 - 1 .. i0 + 4 (x periodic)
-    auto load_phi = [&](int dz, float (&r)[3][6]) {
+    const int il = i0 > 0 ? i0 - 1 : Nx - 1, ih = i0 + 4 < Nx ? i0 + 4 : 0;   // x periodic: Nx == nx
+    // offsets within a plane of node rows j - 1 .. j + 1 and of cell rows j - 1, j (-1: absent)
+    int prow[3], crow[2];
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            int jj = j + dy, kk = k + dz;
-            bool ok = true;
-            if (jj < 0 || jj >= Ny) { if (py) jj = jj < 0 ? jj + Ny : jj - Ny; else ok = false; }
-            if (kk < 0 || kk >= Nz) { if (pz) kk = kk < 0 ? kk + Nz : kk - Nz; else ok = false; }
-            if (ok) {
-                const float* row = x + (size_t)kk * nplane + (size_t)jj * Nx;
+    for (int dy = 0; dy < 3; ++dy) {
+        int jj = j - 1 + dy;
+        if (jj < 0 || jj >= Ny) jj = L.bc.lo[1] == BCP ? (jj < 0 ? jj + Ny : jj - Ny) : -1;
+        prow[dy] = jj < 0 ? -1 : jj * Nx;
+    }
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy) {
+        int cj;
+        crow[cy] = cell_ok(j - 1 + cy, ny, L.bc.lo[1], cj) ? cj * nx : -1;
+    }
+
+    // one node plane kk of phi: rows j - 1 .. j + 1, columns i0 - 1 .. i0 + 4
+    auto load_phi = [&](int kk, float (&r)[3][6]) {
+        bool ok = true;
+        if (kk < 0 || kk >= Nz) { if (pz) kk = kk < 0 ? kk + Nz : kk - Nz; else ok = false; }
+        const float* pl = x + (size_t)(ok ? kk : 0) * nplane;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            if (ok && prow[dy] >= 0) {
+                const float* row = pl + prow[dy];
                 const float4 v = nld4(row + i0);
-                r[dy + 1][0] = row[i0 > 0 ? i0 - 1 : Nx - 1];
-                r[dy + 1][1] = v.x; r[dy + 1][2] = v.y; r[dy + 1][3] = v.z; r[dy + 1][4] = v.w;
-                r[dy + 1][5] = row[i0 + 4 < Nx ? i0 + 4 : 0];
+                r[dy][0] = row[il];
+                r[dy][1] = v.x; r[dy][2] = v.y; r[dy][3] = v.z; r[dy][4] = v.w;
+                r[dy][5] = row[ih];
             } else {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) r[dy + 1][c] = 0.f;
+                for (int c = 0; c < 6; ++c) r[dy][c] = 0.f;
             }
         }
     };
-    // one cell plane k - 1 + cz of sigma: rows j - 1, j; columns i0 - 1 .. i0 + 3 (0 outside)
-    auto load_sig = [&](int cz, float (&r)[2][5]) {
+    // one cell plane ckr of sigma: rows j - 1, j; columns i0 - 1 .. i0 + 3 (0 outside)
+    auto load_sig = [&](int ckr, float (&r)[2][5]) {
+        int ck = 0;
+        const bool okz = cell_ok(ckr, nz, L.bc.lo[2], ck);
+        const float* pl = L.sigma + (size_t)(okz ? ck : 0) * cplane;
 #pragma unroll
         for (int cy = 0; cy < 2; ++cy) {
-            int cj, ck;
-            if (cell_ok(j - 1 + cy, ny, L.bc.lo[1], cj) && cell_ok(k - 1 + cz, nz, L.bc.lo[2], ck)) {
-                const float* row = L.sigma + (size_t)ck * cplane + (size_t)cj * nx;
+            if (okz && crow[cy] >= 0) {
+                const float* row = pl + crow[cy];
                 const float4 v = nld4(row + i0);
-                r[cy][0] = row[i0 > 0 ? i0 - 1 : nx - 1];
+                r[cy][0] = row[il];
                 r[cy][1] = v.x; r[cy][2] = v.y; r[cy][3] = v.z; r[cy][4] = v.w;
             } else {
 #pragma unroll
@@ -72,48 +92,79 @@ k_node_jacobi_v4(NodeLevel<float> L, const float* __restrict__ x, float* __restr
             }
         }
     };
-    float acc[4] = {0.f, 0.f, 0.f, 0.f}, ssum[4] = {0.f, 0.f, 0.f, 0.f};
-    float xi[4];
-    // the cells below the node plane (node_row's c = 0..3), then those above (c = 4..7);
-    // pm: the node plane on the cells' far side, p0: node plane k
-    float p0[3][6], pm[3][6], sg[2][5];
-    load_phi(0, p0);
-#pragma unroll
-    for (int p = 0; p < 4; ++p) xi[p] = p0[1][p + 1];
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        load_phi(half ? 1 : -1, pm);
-        load_sig(half, sg);
+
+    // rolling window of node planes k - 1 .. k + 1 and cell planes k - 1, k.  The
+    // eight cells of a node are summed in node_row's order: the four below the
+    // node plane (half 0), then the four above (half 1).  Half 0 of plane k + 1
+    // needs nothing newer than plane k + 1, so it is computed in step k, after
+    // half 1 of plane k, while the loads of planes k + 2 (phi) and k + 1
+    // (sigma), issued at the top of step k, are in flight: a load has a whole
+    // step of arithmetic to arrive.
+    float P[3][3][6], S[2][2][5];
+    float acc[4], ssum[4];
+    const float c12 = L.ih2 / 12.f, c3 = L.ih2 / 3.f;
+    // cells on one side of node plane k: pc = plane k, pm = the node plane on the cells' far side
+    auto half_sum = [&](const float(&pc)[3][6], const float(&pm)[3][6], const float(&sg)[2][5]) {
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1;
-                const float s = sg[sy > 0 ? 1 : 0][sx > 0 ? p + 1 : p];
+                const float sv = sg[sy > 0 ? 1 : 0][sx > 0 ? p + 1 : p];
                 const int a = p + 1 + sx;  // phi column of node i + sx
-                const float v = ((p0[1 + sy][a] + pm[1][a]) + pm[1 + sy][p + 1]) + pm[1 + sy][a];
-                acc[p] = fmadd(s, v, acc[p]);
-                ssum[p] += s;
+                const float v = ((pc[1 + sy][a] + pm[1][a]) + pm[1 + sy][p + 1]) + pm[1 + sy][a];
+                acc[p] = fmadd(sv, v, acc[p]);
+                ssum[p] += sv;
             }
+    };
+    load_phi(k0 - 1, P[0]);
+    load_phi(k0, P[1]);
+    load_sig(k0 - 1, S[0]);
+    if (KZ > 1) {
+        load_phi(k0 + 1, P[2]);
+        load_sig(k0, S[1]);
     }
-    const float4 bb = nld4(b + (size_t)k * nplane + (size_t)j * Nx + i0);
-    const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
-    const float c12 = L.ih2 / 12.f, c3 = L.ih2 / 3.f;
-    float res[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const float off = acc[p] * c12;
-        const float dg = -ssum[p] * c3;
-        if (node_dirichlet(L, i0 + p, j, k, 3)) {
-            res[p] = 0.f;
-        } else if (RESID) {
-            res[p] = bv[p] - fmadd(dg, xi[p], off);
-        } else {
-            res[p] = fmadd(omega * (bv[p] - fmadd(dg, xi[p], off)), recip(dg), xi[p]);
+    for (int p = 0; p < 4; ++p) acc[p] = ssum[p] = 0.f;
+    half_sum(P[1], P[0], S[0]);
+#pragma unroll
+    for (int t = 0; t < KZ; ++t) {
+        const int k = k0 + t;
+        if (k >= Nz) break;
+        const bool more = t + 1 < KZ && k + 1 < Nz;   // node plane k + 1 belongs to this thread
+        if (KZ == 1) {
+            load_phi(k + 1, P[2]);
+            load_sig(k, S[1]);
+        } else if (more) {
+            load_phi(k + 2, P[t % 3]);
+            load_sig(k + 1, S[t % 2]);
+        }
+        const size_t id = (size_t)k * nplane + (size_t)j * Nx + i0;
+        const float4 bb = nld4(b + id);
+        const float(&pc)[3][6] = P[(t + 1) % 3];
+        half_sum(pc, P[(t + 2) % 3], S[(t + 1) % 2]);
+        const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
+        float res[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const float xi = pc[1][p + 1];
+            const float off = acc[p] * c12;
+            const float dg = -ssum[p] * c3;
+            if (node_dirichlet(L, i0 + p, j, k, 3)) {
+                res[p] = 0.f;
+            } else if (RESID) {
+                res[p] = bv[p] - fmadd(dg, xi, off);
+            } else {
+                res[p] = fmadd(omega * (bv[p] - fmadd(dg, xi, off)), recip(dg), xi);
+            }
+        }
+        *reinterpret_cast<float4*>(out + id) = make_float4(res[0], res[1], res[2], res[3]);
+        if (more) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc[p] = ssum[p] = 0.f;
+            half_sum(P[(t + 2) % 3], pc, S[(t + 1) % 2]);
         }
     }
-    *reinterpret_cast<float4*>(out + (size_t)k * nplane + (size_t)j * Nx + i0) =
-        make_float4(res[0], res[1], res[2], res[3]);
 }
 
 bool node_v4_ok(int dim, const NodeLevel<float>& L, const float* x, const float* out, const float* b)
@@ -124,14 +175,24 @@ bool node_v4_ok(int dim, const NodeLevel<float>& L, const float* x, const float*
 }
 
 void node_v4(const NodeLevel<float>& L, const float* x, float* out, const float* b, float omega, bool resid,
-             cudaStream_t s, int bxw)
+             cudaStream_t s, int bxw, int kz)
 {
     const int nq = L.Nx / 4;
     const int bx = bxw > 0 ? bxw : nq >= 32 ? 32 : nq >= 16 ? 16 : nq >= 8 ? 8 : nq >= 4 ? 4 : 2;
     const dim3 block(bx, 256 / bx);
-    const dim3 grid((nq + bx - 1) / bx, (L.Ny + block.y - 1) / block.y, L.Nz);
-    if (resid) MGP_LAUNCH(k_node_jacobi_v4<true><<<grid, block, 0, s>>>(L, x, out, b, omega));
-    else MGP_LAUNCH(k_node_jacobi_v4<false><<<grid, block, 0, s>>>(L, x, out, b, omega));
+    const long long cols = (long long)((nq + bx - 1) / bx) * ((L.Ny + block.y - 1) / block.y);
+    // default: march four planes per thread where that still leaves at least
+    // two waves of two resident blocks per SM
+    if (kz <= 0) kz = cols * ((L.Nz + 3) / 4) >= 4LL * kNumSMs ? 4 : 1;
+    kz = kz == 4 ? 4 : 1;
+    const dim3 grid((nq + bx - 1) / bx, (L.Ny + block.y - 1) / block.y, (L.Nz + kz - 1) / kz);
+    if (kz == 4) {
+        if (resid) MGP_LAUNCH(k_node_jacobi_v4<true, 4><<<grid, block, 0, s>>>(L, x, out, b, omega));
+        else MGP_LAUNCH(k_node_jacobi_v4<false, 4><<<grid, block, 0, s>>>(L, x, out, b, omega));
+    } else {
+        if (resid) MGP_LAUNCH(k_node_jacobi_v4<true, 1><<<grid, block, 0, s>>>(L, x, out, b, omega));
+        else MGP_LAUNCH(k_node_jacobi_v4<false, 1><<<grid, block, 0, s>>>(L, x, out, b, omega));
+    }
 }
 
 }  // namespace mgp

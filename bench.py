@@ -61,11 +61,16 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=24.0, help="serve: device-memory budget of the slots")
     ap.add_argument("--inflight", type=int, default=8, help="serve: concurrent solves")
     ap.add_argument("--serve-count", type=int, default=256, help="serve: requests per arrival rate")
-    ap.add_argument("--sweep", default="v4", choices=["v4", "pipe"],
-                    help="FP32 cell smoother: two vectorised colour passes (v4) or the pipelined one-launch "
-                         "sweep (pipe, MG_FLAG_SWEEP_PIPE)")
+    ap.add_argument("--sweep", default="v4", choices=["v4", "pipe", "tma"],
+                    help="FP32 cell smoother: two vectorised colour passes (v4), the pipelined one-launch "
+                         "sweep (pipe, MG_FLAG_SWEEP_PIPE) or the TMA-staged one-pass sweep (tma, MG_FLAG_SWEEP_TMA)")
     ap.add_argument("--inner-mac", type=int, default=0,
                     help="FP32 V-cycles per FP64 refinement step of the MAC solve (0: the library's choice)")
+    ap.add_argument("--nu", default="2,1",
+                    help="pre,post smoothing sweeps of the MAC V-cycle (nodal: --nu-nodal)")
+    ap.add_argument("--nu-nodal", default="2,2", help="pre,post smoothing sweeps of the nodal V-cycle")
+    ap.add_argument("--inner-nodal", type=int, default=0,
+                    help="FP32 V-cycles per FP64 refinement step of the nodal solve (0: the library's choice)")
     ap.add_argument("--coarsest", type=int, default=0,
                     help="largest coarsest-level size handed to the dense solve (0: the library's default)")
     ap.add_argument("--only-mixed", action="store_true",
@@ -190,7 +195,7 @@ class Clocks:
 
 
 # the source files whose change invalidates a kernel class's ncu counters
-PROF_SOURCES = {"cell_smooth_fine": ["mg_gsrb4.cu", "mg_sweep.cu", "mg_cell.cu"],
+PROF_SOURCES = {"cell_smooth_fine": ["mg_gsrb_tma.cu", "mg_gsrb4.cu", "mg_sweep.cu", "mg_cell.cu"],
                 "node_smooth_fine": ["mg_nodal4.cu", "mg_nodal.cu", "mg_nodal.cuh"],
                 "cell_restrict_fine": ["mg_gsrb4.cu", "mg_cell.cu"], "cell_resid64": ["mg_cell.cu"],
                 "node_resid64": ["mg_nodal.cu", "mg_nodal.cuh"]}
@@ -248,7 +253,7 @@ def run_batch(args, dev, world, dist):
     kind_names = {0: "default", 1: "4-cell passes, 8 quads/row", 2: "4-cell passes, 16 quads/row",
                   3: "4-cell passes, 32 quads/row", 4: "pipelined one-launch sweep",
                   5: "4-node passes, 8 quads/row, 4 planes/thread", 6: "4-node passes, 16 quads/row, 4 planes/thread",
-                  7: "4-node passes, 32 quads/row, 4 planes/thread"}
+                  7: "4-node passes, 32 quads/row, 4 planes/thread", 8: "TMA-staged one-pass sweep"}
     tuned = {}
     for sp, s in zip(specs, solvers):
         tuned.setdefault(f"{sp['n']}^3", [kind_names.get(N.mg_smoother_kind(s.handle, l), "?")
@@ -592,12 +597,14 @@ def main():
 
     def make(prec):
         # every step starts the solves from phi = 0 (the step zeroes phi anyway)
-        fl = N.MG_FLAG_ZERO_GUESS | (N.MG_FLAG_SWEEP_PIPE if args.sweep == "pipe" else 0)
+        fl = N.MG_FLAG_ZERO_GUESS | {"v4": 0, "pipe": N.MG_FLAG_SWEEP_PIPE, "tma": N.MG_FLAG_SWEEP_TMA}[args.sweep]
         cm = {"coarsest_max": args.coarsest} if args.coarsest > 0 else {}
+        nu_c = [int(v) for v in args.nu.split(",")]
+        nu_n = [int(v) for v in args.nu_nodal.split(",")]
         mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream, flags=fl,
-                               inner_cycles=args.inner_mac, **cm)
+                               inner_cycles=args.inner_mac, nu1=nu_c[0], nu2=nu_c[1], **cm)
         nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream, flags=N.MG_FLAG_ZERO_GUESS,
-                               **cm)
+                               inner_cycles=args.inner_nodal, nu1=nu_n[0], nu2=nu_n[1], **cm)
         phim = torch.zeros(mac.vec_shape, dtype=torch.float64, device=dev)
         phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)
         return mac, nod, phim, phin
@@ -694,7 +701,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": dict(workload_config(n, args.tol), parallelism=f"independent solves x{world}",
-                           cell_smoother=args.sweep),
+                           cell_smoother=args.sweep, smoothing={"mac": args.nu, "nodal": args.nu_nodal}),
             "clocks": clocks, "gpu_launches": launches, "roofline": roof_line,
             "solver": {"mac": {k: st_mac[k] for k in ("iters", "vcycles", "rel_resid", "rel_constraint")},
                        "nodal": {k: st_nod[k] for k in ("iters", "vcycles", "rel_resid", "rel_constraint")}}}

@@ -159,6 +159,12 @@ typedef struct {
  * is then f itself and costs no operator application (one FP64 residual fewer
  * per solve).  phi is still written with the solution. */
 #define MG_FLAG_ZERO_GUESS 16
+/* flags: FP32 3-D cell levels with 32 <= nx <= 256, nx % 4 == 0, ny % 4 == 0
+ * and z not periodic sweep with the one-pass kernel whose operands are staged
+ * in shared memory by bulk asynchronous (TMA) copies: red and black of a sweep
+ * in one pass over memory (same arithmetic).  A stage copy that does not
+ * complete within about two seconds makes the solve return MG_ERR_CUDA. */
+#define MG_FLAG_SWEEP_TMA 32
 
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
@@ -378,8 +384,8 @@ mg_status mg_reciprocal_f64(const double* x, double* y, size_t n, void* stream);
 /* The smoother kernel a level uses: 0 the default rule, 1..3 the vectorised
  * passes with 8/16/32 quads per block row, 4 the shared-memory kernel, 5..7
  * (nodal levels) the vectorised passes with 8/16/32 quads per block row
- * marching four node planes per thread; -1 for a null handle or a level out of
- * range. */
+ * marching four node planes per thread, 8 (cell levels) the TMA-staged
+ * one-pass sweep; -1 for a null handle or a level out of range. */
 int mg_smoother_kind(const mg_handle* h, int level);
 
 void mg_prof_enable(int on);

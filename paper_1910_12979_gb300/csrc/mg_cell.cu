@@ -398,7 +398,7 @@ void cell_prolong_add(int dim, const CellLevel<T>& F, const CellLevel<T>& C, T* 
 {
     long long n = (long long)F.nx * F.ny * F.nz;
     if constexpr (std::is_same<T, float>::value) {
-        if (order == 1 && cell_prolong_v4_ok(dim, F, xf)) {
+        if (order == 1 && cell_prolong_v4_ok(dim, F, xf, xc)) {
             cell_prolong_v4(F, C, xf, xc, s);
             return;
         }

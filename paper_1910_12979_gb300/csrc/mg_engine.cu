@@ -233,7 +233,8 @@ mg_status plan(mg_handle* h, Bump& B)
             for (int d = 0; d < dim; ++d) {
                 size_t m = (size_t)(n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2));
                 v.B64[d] = B.take<double>(m);
-                if (mixed) v.B32[d] = B.take<float>(m);
+                // + 4: the one-pass sweep copies x-face rows rounded out to 16-byte bounds
+                if (mixed) v.B32[d] = B.take<float>(m + 4);
             }
             if (!mixed) v.invd64 = B.take<double>(nc);
         } else {
@@ -381,6 +382,7 @@ mg_status readback(mg_handle* h)
 {
     MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
     MG_CK(cudaStreamSynchronize(h->stream));
+    if (h->hs->async_err) return fail(MG_ERR_CUDA, "an asynchronous shared-memory copy did not complete in time");
     return MG_OK;
 }
 
@@ -493,8 +495,25 @@ void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, i
     const double cells = (double)h->lev[l].ncell;
     T* t = lt<T>(h, l);
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-    const int kind = h->lev[l].kind;   // 1..3: four-cell passes, 8/16/32 quads per block row; 4: pipelined
+    const int kind = h->lev[l].kind;   // 1..3: four-cell passes, 8/16/32 quads per block row; 4: pipelined;
+                                       // 8: one pass, TMA-staged
     if constexpr (std::is_same<T, float>::value) {
+        const bool tma = kind == 8 || (kind == 0 && (h->opt.flags & MG_FLAG_SWEEP_TMA));
+        if (tma && !(h->opt.flags & MG_FLAG_NO_FUSED) && cell_gsrb_tma_ok(h->dim, V, x, t, b) &&
+            cell_gsrb_tma_fits(V.nx)) {
+            T* src = x;
+            T* dst = t;
+            for (int k = 0; k < nu; ++k) {
+                const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 4.0 * sizeof(T) * cells, s) : -1;
+                cell_gsrb_tma(V, src, dst, b, &h->d->async_err, s);
+                prof_end(pr, s);
+                T* tmp = src;
+                src = dst;
+                dst = tmp;
+            }
+            if (src != x) cudaMemcpyAsync(x, src, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
+            return;
+        }
         const bool pipe = kind == 4 || (kind == 0 && (h->opt.flags & MG_FLAG_SWEEP_PIPE));
         if (!(h->opt.flags & MG_FLAG_NO_FUSED) && !pipe && cell_gsrb_v4_ok(h->dim, V, x, b)) {
             for (int k = 0; k < nu; ++k)
@@ -1034,6 +1053,7 @@ mg_status graph_result(mg_handle* h, long long fixed, long long body, long long 
 {
     const DevScalars& r = *h->hs;
     add_launches(fixed + body * r.iters + ifb * r.n_two);
+    if (r.async_err) return fail(MG_ERR_CUDA, "an asynchronous shared-memory copy did not complete in time");
     if (r.info != 0) return fail(MG_ERR_UNSUPPORTED, "the coarsest-level operator is singular");
     if (st) {
         st->iters = r.iters;
@@ -1148,6 +1168,7 @@ mg_status autotune(mg_handle* h)
                 for (int k = 1; k <= 3; ++k)
                     if ((4 << k) <= v.n[0] / 4) cand.push_back(k);
             if (cell_gsrb_fused_ok<float>(h->dim, V)) cand.push_back(4);
+            if (cell_gsrb_tma_ok(h->dim, V, x, t, b) && cell_gsrb_tma_fits(V.nx)) cand.push_back(8);
         }
         int best = 0;
         if (cand.size() > 1) {
@@ -1278,6 +1299,9 @@ mg_status mg_setup(const mg_coeff* c, const mg_geometry* g, const mg_bc* bc, con
     // zero every work vector once (Dirichlet planes of nodal vectors stay 0)
     cudaMemsetAsync(h->ws, 0, need - 256, h->stream);
     rc = build_coefficients(h, c);
+    // one-time limits of the TMA-staged sweep, here rather than inside a stream capture
+    if (rc == MG_OK && h->prec == MG_PREC_MIXED && h->loc == MG_LOC_CELL && h->dim == 3)
+        (void)cell_gsrb_tma_fits(h->lev[0].n[0]);
     if (rc == MG_OK && (h->opt.flags & MG_FLAG_AUTOTUNE)) rc = autotune(h);
     if (rc != MG_OK) { mg_destroy(h); return rc; }
     *out = h;

@@ -134,93 +134,115 @@ void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, 
 
 namespace mgp {
 
+// Element e (0 .. 7) of the pair (v, n).
+__device__ __forceinline__ float el8(const float4& v, const float4& n, int e)
+{
+    return e < 4 ? el(v, e) : el(n, e - 4);
+}
+
 // Residual r = b - L x of a 3-D FP32 level averaged over the 2 x 2 x 2 children
-// of each coarse cell, vectorised like k_gsrb_v4.  A lane owns one quad of four
-// x-cells in one fine row and plane; the 32 lanes of a warp are 8 quads x 2
-// rows x 2 planes (lane bits: plane, row, quad), i.e. the children of 16
-// coarse cells.  A lane sums its residuals over x-pairs; one shuffle adds the
-// two rows, a second the two planes, and the lane of the lower row and plane
-// writes the two coarse cells.  The per-cell arithmetic and the order of the
-// sums (x pair, then y, then z) are those of k_resid_restrict_t, so the coarse
-// right-hand sides are identical.  Requirements: nx % 4 == 0, ny and nz even.
-__global__ void __launch_bounds__(256)
+// of each coarse cell, vectorised like k_gsrb_v4.  A thread owns one quad of
+// four x-cells in one fine row and plane; the lanes along x are consecutive
+// quads of the same row, so every load is a contiguous run, and a block holds
+// the four fine rows of two coarse rows in the two fine planes of a coarse
+// plane (threadIdx.y, threadIdx.z).  The x-neighbours of a quad and its fifth
+// x-face come from the neighbouring lanes by shuffles, the x-faces of a row
+// (stride nx + 1: a row starts at a misalignment a = row & 3 floats) as one
+// aligned 16-byte load per lane, so there are no scalar loads.  Each thread
+// sums its residuals over x-pairs; the row and plane pairs are added through
+// shared memory by the threads of the lower fine row and plane.  The per-cell
+// arithmetic and the order of the sums (x pair, then y, then z) are those of
+// k_resid_restrict_t, so the coarse right-hand sides are identical.
+// Requirements: nx % 4 == 0, ny and nz even, the x-face array readable 3
+// floats past its end; blocks of (32 or a divisor of 32) x 4 x 2 threads.
+constexpr int kRRy = 4;
+__global__ void __launch_bounds__(256, 4)
 k_resid_restrict_v4(CellLevel<float> F, const float* __restrict__ x, const float* __restrict__ b,
                     float* __restrict__ bc)
 {
-    const int nx = F.nx, ny = F.ny, nz = F.nz;
-    const int lane = threadIdx.x;                              // 0..31
-    const int q = blockIdx.x * 8 + (lane >> 2);                // quad along x
-    const int cj = blockIdx.y * blockDim.y + threadIdx.y;      // coarse row
-    const int j = 2 * cj + ((lane >> 1) & 1);
-    const int k = 2 * blockIdx.z + (lane & 1);
-    const bool live = 4 * q < nx && 2 * cj < ny;
+    __shared__ float2 part[2][kRRy][32];
+    const int nx = F.nx, ny = F.ny, nz = F.nz, nq = nx / 4;
+    const int qg = blockIdx.x * blockDim.x + threadIdx.x;      // quad along x
+    const int jg = blockIdx.y * kRRy + threadIdx.y;             // fine row
+    const bool live = qg < nq && jg < ny;
+    // lanes past the end work on the last quad / row (their results are
+    // dropped), so that every lane of a warp takes part in the shuffles
+    const int q = qg < nq ? qg : nq - 1, j = jg < ny ? jg : ny - 1;
+    const int k = 2 * blockIdx.z + threadIdx.z;
+    const bool first = threadIdx.x == 0 || q == 0, last = threadIdx.x == blockDim.x - 1 || q == nq - 1;
     const int i0 = 4 * q;
     const size_t plane = (size_t)nx * ny;
     const bool px = F.bc.lo[0] == BCP, py = F.bc.lo[1] == BCP, pz = F.bc.lo[2] == BCP;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float s0 = 0.f, s1 = 0.f;   // x-pair sums for coarse x-cells 2q and 2q + 1
-    if (live) {
-        const size_t row = (size_t)k * plane + (size_t)j * nx;
-        const bool hym = j > 0 || py, hyp = j < ny - 1 || py;
-        const bool hzm = k > 0 || pz, hzp = k < nz - 1 || pz;
-        const size_t rym = j > 0 ? row - nx : row + (size_t)(ny - 1) * nx;
-        const size_t ryp = j < ny - 1 ? row + nx : row - (size_t)(ny - 1) * nx;
-        const size_t rzm = k > 0 ? row - plane : row + (size_t)(nz - 1) * plane;
-        const size_t rzp = k < nz - 1 ? row + plane : row - (size_t)(nz - 1) * plane;
-        const float4 xc = ld4(x + row + i0);
-        const float4 bb = ld4s(b + row + i0);
-        const float4 xym = hym ? ld4(x + rym + i0) : zero4;
-        const float4 xyp = hyp ? ld4(x + ryp + i0) : zero4;
-        const float4 xzm = hzm ? ld4(x + rzm + i0) : zero4;
-        const float4 xzp = hzp ? ld4(x + rzp + i0) : zero4;
-        float xl = 0.f, xr = 0.f;
-        if (i0 > 0) xl = x[row + i0 - 1];
-        else if (px) xl = x[row + nx - 1];
-        if (i0 + 4 < nx) xr = x[row + i0 + 4];
-        else if (px) xr = x[row];
-        const size_t fxb = ((size_t)k * ny + j) * (nx + 1) + i0;
-        const float fx[5] = {__ldcs(F.bx + fxb), __ldcs(F.bx + fxb + 1), __ldcs(F.bx + fxb + 2),
-                             __ldcs(F.bx + fxb + 3), __ldcs(F.bx + fxb + 4)};
-        const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
-        const float4 fyl = ld4s(F.by + fyb), fyh = ld4s(F.by + fyb + nx);
-        const float4 fzl = ld4s(F.bz + row + i0), fzh = ld4s(F.bz + row + plane + i0);
-        const float xs[6] = {xl, xc.x, xc.y, xc.z, xc.w, xr};
-        float r[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int i = i0 + p;
-            float off = 0.f, dg = 0.f;
-            const float bxl = fx[p], bxh = fx[p + 1];
-            if (i > 0 || px) { off = fmadd(bxl, xs[p], off); dg += bxl; }
-            else if (F.bc.lo[0] == BCD) { dg += 2.f * bxl; }
-            if (i < nx - 1 || px) { off = fmadd(bxh, xs[p + 2], off); dg += bxh; }
-            else if (F.bc.hi[0] == BCD) { dg += 2.f * bxh; }
-            const float byl = el(fyl, p), byh = el(fyh, p);
-            if (hym) { off = fmadd(byl, el(xym, p), off); dg += byl; }
-            else if (F.bc.lo[1] == BCD) { dg += 2.f * byl; }
-            if (hyp) { off = fmadd(byh, el(xyp, p), off); dg += byh; }
-            else if (F.bc.hi[1] == BCD) { dg += 2.f * byh; }
-            const float bzl = el(fzl, p), bzh = el(fzh, p);
-            if (hzm) { off = fmadd(bzl, el(xzm, p), off); dg += bzl; }
-            else if (F.bc.lo[2] == BCD) { dg += 2.f * bzl; }
-            if (hzp) { off = fmadd(bzh, el(xzp, p), off); dg += bzh; }
-            else if (F.bc.hi[2] == BCD) { dg += 2.f * bzh; }
-            r[p] = el(bb, p) - fmadd(-dg, xs[p + 1], off);
-        }
-        s0 = r[0] + r[1];
-        s1 = r[2] + r[3];
+    const size_t row = (size_t)k * plane + (size_t)j * nx;
+    const bool hym = j > 0 || py, hyp = j < ny - 1 || py;
+    const bool hzm = k > 0 || pz, hzp = k < nz - 1 || pz;
+    const size_t rym = j > 0 ? row - nx : row + (size_t)(ny - 1) * nx;
+    const size_t ryp = j < ny - 1 ? row + nx : row - (size_t)(ny - 1) * nx;
+    const size_t rzm = k > 0 ? row - plane : row + (size_t)(nz - 1) * plane;
+    const size_t rzp = k < nz - 1 ? row + plane : row - (size_t)(nz - 1) * plane;
+    const float4 xc = ld4(x + row + i0);
+    const float4 bb = ld4s(b + row + i0);
+    const float4 xym = hym ? ld4(x + rym + i0) : zero4;
+    const float4 xyp = hyp ? ld4(x + ryp + i0) : zero4;
+    const float4 xzm = hzm ? ld4(x + rzm + i0) : zero4;
+    const float4 xzp = hzp ? ld4(x + rzp + i0) : zero4;
+    // x-faces i0 .. i0+4 of the row: aligned 16-byte loads from the misalignment a of the row start
+    const size_t frow = ((size_t)k * ny + j) * (nx + 1);
+    const int a = (int)(frow & 3);
+    const float* fb = F.bx + frow - a + i0;
+    const float4 fv = __ldcs(reinterpret_cast<const float4*>(fb));
+    const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
+    const float4 fyl = ld4s(F.by + fyb), fyh = ld4s(F.by + fyb + nx);
+    const float4 fzl = ld4s(F.bz + row + i0), fzh = ld4s(F.bz + row + plane + i0);
+    // x-neighbours of the quad: the neighbouring lanes' edge cells
+    float xl = __shfl_up_sync(0xffffffffu, xc.w, 1), xr = __shfl_down_sync(0xffffffffu, xc.x, 1);
+    float4 fn;
+    fn.x = __shfl_down_sync(0xffffffffu, fv.x, 1);
+    fn.y = __shfl_down_sync(0xffffffffu, fv.y, 1);
+    fn.z = __shfl_down_sync(0xffffffffu, fv.z, 1);
+    fn.w = __shfl_down_sync(0xffffffffu, fv.w, 1);
+    if (first) xl = i0 > 0 ? x[row + i0 - 1] : (px ? x[row + nx - 1] : 0.f);
+    if (last) {
+        xr = i0 + 4 < nx ? x[row + i0 + 4] : (px ? x[row] : 0.f);
+        fn = __ldcs(reinterpret_cast<const float4*>(fb + 4));
     }
-    // rows: the lane of row 2cj adds its partner's (row 2cj + 1) sums
-    s0 = s0 + __shfl_xor_sync(0xffffffffu, s0, 2);
-    s1 = s1 + __shfl_xor_sync(0xffffffffu, s1, 2);
-    // planes
-    const float o0 = __shfl_xor_sync(0xffffffffu, s0, 1), o1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-    if (live && (lane & 3) == 0) {
+    float fx[5];
+#pragma unroll
+    for (int p = 0; p < 5; ++p) fx[p] = el8(fv, fn, a + p);
+    const float xs[6] = {xl, xc.x, xc.y, xc.z, xc.w, xr};
+    float r[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int i = i0 + p;
+        float off = 0.f, dg = 0.f;
+        const float bxl = fx[p], bxh = fx[p + 1];
+        if (i > 0 || px) { off = fmadd(bxl, xs[p], off); dg += bxl; }
+        else if (F.bc.lo[0] == BCD) { dg += 2.f * bxl; }
+        if (i < nx - 1 || px) { off = fmadd(bxh, xs[p + 2], off); dg += bxh; }
+        else if (F.bc.hi[0] == BCD) { dg += 2.f * bxh; }
+        const float byl = el(fyl, p), byh = el(fyh, p);
+        if (hym) { off = fmadd(byl, el(xym, p), off); dg += byl; }
+        else if (F.bc.lo[1] == BCD) { dg += 2.f * byl; }
+        if (hyp) { off = fmadd(byh, el(xyp, p), off); dg += byh; }
+        else if (F.bc.hi[1] == BCD) { dg += 2.f * byh; }
+        const float bzl = el(fzl, p), bzh = el(fzh, p);
+        if (hzm) { off = fmadd(bzl, el(xzm, p), off); dg += bzl; }
+        else if (F.bc.lo[2] == BCD) { dg += 2.f * bzl; }
+        if (hzp) { off = fmadd(bzh, el(xzp, p), off); dg += bzh; }
+        else if (F.bc.hi[2] == BCD) { dg += 2.f * bzh; }
+        r[p] = el(bb, p) - fmadd(-dg, xs[p + 1], off);
+    }
+    part[threadIdx.z][threadIdx.y][threadIdx.x] = make_float2(r[0] + r[1], r[2] + r[3]);
+    __syncthreads();
+    if (live && threadIdx.z == 0 && (threadIdx.y & 1) == 0) {
+        const float2 a0 = part[0][threadIdx.y][threadIdx.x], a1 = part[0][threadIdx.y + 1][threadIdx.x];
+        const float2 c0 = part[1][threadIdx.y][threadIdx.x], c1 = part[1][threadIdx.y + 1][threadIdx.x];
         const int cnx = nx / 2, cny = ny / 2;
         float2 v;
-        v.x = (s0 + o0) * 0.125f;
-        v.y = (s1 + o1) * 0.125f;
-        *reinterpret_cast<float2*>(bc + ((size_t)blockIdx.z * cny + cj) * cnx + 2 * q) = v;
+        v.x = ((a0.x + a1.x) + (c0.x + c1.x)) * 0.125f;
+        v.y = ((a0.y + a1.y) + (c0.y + c1.y)) * 0.125f;
+        *reinterpret_cast<float2*>(bc + ((size_t)blockIdx.z * cny + (jg >> 1)) * cnx + 2 * q) = v;
     }
 }
 
@@ -228,14 +250,15 @@ bool cell_resid_restrict_v4_ok(int dim, const CellLevel<float>& F, const float* 
 {
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
     return dim == 3 && F.nx % 4 == 0 && F.nx >= 8 && F.ny % 2 == 0 && F.nz % 2 == 0 && a16(x) && a16(b) &&
-           a16(F.by) && a16(F.bz) && ((uintptr_t)bc & 7) == 0;
+           a16(F.bx) && a16(F.by) && a16(F.bz) && ((uintptr_t)bc & 7) == 0;
 }
 
 void cell_resid_restrict_v4(const CellLevel<float>& F, const float* x, const float* b, float* bc, cudaStream_t s)
 {
     const int nq = F.nx / 4, cny = F.ny / 2, cnz = F.nz / 2;
-    const dim3 block(32, 8);
-    const dim3 grid((nq + 7) / 8, (cny + 7) / 8, cnz);
+    const int bx = nq >= 32 ? 32 : nq >= 16 ? 16 : nq >= 8 ? 8 : nq >= 4 ? 4 : 2;
+    const dim3 block(bx, kRRy, 2);
+    const dim3 grid((nq + bx - 1) / bx, (2 * cny + kRRy - 1) / kRRy, cnz);
     MGP_LAUNCH(k_resid_restrict_v4<<<grid, block, 0, s>>>(F, x, b, bc));
 }
 
@@ -244,8 +267,12 @@ void cell_resid_restrict_v4(const CellLevel<float>& F, const float* x, const flo
 namespace mgp {
 
 // Linear prolongation and correction, x_f += P x_c, four fine cells of a row per
-// thread (one 16-byte read-modify-write); the coarse values come through L1.
-// The arithmetic is prolong_value's, as in k_prolong_add.
+// thread (one 16-byte read-modify-write).  The four cells share their coarse
+// rows (parent and neighbour in y, times parent and neighbour in z) and, along
+// x, the parents c0 = i0/2, c0+1 and the outer neighbours of cells i0 and i0+3:
+// 4 x 4 coarse values (a pair load and two scalars per row, through L1), each
+// x-interpolation formed once.  The arithmetic -- weights, fused multiply-adds
+// and their order -- is prolong_value's, so the result equals k_prolong_add's.
 __global__ void __launch_bounds__(256)
 k_prolong_add_v4(CellLevel<float> F, CellLevel<float> C, float* __restrict__ xf, const float* __restrict__ xc)
 {
@@ -253,21 +280,45 @@ k_prolong_add_v4(CellLevel<float> F, CellLevel<float> C, float* __restrict__ xf,
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (4 * q >= F.nx || j >= F.ny) return;
-    const int i0 = 4 * q;
-    float4 v = *reinterpret_cast<const float4*>(xf + ((size_t)k * F.ny + j) * F.nx + i0);
-    float add[4];
+    const int i0 = 4 * q, c0 = 2 * q;
+    const Lin1D l0 = lin1d(i0, C.nx, F.bc.lo[0], F.bc.hi[0]);       // p = c0, q: left neighbour
+    const Lin1D l3 = lin1d(i0 + 3, C.nx, F.bc.lo[0], F.bc.hi[0]);   // p = c0 + 1, q: right neighbour
+    const Lin1D ly = lin1d(j, C.ny, F.bc.lo[1], F.bc.hi[1]);
+    const Lin1D lz = lin1d(k, C.nz, F.bc.lo[2], F.bc.hi[2]);
+    const float w1 = 0.75f, w2 = 0.25f;
+    const float a0 = w2 * l0.sq, a3 = w2 * l3.sq, ay = w2 * ly.sq, az = w2 * lz.sq;
+    // prolong_value's lo / hi of one coarse row for the four cells
+    auto xint = [&](int cb, int cc, float (&o)[4]) {
+        const float* r = xc + ((size_t)cc * C.ny + cb) * C.nx;
+        const float2 m = *reinterpret_cast<const float2*>(r + c0);
+        const float vl = r[l0.q], vr = r[l3.q];
+        o[0] = fmadd(a0, vl, w1 * m.x);   // cell i0:     P = c0,     Q = l0.q
+        o[1] = fmadd(w2, m.y, w1 * m.x);  // cell i0 + 1: P = c0,     Q = c0 + 1
+        o[2] = fmadd(w2, m.x, w1 * m.y);  // cell i0 + 2: P = c0 + 1, Q = c0
+        o[3] = fmadd(a3, vr, w1 * m.y);   // cell i0 + 3: P = c0 + 1, Q = l3.q
+    };
+    float pl[2][4];   // prolong_value's plane(lz.p), plane(lz.q)
 #pragma unroll
-    for (int p = 0; p < 4; ++p) add[p] = prolong_value<3>(F, C, xc, i0 + p, j, k, 1);
-    v.x += add[0];
-    v.y += add[1];
-    v.z += add[2];
-    v.w += add[3];
-    *reinterpret_cast<float4*>(xf + ((size_t)k * F.ny + j) * F.nx + i0) = v;
+    for (int e = 0; e < 2; ++e) {
+        const int cc = e ? lz.q : lz.p;
+        float lo[4], hi[4];
+        xint(ly.p, cc, lo);
+        xint(ly.q, cc, hi);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) pl[e][p] = fmadd(ay, hi[p], w1 * lo[p]);
+    }
+    float* px = xf + ((size_t)k * F.ny + j) * F.nx + i0;
+    float4 v = *reinterpret_cast<const float4*>(px);
+    v.x += fmadd(az, pl[1][0], w1 * pl[0][0]);
+    v.y += fmadd(az, pl[1][1], w1 * pl[0][1]);
+    v.z += fmadd(az, pl[1][2], w1 * pl[0][2]);
+    v.w += fmadd(az, pl[1][3], w1 * pl[0][3]);
+    *reinterpret_cast<float4*>(px) = v;
 }
 
-bool cell_prolong_v4_ok(int dim, const CellLevel<float>& F, const float* xf)
+bool cell_prolong_v4_ok(int dim, const CellLevel<float>& F, const float* xf, const float* xc)
 {
-    return dim == 3 && F.nx % 4 == 0 && F.nx >= 8 && ((uintptr_t)xf & 15) == 0;
+    return dim == 3 && F.nx % 4 == 0 && F.nx >= 8 && ((uintptr_t)xf & 15) == 0 && ((uintptr_t)xc & 7) == 0;
 }
 
 void cell_prolong_v4(const CellLevel<float>& F, const CellLevel<float>& C, float* xf, const float* xc, cudaStream_t s)

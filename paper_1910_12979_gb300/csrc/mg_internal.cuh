@@ -72,6 +72,7 @@ struct DevScalars {
     double prev_rel;           // relative residual before the last refinement step
     int two;                   // the next refinement step runs a second V-cycle
     int n_two;                 // refinement steps that ran a second V-cycle (launch accounting)
+    int async_err;             // set by a kernel whose bounded wait for an asynchronous copy gave up
 };
 
 // Every kernel launch of the library goes through MGP_LAUNCH, which counts it
@@ -106,11 +107,18 @@ bool cell_gsrb_v4_ok(int dim, const CellLevel<float>& L, const float* x, const f
 // bxw: quads per block row (8, 16 or 32; 0 picks by the level's width)
 void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, int color, cudaStream_t s,
                   int bxw = 0);
+// one full red-black sweep in one pass over memory, operands staged in shared
+// memory by bulk asynchronous copies (xin -> xout; same results as two
+// cell_gsrb passes); err: a device word set if a bounded wait gave up
+bool cell_gsrb_tma_ok(int dim, const CellLevel<float>& L, const float* xin, const float* xout, const float* b);
+bool cell_gsrb_tma_fits(int nx);
+void cell_gsrb_tma(const CellLevel<float>& L, const float* xin, float* xout, const float* b, int* err,
+                   cudaStream_t s);
 // 3-D residual + restriction, vectorised like cell_gsrb_v4; same results as cell_resid_restrict
 bool cell_resid_restrict_v4_ok(int dim, const CellLevel<float>& F, const float* x, const float* b, const float* bc);
 void cell_resid_restrict_v4(const CellLevel<float>& F, const float* x, const float* b, float* bc, cudaStream_t s);
 // 3-D linear prolongation and correction, four fine cells per thread
-bool cell_prolong_v4_ok(int dim, const CellLevel<float>& F, const float* xf);
+bool cell_prolong_v4_ok(int dim, const CellLevel<float>& F, const float* xf, const float* xc);
 void cell_prolong_v4(const CellLevel<float>& F, const CellLevel<float>& C, float* xf, const float* xc, cudaStream_t s);
 template <typename T>
 void cell_gsrb_sweep(int dim, const CellLevel<T>& L, const T* xin, T* xout, const T* b, cudaStream_t s);
@@ -170,7 +178,7 @@ void node_prolong_add(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, T* 
 bool node_v4_ok(int dim, const NodeLevel<float>& L, const float* x, const float* out, const float* b);
 void node_v4(const NodeLevel<float>& L, const float* x, float* out, const float* b, float omega, bool resid,
              cudaStream_t s, int bxw = 0, int kz = 0);
-bool node_prolong_v4_ok(int dim, const NodeLevel<float>& F, const float* xf);
+bool node_prolong_v4_ok(int dim, const NodeLevel<float>& F, const float* xf, const float* xc);
 void node_prolong_v4(const NodeLevel<float>& F, const NodeLevel<float>& C, float* xf, const float* xc, cudaStream_t s);
 void node_resid64(int dim, const NodeLevel<double>& L, const double* x, const double* b, float* r32,
                   const double* scale, double* partials, cudaStream_t s);

@@ -148,7 +148,7 @@ __global__ void k_node_prolong(NodeLevel<T> F, NodeLevel<T> C, T* __restrict__ x
                     if (cnt[d] == 2) w *= T(0.5);
                     if (C.bc.lo[d] == BCP && q[d] >= Nc[d]) q[d] -= Nc[d];
                 }
-                s += w * xc[((size_t)q[2] * C.Ny + q[1]) * C.Nx + q[0]];
+                s = fmadd(w, xc[((size_t)q[2] * C.Ny + q[1]) * C.Nx + q[0]], s);
             }
     xf[t] += s;
 }
@@ -674,7 +674,7 @@ template <typename T>
 void node_prolong_add(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, T* xf, const T* xc, cudaStream_t s)
 {
     if constexpr (std::is_same<T, float>::value) {
-        if (node_prolong_v4_ok(dim, F, xf)) {
+        if (node_prolong_v4_ok(dim, F, xf, xc)) {
             node_prolong_v4(F, C, xf, xc, s);
             return;
         }

@@ -200,9 +200,13 @@ void node_v4(const NodeLevel<float>& L, const float* x, float* out, const float*
 namespace mgp {
 
 // Trilinear prolongation and correction of nodal FP32 levels, four fine nodes
-// of a row per thread (one 16-byte read-modify-write); coarse values through
-// L1.  Same weights and order of operations as k_node_prolong.  Requirements:
-// x periodic, Nx % 4 == 0.
+// of a row per thread (one 16-byte read-modify-write).  Along x the four nodes
+// i0 .. i0+3 (i0 = 4q, x periodic) use the coarse nodes c = i0/2, c+1 and c+2
+// (node i0: c; i0+1: c, c+1; i0+2: c+1; i0+3: c+1, c+2), so each coarse row
+// (one or two in y, times one or two in z) is read once: a pair load and a
+// scalar through L1.  The weights and the order of the fused multiply-adds
+// (z, then y, then x) are k_node_prolong's.  Requirements: x periodic,
+// Nx % 4 == 0, xc 8-byte aligned.
 __global__ void __launch_bounds__(256)
 k_node_prolong_v4(NodeLevel<float> F, NodeLevel<float> C, float* __restrict__ xf, const float* __restrict__ xc)
 {
@@ -210,38 +214,39 @@ k_node_prolong_v4(NodeLevel<float> F, NodeLevel<float> C, float* __restrict__ xf
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (4 * q >= F.Nx || j >= F.Ny) return;
-    const int i0 = 4 * q;
+    const int i0 = 4 * q, cx = 2 * q, cx2 = cx + 2 < C.Nx ? cx + 2 : cx + 2 - C.Nx;
     const size_t id = ((size_t)k * F.Ny + j) * F.Nx + i0;
     float4 v = *reinterpret_cast<const float4*>(xf + id);
-    float o[4] = {v.x, v.y, v.z, v.w};
-    const int cy0 = j >> 1, ny_ = 1 + (j & 1), cz0 = k >> 1, nz_ = 1 + (k & 1);
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int i = i0 + p;
-        if (node_dirichlet(F, i, j, k, 3)) continue;
-        const int cx0 = i >> 1, nx_ = 1 + (i & 1);
-        float s = 0.f;
-        for (int c = 0; c < nz_; ++c)
-            for (int b = 0; b < ny_; ++b)
-                for (int a = 0; a < nx_; ++a) {
-                    int qx = cx0 + a, qy = cy0 + b, qz = cz0 + c;
-                    float w = 1.f;
-                    if (nx_ == 2) w *= 0.5f;
-                    if (qx >= C.Nx) qx -= C.Nx;   // x periodic
-                    if (ny_ == 2) w *= 0.5f;
-                    if (C.bc.lo[1] == BCP && qy >= C.Ny) qy -= C.Ny;
-                    if (nz_ == 2) w *= 0.5f;
-                    if (C.bc.lo[2] == BCP && qz >= C.Nz) qz -= C.Nz;
-                    s += w * xc[((size_t)qz * C.Ny + qy) * C.Nx + qx];
-                }
-        o[p] += s;
+    const int ny_ = 1 + (j & 1), nz_ = 1 + (k & 1);
+    const float wyz = (ny_ == 2 ? 0.5f : 1.f) * (nz_ == 2 ? 0.5f : 1.f);
+    const float we = wyz, wo = 0.5f * wyz;   // weights of even / odd nodes
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c = 0; c < nz_; ++c) {
+        int qz = (k >> 1) + c;
+        if (C.bc.lo[2] == BCP && qz >= C.Nz) qz -= C.Nz;
+        for (int b = 0; b < ny_; ++b) {
+            int qy = (j >> 1) + b;
+            if (C.bc.lo[1] == BCP && qy >= C.Ny) qy -= C.Ny;
+            const float* r = xc + ((size_t)qz * C.Ny + qy) * C.Nx;
+            const float2 m = *reinterpret_cast<const float2*>(r + cx);
+            const float x2 = r[cx2];
+            s[0] = fmadd(we, m.x, s[0]);
+            s[1] = fmadd(wo, m.y, fmadd(wo, m.x, s[1]));
+            s[2] = fmadd(we, m.y, s[2]);
+            s[3] = fmadd(wo, x2, fmadd(wo, m.y, s[3]));
+        }
     }
+    float o[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        if (!node_dirichlet(F, i0 + p, j, k, 3)) o[p] += s[p];
     *reinterpret_cast<float4*>(xf + id) = make_float4(o[0], o[1], o[2], o[3]);
 }
 
-bool node_prolong_v4_ok(int dim, const NodeLevel<float>& F, const float* xf)
+bool node_prolong_v4_ok(int dim, const NodeLevel<float>& F, const float* xf, const float* xc)
 {
-    return dim == 3 && F.bc.lo[0] == BCP && F.Nx % 4 == 0 && F.Nx >= 8 && ((uintptr_t)xf & 15) == 0;
+    return dim == 3 && F.bc.lo[0] == BCP && F.Nx % 4 == 0 && F.Nx >= 8 && ((uintptr_t)xf & 15) == 0 &&
+           ((uintptr_t)xc & 7) == 0;
 }
 
 void node_prolong_v4(const NodeLevel<float>& F, const NodeLevel<float>& C, float* xf, const float* xc, cudaStream_t s)

@@ -22,6 +22,7 @@ MG_FLAG_NO_GRAPH = 2
 MG_FLAG_SWEEP_PIPE = 4
 MG_FLAG_AUTOTUNE = 8
 MG_FLAG_ZERO_GUESS = 16
+MG_FLAG_SWEEP_TMA = 32
 
 BC = {"periodic": MG_BC_PERIODIC, "neumann": MG_BC_NEUMANN, "dirichlet": MG_BC_DIRICHLET}
 

@@ -356,12 +356,14 @@ def test_not_converged_returns_best_phi():
     ((64, 64, 64), (("neumann", "dirichlet", "periodic"), ("dirichlet", "neumann", "periodic"))),
     ((96, 40, 24), (("dirichlet", "periodic", "dirichlet"), ("neumann", "periodic", "neumann"))),
     ((32, 16, 44), (("neumann", "neumann", "dirichlet"), ("neumann", "dirichlet", "neumann"))),
+    ((256, 16, 24), (("periodic", "periodic", "dirichlet"), ("periodic", "periodic", "neumann"))),
 ])
 def test_fused_sweep_matches_two_pass(n, bcs):
-    """The vectorised colour passes, the pipelined one-launch sweep and the plain
-    colour passes are the same arithmetic: identical phi, bit for bit (same
-    iterations, same residual), on cubic and ragged grids under every boundary
-    kind."""
+    """The vectorised colour passes, the pipelined one-launch sweep, the
+    TMA-staged one-pass sweep and the plain colour passes are the same
+    arithmetic: identical phi, bit for bit (same iterations, same residual), on
+    cubic and ragged grids under every boundary kind (the TMA sweep runs on the
+    levels it fits: 32 <= nx <= 256, z not periodic)."""
     rng = np.random.default_rng(9)
     sigma = T(np.exp(rng.uniform(0.0, np.log(1e3), size=n[::-1])))
     geom = dict(I.geometry(n, bcs[0], bcs[1]), h=(1.0 / max(n),) * 3)   # square cells
@@ -370,7 +372,7 @@ def test_fused_sweep_matches_two_pass(n, bcs):
         f -= f.mean()
     for prec in ("mixed", "fp64"):
         out = []
-        for flags in (0, N.MG_FLAG_SWEEP_PIPE, N.MG_FLAG_NO_FUSED):
+        for flags in (0, N.MG_FLAG_SWEEP_PIPE, N.MG_FLAG_SWEEP_TMA, N.MG_FLAG_NO_FUSED):
             s = ProjectionSolver(geom, sigma, loc="cell", prec=prec, flags=flags, max_iters=6)
             phi = torch.zeros_like(f)
             st = s.solve(f, phi, tol=1e-11, allow_not_converged=True)

@@ -145,16 +145,16 @@ __device__ __forceinline__ float el8(const float4& v, const float4& n, int e)
 // four x-cells in one fine row and plane; the lanes along x are consecutive
 // quads of the same row, so every load is a contiguous run, and a block holds
 // the four fine rows of two coarse rows in the two fine planes of a coarse
-// plane (threadIdx.y, threadIdx.z).  The x-neighbours of a quad and its fifth
-// x-face come from the neighbouring lanes by shuffles, the x-faces of a row
-// (stride nx + 1: a row starts at a misalignment a = row & 3 floats) as one
-// aligned 16-byte load per lane, so there are no scalar loads.  Each thread
-// sums its residuals over x-pairs; the row and plane pairs are added through
-// shared memory by the threads of the lower fine row and plane.  The per-cell
+// plane (threadIdx.y, threadIdx.z).  The x-neighbours of a quad come from the
+// neighbouring lanes by shuffles (a load only at the ends of a warp's run of
+// quads); the five x-faces are scalar loads (one aligned 16-byte load plus
+// shuffles and a data-dependent select measured slower).  Each thread sums its
+// residuals over x-pairs; the row and plane pairs are added through shared
+// memory by the threads of the lower fine row and plane.  The per-cell
 // arithmetic and the order of the sums (x pair, then y, then z) are those of
 // k_resid_restrict_t, so the coarse right-hand sides are identical.
-// Requirements: nx % 4 == 0, ny and nz even, the x-face array readable 3
-// floats past its end; blocks of (32 or a divisor of 32) x 4 x 2 threads.
+// Requirements: nx % 4 == 0, ny and nz even; blocks of (32 or a divisor of 32)
+// x 4 x 2 threads.
 constexpr int kRRy = 4;
 __global__ void __launch_bounds__(256, 4)
 k_resid_restrict_v4(CellLevel<float> F, const float* __restrict__ x, const float* __restrict__ b,
@@ -187,29 +187,16 @@ k_resid_restrict_v4(CellLevel<float> F, const float* __restrict__ x, const float
     const float4 xyp = hyp ? ld4(x + ryp + i0) : zero4;
     const float4 xzm = hzm ? ld4(x + rzm + i0) : zero4;
     const float4 xzp = hzp ? ld4(x + rzp + i0) : zero4;
-    // x-faces i0 .. i0+4 of the row: aligned 16-byte loads from the misalignment a of the row start
-    const size_t frow = ((size_t)k * ny + j) * (nx + 1);
-    const int a = (int)(frow & 3);
-    const float* fb = F.bx + frow - a + i0;
-    const float4 fv = __ldcs(reinterpret_cast<const float4*>(fb));
+    const size_t fxb = ((size_t)k * ny + j) * (nx + 1) + i0;
+    const float fx[5] = {__ldcs(F.bx + fxb), __ldcs(F.bx + fxb + 1), __ldcs(F.bx + fxb + 2),
+                         __ldcs(F.bx + fxb + 3), __ldcs(F.bx + fxb + 4)};
     const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
     const float4 fyl = ld4s(F.by + fyb), fyh = ld4s(F.by + fyb + nx);
     const float4 fzl = ld4s(F.bz + row + i0), fzh = ld4s(F.bz + row + plane + i0);
     // x-neighbours of the quad: the neighbouring lanes' edge cells
     float xl = __shfl_up_sync(0xffffffffu, xc.w, 1), xr = __shfl_down_sync(0xffffffffu, xc.x, 1);
-    float4 fn;
-    fn.x = __shfl_down_sync(0xffffffffu, fv.x, 1);
-    fn.y = __shfl_down_sync(0xffffffffu, fv.y, 1);
-    fn.z = __shfl_down_sync(0xffffffffu, fv.z, 1);
-    fn.w = __shfl_down_sync(0xffffffffu, fv.w, 1);
     if (first) xl = i0 > 0 ? x[row + i0 - 1] : (px ? x[row + nx - 1] : 0.f);
-    if (last) {
-        xr = i0 + 4 < nx ? x[row + i0 + 4] : (px ? x[row] : 0.f);
-        fn = __ldcs(reinterpret_cast<const float4*>(fb + 4));
-    }
-    float fx[5];
-#pragma unroll
-    for (int p = 0; p < 5; ++p) fx[p] = el8(fv, fn, a + p);
+    if (last) xr = i0 + 4 < nx ? x[row + i0 + 4] : (px ? x[row] : 0.f);
     const float xs[6] = {xl, xc.x, xc.y, xc.z, xc.w, xr};
     float r[4];
 #pragma unroll

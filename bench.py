@@ -719,15 +719,17 @@ def main():
                                       "recorded"}
 
     # end to end through the public API with host buffers: every step copies its inputs from pinned
-    # host memory and reads its projected velocities back.  Two device input sets and a copy stream
-    # let the copies of step k+1 (and the read-back of step k) overlap the solves of step k.
+    # host memory and reads its projected velocities back.  Two device input and output sets, an
+    # upload stream and a read-back stream (the two copy directions run concurrently) let the copies
+    # of step k+1 and the read-back of step k-1 overlap the solves of step k.
     if not args.no_e2e:
         mac, nod, phim, phin = mixed
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         h_in = [pin(p["sigma"]), pin(p["beta0"]), pin(p["S"])] + [pin(b) for b in p["beta0_face"]] + \
                [pin(u) for u in p["U_mac"]] + [pin(u) for u in p["U_cell"]]
         h2d = sum(t.numel() * t.element_size() for t in h_in)
-        cstream = torch.cuda.Stream(device=dev)
+        ustream = torch.cuda.Stream(device=dev)   # host -> device
+        dstream = torch.cuda.Stream(device=dev)   # device -> host
         with torch.cuda.stream(stream):
             d_sets = [[torch.empty_like(sigma) for _ in range(3)] + [torch.empty_like(b) for b in b0f] +
                       [torch.empty_like(u) for u in U0m] + [torch.empty_like(u) for u in U0c] for _ in range(2)]
@@ -736,18 +738,21 @@ def main():
         d2h = sum(t.numel() * t.element_size() for t in h_out[0])
         h2d_done = [torch.cuda.Event() for _ in range(2)]
         comp_done = [torch.cuda.Event() for _ in range(2)]
+        d2h_done = [torch.cuda.Event() for _ in range(2)]
 
         def upload(i):
-            with torch.cuda.stream(cstream):
+            with torch.cuda.stream(ustream):
+                ustream.wait_event(comp_done[i])   # the solves that read input set i are done
                 for d, hsrc in zip(d_sets[i], h_in):
                     d.copy_(hsrc, non_blocking=True)
-                h2d_done[i].record(cstream)
+                h2d_done[i].record(ustream)
 
         def compute(i):
             sg, b0, Sv = d_sets[i][0], d_sets[i][1], d_sets[i][2]
             bf, u0m, u0c = d_sets[i][3:6], d_sets[i][6:9], d_sets[i][9:12]
             um, uc = w_sets[i][:3], w_sets[i][3:]
             stream.wait_event(h2d_done[i])
+            stream.wait_event(d2h_done[i])   # output set i has been read back
             with torch.cuda.stream(stream):
                 mac.update_coeff(sg)
                 nod.update_coeff(sg)
@@ -758,12 +763,22 @@ def main():
                 comp_done[i].record(stream)
 
         def download(i):
-            cstream.wait_event(comp_done[i])
-            with torch.cuda.stream(cstream):
+            with torch.cuda.stream(dstream):
+                dstream.wait_event(comp_done[i])
                 for hd, d in zip(h_out[i], w_sets[i]):
                     hd.copy_(d, non_blocking=True)
+                d2h_done[i].record(dstream)
 
-        def run(K):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+
+        def run(K, timed=False):
+            torch.cuda.synchronize(dev)
+            if timed:
+                e0.record(stream)
+            for i in range(2):   # fresh events (after e0): nothing to wait for at the start
+                comp_done[i].record(stream)
+                d2h_done[i].record(stream)
             upload(0)
             if K > 1:
                 upload(1)
@@ -771,21 +786,18 @@ def main():
                 compute(k % 2)
                 download(k % 2)
                 if k + 2 < K:
-                    upload(k % 2)   # after this step's read-back (same stream) and its solves (event)
-            cstream.synchronize()
-            stream.synchronize()
+                    upload(k % 2)   # after this step's solves (event): input set k % 2 is free
+            stream.wait_event(d2h_done[(K - 1) % 2])
+            stream.wait_event(h2d_done[(K - 1) % 2])
+            if timed:
+                e1.record(stream)
+            torch.cuda.synchronize(dev)
 
         run(2)
         Ke = max(2, min(args.steps, 6))
         if dist is not None:
             dist.barrier()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(cstream)
-        run(Ke)
-        e1.record(cstream)
-        e1.synchronize()
+        run(Ke, timed=True)
         mse = e0.elapsed_time(e1)
         if dist is not None:
             t = torch.tensor([mse], dtype=torch.float64, device=dev)
@@ -793,8 +805,10 @@ def main():
             mse = float(t.item())
         line["e2e"] = {"value": 2.0 * Ke * world / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": mse / Ke,
-                       "note": "pinned host inputs copied and results read back every step on a copy stream, "
-                               "overlapping the solves of the neighbouring step (double-buffered device inputs)"}
+                       "note": "pinned host inputs copied and results read back every step on an upload and "
+                               "a read-back stream, overlapping the solves of the neighbouring steps "
+                               "(double-buffered device inputs and outputs); each step also rebuilds both "
+                               "hierarchies' coefficients from the uploaded sigma"}
 
     # plain FP64 GPU multigrid on the same workload (graph path, like graph_path above)
     if not args.no_fp64:

@@ -134,12 +134,6 @@ void cell_gsrb_v4(int dim, const CellLevel<float>& L, float* x, const float* b, 
 
 namespace mgp {
 
-// Element e (0 .. 7) of the pair (v, n).
-__device__ __forceinline__ float el8(const float4& v, const float4& n, int e)
-{
-    return e < 4 ? el(v, e) : el(n, e - 4);
-}
-
 // Residual r = b - L x of a 3-D FP32 level averaged over the 2 x 2 x 2 children
 // of each coarse cell, vectorised like k_gsrb_v4.  A thread owns one quad of
 // four x-cells in one fine row and plane; the lanes along x are consecutive

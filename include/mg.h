@@ -287,14 +287,15 @@ typedef enum {
                                      colour pass where the level does not tile (2 words/cell) */
     MG_PROF_RESID64 = 1,          /* FP64 fine residual of a cell system (+ FP32 copy in mixed
                                      mode): phi, f, sigma in FP64 (+ r in FP32) per cell;
-                                     17 FP64 flops per cell */
+                                     15 FP64 flops per cell (6 face FMAs, the diagonal FMA,
+                                     one subtraction) */
     MG_PROF_NODE_SMOOTH_FINE = 2, /* one Jacobi sweep on the finest nodal level: phi, f, sigma read, phi written */
     MG_PROF_CELL_RESTRICT_FINE = 3, /* fused residual + restriction on the finest cell level:
                                        phi, f, sigma read, 1/2^dim word written per cell */
     MG_PROF_NODE_RESID64 = 4,     /* FP64 fine residual of a nodal system (+ FP32 copy):
                                      phi, f, sigma in FP64 (+ r in FP32) per node; FP64 flops
-                                     per node of the form evaluated: 45 for the row assembled
-                                     from 8 sigma (2-D, small 3-D grids), about 26.8 for the
+                                     per node of the form evaluated: 44 for the row assembled
+                                     from 8 sigma (2-D, small 3-D grids), about 25.8 for the
                                      sum-factorised 3-D form (edge sigma sums set up once) */
     MG_PROF_COUNT = 5
 } mg_prof_kernel;
@@ -376,6 +377,11 @@ mg_status mg_rotation_forces(const mg_geometry* geom, const double omega[3], con
  * MG_ERR_INVALID_ARG for null pointers with n > 0. */
 mg_status mg_convert_f64_to_f32(const double* x, float* y, size_t n, void* stream);
 mg_status mg_convert_f32_to_f64(const float* x, double* y, size_t n, void* stream);
+/* y = x * 2^shift rounded to binary32, the exponent shift folded into the
+ * conversion (how the FP64 residual kernels scale the residual by a power of
+ * two near 1/||f|| without an FP64 multiply); -1022 <= shift <= 1023, else
+ * MG_ERR_INVALID_ARG; arguments otherwise as above. */
+mg_status mg_convert_f64_to_f32_pow2(const double* x, float* y, size_t n, int shift, void* stream);
 /* y = 1/x as the library's FP64 kernels compute it where they divide (face
  * coefficients, projection updates): Newton's method from a binary32 estimate,
  * within about one ulp of the quotient; arguments as above. */

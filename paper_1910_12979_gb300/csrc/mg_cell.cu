@@ -188,23 +188,104 @@ __global__ void k_prolong_add(CellLevel<T> F, CellLevel<T> C, T* __restrict__ xf
 
 // -------------------------------------------------------- FP64 residuals
 
+// r = f - L x in FP64, its FP32 copy r / fscale (fscale a power of two, folded
+// into the conversion) and the partial sums of the copy's squares.  A thread
+// takes quads of four consecutive cells (flat index), grid-stride; the sums
+// follow that order, which the vectorised kernel below and the zero-guess
+// initialisation share, so all three give the same norm.
 template <int DIM, bool HAS_DIAG>
 __global__ void k_resid64(CellLevel<double> L, const double* __restrict__ x, const double* __restrict__ b,
                           float* __restrict__ r32, const double* __restrict__ scale, double* __restrict__ partials)
 {
-    const int total = L.nx * L.ny * L.nz;
-    const double inv = 1.0 / *scale;
+    const int total = L.nx * L.ny * L.nz, nquad = (total + 3) / 4;
+    const int sh = pow2_shift(*scale);
     float acc = 0.f;
     const GlobalPhi<double> ph{x, L.nx, L.ny};
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        int i, j, k;
-        unflat(t, L.nx, L.ny, i, j, k);
-        double off, dg;
-        cell_row<DIM>(L, i, j, k, ph, off, dg);
-        const double d = HAS_DIAG ? L.diag[t] : dg;
-        const float rs = f64_to_f32_rn((b[t] - (off - d * x[t])) * inv);
-        acc = fmaf(rs, rs, acc);
-        if (r32) r32[t] = rs;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nquad; u += gridDim.x * blockDim.x)
+        for (int t = 4 * u; t < 4 * u + 4 && t < total; ++t) {
+            int i, j, k;
+            unflat(t, L.nx, L.ny, i, j, k);
+            double off, dg;
+            cell_row<DIM>(L, i, j, k, ph, off, dg);
+            const double d = HAS_DIAG ? L.diag[t] : dg;
+            const float rs = f64_to_f32_pow2(b[t] - fmadd(-d, x[t], off), sh);
+            acc = fmaf(rs, rs, acc);
+            if (r32) r32[t] = rs;
+        }
+    double a[1] = {(double)acc};
+    block_reduce_store<1>(a, partials);
+}
+
+// The same residual, four consecutive cells of an x-row per thread (3-D,
+// nx % 4 == 0, stored diagonal): the row, its y- and z-neighbour rows, b, the
+// diagonal and the y-/z-faces as 16-byte loads, the quad's x-neighbours from
+// the neighbouring lanes, the integer index work once per quad.  Every cell's
+// FP64 arithmetic is cell_row's (face terms x-lo, x-hi, y-lo, y-hi, z-lo, z-hi,
+// fused multiply-adds from 0) followed by b - fma(-d, x, off): identical values.
+__global__ void __launch_bounds__(256)
+k_resid64_v4(CellLevel<double> L, const double* __restrict__ x, const double* __restrict__ b,
+             float* __restrict__ r32, const double* __restrict__ scale, double* __restrict__ partials)
+{
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nq = nx / 4;
+    const int nquad = nq * ny * nz;
+    const int sh = pow2_shift(*scale);
+    const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
+    const size_t plane = (size_t)nx * ny;
+    float acc = 0.f;
+    auto ld2 = [](const double* p) { return *reinterpret_cast<const double2*>(p); };
+    const double2 z2 = make_double2(0.0, 0.0);
+    const int stride = gridDim.x * blockDim.x;
+    for (int u0 = blockIdx.x * blockDim.x; u0 < nquad; u0 += stride) {
+        // every lane of the warp runs the iteration (shuffles); lanes past the end compute the last quad
+        const int ug = u0 + threadIdx.x;
+        const bool live = ug < nquad;
+        const int u = live ? ug : nquad - 1;
+        const int q = u % nq, rowi = u / nq, j = rowi % ny, k = rowi / ny;
+        const int i0 = 4 * q;
+        const size_t row = (size_t)k * plane + (size_t)j * nx, c = row + i0;
+        const double2 xa = ld2(x + c), xb = ld2(x + c + 2);
+        const bool hym = j > 0 || py, hyp = j < ny - 1 || py, hzm = k > 0 || pz, hzp = k < nz - 1 || pz;
+        const size_t rym = j > 0 ? row - nx : row + (size_t)(ny - 1) * nx;
+        const size_t ryp = j < ny - 1 ? row + nx : row - (size_t)(ny - 1) * nx;
+        const size_t rzm = k > 0 ? row - plane : row + (size_t)(nz - 1) * plane;
+        const size_t rzp = k < nz - 1 ? row + plane : row - (size_t)(nz - 1) * plane;
+        const double2 ym0 = hym ? ld2(x + rym + i0) : z2, ym1 = hym ? ld2(x + rym + i0 + 2) : z2;
+        const double2 yp0 = hyp ? ld2(x + ryp + i0) : z2, yp1 = hyp ? ld2(x + ryp + i0 + 2) : z2;
+        const double2 zm0 = hzm ? ld2(x + rzm + i0) : z2, zm1 = hzm ? ld2(x + rzm + i0 + 2) : z2;
+        const double2 zp0 = hzp ? ld2(x + rzp + i0) : z2, zp1 = hzp ? ld2(x + rzp + i0 + 2) : z2;
+        const double2 ba = ld2(b + c), bb = ld2(b + c + 2), da = ld2(L.diag + c), db = ld2(L.diag + c + 2);
+        // x-neighbours: the previous / next quad's edge cells when that quad is in the same row and warp
+        const int lane = threadIdx.x & 31;
+        double xl = __shfl_up_sync(0xffffffffu, xb.y, 1), xr = __shfl_down_sync(0xffffffffu, xa.x, 1);
+        if (lane == 0 || q == 0) xl = i0 > 0 ? x[c - 1] : (px ? x[row + nx - 1] : 0.0);
+        if (lane == 31 || q == nq - 1) xr = i0 + 4 < nx ? x[c + 4] : (px ? x[row] : 0.0);
+        const size_t fxb = ((size_t)k * ny + j) * (nx + 1) + i0;
+        const double fx[5] = {L.bx[fxb], L.bx[fxb + 1], L.bx[fxb + 2], L.bx[fxb + 3], L.bx[fxb + 4]};
+        const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
+        const double2 fyl0 = ld2(L.by + fyb), fyl1 = ld2(L.by + fyb + 2);
+        const double2 fyh0 = ld2(L.by + fyb + nx), fyh1 = ld2(L.by + fyb + nx + 2);
+        const double2 fzl0 = ld2(L.bz + c), fzl1 = ld2(L.bz + c + 2);
+        const double2 fzh0 = ld2(L.bz + c + plane), fzh1 = ld2(L.bz + c + plane + 2);
+        auto e2 = [](const double2& lo, const double2& hi, int p) { return p == 0 ? lo.x : p == 1 ? lo.y : p == 2 ? hi.x : hi.y; };
+        const double xs[6] = {xl, xa.x, xa.y, xb.x, xb.y, xr};
+        float rsv[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int i = i0 + p;
+            double off = 0.0;
+            if (i > 0 || px) off = fmadd(fx[p], xs[p], off);
+            if (i < nx - 1 || px) off = fmadd(fx[p + 1], xs[p + 2], off);
+            if (hym) off = fmadd(e2(fyl0, fyl1, p), e2(ym0, ym1, p), off);
+            if (hyp) off = fmadd(e2(fyh0, fyh1, p), e2(yp0, yp1, p), off);
+            if (hzm) off = fmadd(e2(fzl0, fzl1, p), e2(zm0, zm1, p), off);
+            if (hzp) off = fmadd(e2(fzh0, fzh1, p), e2(zp0, zp1, p), off);
+            rsv[p] = f64_to_f32_pow2(e2(ba, bb, p) - fmadd(-e2(da, db, p), xs[p + 1], off), sh);
+        }
+        if (live) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc = fmaf(rsv[p], rsv[p], acc);
+            if (r32) *reinterpret_cast<float4*>(r32 + c) = make_float4(rsv[0], rsv[1], rsv[2], rsv[3]);
+        }
     }
     double a[1] = {(double)acc};
     block_reduce_store<1>(a, partials);
@@ -413,8 +494,14 @@ void cell_prolong_add(int dim, const CellLevel<T>& F, const CellLevel<T>& C, T* 
 }
 
 void cell_resid64(int dim, const CellLevel<double>& L, const double* x, const double* b, float* r32,
-                  const double* scale, double* partials, cudaStream_t s)
+                  const double* scale, double* partials, cudaStream_t s, bool vec)
 {
+    auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    if (vec && dim == 3 && L.diag && L.nx % 4 == 0 && a16(x) && a16(b) && a16(L.diag) && a16(L.by) && a16(L.bz) &&
+        (!r32 || a16(r32)) && (size_t)L.nx * L.ny * L.nz / 4 < (size_t)1 << 30) {
+        MGP_LAUNCH(k_resid64_v4<<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
+        return;
+    }
     if (dim == 2) {
         if (L.diag) MGP_LAUNCH(k_resid64<2, true><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));
         else MGP_LAUNCH(k_resid64<2, false><<<kRedBlocks, kThreads, 0, s>>>(L, x, b, r32, scale, partials));

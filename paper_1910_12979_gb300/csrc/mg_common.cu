@@ -11,7 +11,8 @@ void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relax
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // Sum the kRedBlocks partials of each slot in a fixed order: out[q].
-__global__ void k_finalize(const double* __restrict__ partials, int nslots, double* __restrict__ out)
+__global__ void k_finalize(const double* __restrict__ partials, int nslots, double* __restrict__ out,
+                           const double* __restrict__ mul)
 {
     __shared__ double sh[kThreads];
     for (int q = 0; q < nslots; ++q) {
@@ -23,14 +24,14 @@ __global__ void k_finalize(const double* __restrict__ partials, int nslots, doub
             if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
             __syncthreads();
         }
-        if (threadIdx.x == 0) out[q] = sh[0];
+        if (threadIdx.x == 0) out[q] = mul ? sh[0] * *mul : sh[0];
         __syncthreads();
     }
 }
 
-void reduce_finalize(const double* partials, int nslots, double* out, cudaStream_t s)
+void reduce_finalize(const double* partials, int nslots, double* out, cudaStream_t s, const double* mul)
 {
-    MGP_LAUNCH(k_finalize<<<1, kThreads, 0, s>>>(partials, nslots, out));
+    MGP_LAUNCH(k_finalize<<<1, kThreads, 0, s>>>(partials, nslots, out, mul));
 }
 
 __global__ void k_sum_sq(const double* __restrict__ v, size_t n, double* __restrict__ partials)
@@ -123,13 +124,15 @@ __global__ void k_to64(double* __restrict__ d, const float* __restrict__ a, size
 __global__ void k_init_zero_guess(const double* __restrict__ f, float* __restrict__ r32,
                                   const double* __restrict__ scale, double* __restrict__ partials, int n)
 {
-    const double inv = 1.0 / *scale;
+    const int sh = pow2_shift(*scale);
     float acc = 0.f;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const float rs = f64_to_f32_rn(f[t] * inv);
-        acc = fmaf(rs, rs, acc);
-        if (r32) r32[t] = rs;
-    }
+    const int nquad = (n + 3) / 4;   // quads of consecutive entries, as the cell FP64 residual kernels
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nquad; u += gridDim.x * blockDim.x)
+        for (int t = 4 * u; t < 4 * u + 4 && t < n; ++t) {
+            const float rs = f64_to_f32_pow2(f[t], sh);
+            acc = fmaf(rs, rs, acc);
+            if (r32) r32[t] = rs;
+        }
     double a[1] = {(double)acc};
     block_reduce_store<1>(a, partials);
 }
@@ -160,6 +163,16 @@ void vec_copy_f64(double* dst, const double* src, size_t n, cudaStream_t s)
 {
     MGP_LAUNCH(k_copy64<<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
 }
+__global__ void k_to32_pow2(float* __restrict__ d, const double* __restrict__ a, size_t n, int sh)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        d[t] = f64_to_f32_pow2(a[t], sh);
+}
+void vec_to_f32_pow2(float* dst, const double* src, size_t n, int shift, cudaStream_t s)
+{
+    MGP_LAUNCH(k_to32_pow2<<<kRedBlocks, kThreads, 0, s>>>(dst, src, n, shift));
+}
+
 void vec_to_f32(float* dst, const double* src, size_t n, cudaStream_t s)
 {
     if (al16(dst) && al16(src)) MGP_LAUNCH(k_to32<true><<<kRedBlocks, kThreads, 0, s>>>(dst, src, n));
@@ -173,11 +186,7 @@ void vec_axpy_f32(double* phi, const float* e, const double* scale, size_t n, cu
     else MGP_LAUNCH(k_axpy32<false><<<kRedBlocks, kThreads, 0, s>>>(phi, e, scale, n));
 }
 
-__global__ void k_fscale(DevScalars* d)
-{
-    const double f2 = d->fnorm2;
-    d->fscale = f2 > 0.0 ? sqrt(f2) : 1.0;
-}
+__global__ void k_fscale(DevScalars* d) { set_fscale(d); }
 void scalars_set_fscale(DevScalars* d, cudaStream_t s) { MGP_LAUNCH(k_fscale<<<1, 1, 0, s>>>(d)); }
 
 // ------------------------------------------------------------ dense solve

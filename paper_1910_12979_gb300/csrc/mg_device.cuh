@@ -89,6 +89,50 @@ __device__ __forceinline__ double f32_to_f64(float f)
     return (double)f;
 }
 
+// f64_to_f32_rn(v * 2^s) with the exact power-of-two scaling folded into the
+// exponent field, so the scaling costs no FP64 operation: the FP64 residual
+// kernels scale r by a power of two near 1/||f|| this way.  Normal results are
+// the format definition's (as above); zeros keep their sign; everything else
+// (subnormal or non-finite operands, results outside the normal binary32
+// range) takes scalbn and the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_pow2(double v, int s)
+{
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const int eo = e + s - 896;   // binary32 exponent field of v * 2^s
+    if (e != 0 && e != 0x7ff && eo >= 1 && eo <= 254) {
+        unsigned r = ((unsigned)eo << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu, half = 0x10000000u;
+        r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;
+        return __uint_as_float(r | (hi & 0x80000000u));
+    }
+    if (e == 0 && ((hi & 0xfffffu) | lo) == 0) return __uint_as_float(hi & 0x80000000u);
+    return __double2float_rn(scalbn(v, s));
+}
+// -log2 p of a power of two p (the residual scale)
+__device__ __forceinline__ int pow2_shift(double p)
+{
+    return 1023 - (int)(((unsigned)__double2hiint(p) >> 20) & 0x7ffu);
+}
+// the largest power of two <= x, for finite normal x > 0
+__device__ __forceinline__ double pow2_floor(double x) { return __hiloint2double(__double2hiint(x) & 0x7ff00000, 0); }
+
+// the residual scale of a solve from ||f||^2: the power of two <= ||f|| (1
+// when f = 0) and the factor that turns sums of scaled squares into squared
+// relative residuals
+__device__ __forceinline__ void set_fscale(DevScalars* d)
+{
+    const double f2 = d->fnorm2;
+    if (f2 > 0.0) {
+        const double p = pow2_floor(sqrt(f2));
+        d->fscale = p;
+        d->rscale2 = (p * p) / f2;
+    } else {
+        d->fscale = 1.0;
+        d->rscale2 = 1.0;
+    }
+}
+
 // 1/d by Newton's method on g(y) = 1/y - d, whose step y <- y + y (1 - d y)
 // squares the relative error.  The start is PTX rcp.approx.ftz.f32 of d rounded
 // to binary32 (relative error below about 2^-22 in all); two steps bring it to

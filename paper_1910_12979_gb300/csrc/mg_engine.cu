@@ -390,7 +390,7 @@ __global__ void k_keep(DevScalars* d, int fslot, int srcslot)
 {
     if (fslot >= 0) {
         d->fnorm2 = d->red[fslot];
-        d->fscale = d->fnorm2 > 0.0 ? sqrt(d->fnorm2) : 1.0;
+        set_fscale(d);
     }
     if (srcslot >= 0) d->src2 = d->red[srcslot];
 }
@@ -415,10 +415,15 @@ void finish_rhs(mg_handle* h, int fslot, int srcslot)
 // FP64 operations per node of the sum-factorised nodal residual, an FMA
 // counted as two: per cell position 3 adds (2x2 phi sum) + 1 add + 1 mul (Q),
 // times 297/256 cell positions per node; per node 3 + 1 adds (2x2 Q sums),
-// 6 FMAs (edge terms), 1 mul + 1 FMA (scaling and diagonal), 1 sub, 1 mul.
-constexpr double kNodeResidSFFlops = 5.0 * 297.0 / 256.0 + 21.0;
+// 6 FMAs (edge terms), 1 mul + 1 FMA (scaling and diagonal), 1 sub.  The
+// residual's power-of-two scale folds into the FP32 conversion (no operation).
+constexpr double kNodeResidSFFlops = 5.0 * 297.0 / 256.0 + 20.0;
+// FP64 operations per cell of the cell residual: 6 FMAs (face terms), 1 FMA
+// (stored diagonal), 1 sub; per node of the nodal row assembled from 8 sigma: 44
+constexpr double kCellResidFlops = 15.0, kNodeResidRowFlops = 44.0;
 
-// ||f - L phi||^2 / ||f||^2 -> d->rnorm2; optional FP32 copy of the residual / ||f||.
+// ||f - L phi||^2 / ||f||^2 -> d->rnorm2; optional FP32 copy of the residual
+// divided by fscale (the power of two <= ||f||).
 void residual64(mg_handle* h, const double* phi, float* r32)
 {
     cudaStream_t s = h->stream;
@@ -427,16 +432,17 @@ void residual64(mg_handle* h, const double* phi, float* r32)
     const Level& v0 = h->lev[0];
     const bool sf = nodal && v0.dq64;
     const int pr = prof_begin(nodal ? MG_PROF_NODE_RESID64 : MG_PROF_RESID64, (24.0 + (r32 ? 4.0 : 0.0)) * nv, s,
-                              (sf ? kNodeResidSFFlops : nodal ? 45.0 : 17.0) * nv);
+                              (sf ? kNodeResidSFFlops : nodal ? kNodeResidRowFlops : kCellResidFlops) * nv);
     if (h->loc == MG_LOC_CELL)
-        cell_resid64(h->dim, cview<double>(h, 0), phi, h->f64, r32, &h->d->fscale, h->partials, s);
+        cell_resid64(h->dim, cview<double>(h, 0), phi, h->f64, r32, &h->d->fscale, h->partials, s,
+                     !(h->opt.flags & MG_FLAG_NO_FUSED));
     else if (sf)
         node_resid64_sf(nview<double>(h, 0), NodeEdges{{v0.ew64[0], v0.ew64[1], v0.ew64[2]}, v0.dq64}, phi, h->f64,
                         r32, &h->d->fscale, h->partials, s);
     else
         node_resid64(h->dim, nview<double>(h, 0), phi, h->f64, r32, &h->d->fscale, h->partials, s);
     prof_end(pr, s);
-    reduce_finalize(h->partials, 1, &h->d->rnorm2, s);
+    reduce_finalize(h->partials, 1, &h->d->rnorm2, s, &h->d->rscale2);
 }
 
 // The first residual when the solve starts from phi = 0 (MG_FLAG_ZERO_GUESS):
@@ -447,7 +453,7 @@ void init_zero_guess(mg_handle* h, double* phi, float* r32)
     const size_t n = h->lev[0].nvec;
     cudaMemsetAsync(phi, 0, n * sizeof(double), s);
     vec_init_zero_guess(h->f64, r32, &h->d->fscale, h->partials, n, s);
-    reduce_finalize(h->partials, 1, &h->d->rnorm2, s);
+    reduce_finalize(h->partials, 1, &h->d->rnorm2, s, &h->d->rscale2);
 }
 
 bool zero_guess(const mg_handle* h) { return (h->opt.flags & MG_FLAG_ZERO_GUESS) != 0; }
@@ -1552,6 +1558,16 @@ mg_status mg_convert_f64_to_f32(const double* x, float* y, size_t n, void* strea
     if (n == 0) return MG_OK;
     if (!x || !y) return fail(MG_ERR_INVALID_ARG, "null array");
     vec_to_f32(y, x, n, (cudaStream_t)stream);
+    MG_CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status mg_convert_f64_to_f32_pow2(const double* x, float* y, size_t n, int shift, void* stream)
+{
+    if (n == 0) return MG_OK;
+    if (!x || !y) return fail(MG_ERR_INVALID_ARG, "null array");
+    if (shift < -1022 || shift > 1023) return fail(MG_ERR_INVALID_ARG, "shift out of range");
+    vec_to_f32_pow2(y, x, n, shift, (cudaStream_t)stream);
     MG_CK(cudaGetLastError());
     return MG_OK;
 }

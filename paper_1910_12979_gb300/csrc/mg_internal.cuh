@@ -57,7 +57,8 @@ struct DevScalars {
     double red[kRedSlots];     // last reduction results
     double fnorm2;             // ||f||^2 of the system being solved
     double rnorm2;             // ||f - L phi||^2 / ||f||^2, latest (squared relative residual)
-    double fscale;             // r32 = (f - L phi) / fscale in mixed refinement
+    double fscale;             // r32 = (f - L phi) / fscale in mixed refinement: the power of two <= ||f||
+    double rscale2;            // (fscale / ||f||)^2: turns the sum of r32^2 into ||f - L phi||^2 / ||f||^2
     double mean;               // mean removed from f (singular problems)
     double src2;               // ||beta0 S||^2 or ||S_N||^2
     double con2;               // post-projection constraint^2
@@ -129,8 +130,9 @@ void cell_prolong_add(int dim, const CellLevel<T>& F, const CellLevel<T>& C, T* 
                       cudaStream_t s);
 // r = b - L x in FP64; optional FP32 copy r/scale; partials of sum (r/scale)^2
 // (accumulated in FP32: the norm only steers convergence decisions)
+// vec: the four-cells-per-thread kernel where the level allows it (same results)
 void cell_resid64(int dim, const CellLevel<double>& L, const double* x, const double* b, float* r32,
-                  const double* scale, double* partials, cudaStream_t s);
+                  const double* scale, double* partials, cudaStream_t s, bool vec = true);
 void cell_apply64(int dim, const CellLevel<double>& L, const double* x, double* out, cudaStream_t s);
 // f = D(beta0 U) - beta0 S with partials {sum f, sum (beta0 S)^2, sum f^2}; f may be null
 void cell_rhs(int dim, const CellLevel<double>& L, const double* h, const double* const U[3],
@@ -179,6 +181,11 @@ bool node_v4_ok(int dim, const NodeLevel<float>& L, const float* x, const float*
 void node_v4(const NodeLevel<float>& L, const float* x, float* out, const float* b, float omega, bool resid,
              cudaStream_t s, int bxw = 0, int kz = 0);
 bool node_prolong_v4_ok(int dim, const NodeLevel<float>& F, const float* xf, const float* xc);
+// full-weighting restriction of FP32 3-D nodal levels with x periodic, two
+// coarse nodes per thread (same results as k_node_restrict)
+bool node_restrict_v4_ok(int dim, const NodeLevel<float>& F, const float* rf, const float* bc);
+void node_restrict_v4(const NodeLevel<float>& F, const NodeLevel<float>& C, const float* rf, float* bc,
+                      cudaStream_t s);
 void node_prolong_v4(const NodeLevel<float>& F, const NodeLevel<float>& C, float* xf, const float* xc, cudaStream_t s);
 void node_resid64(int dim, const NodeLevel<double>& L, const double* x, const double* b, float* r32,
                   const double* scale, double* partials, cudaStream_t s);
@@ -204,13 +211,16 @@ template <typename T>
 void node_zero_dirichlet(int dim, const NodeLevel<T>& L, T* x, cudaStream_t s);
 
 // Generic helpers.
-void reduce_finalize(const double* partials, int nslots, double* out, cudaStream_t s);
+// out[q] = sum of the partials of slot q (times *mul when mul is given)
+void reduce_finalize(const double* partials, int nslots, double* out, cudaStream_t s, const double* mul = nullptr);
 // partials {sum v, sum v^2} of v[0..n)
 void vec_sum_sq(const double* v, size_t n, double* partials, cudaStream_t s);
 // v[i] -= *mean (mean = sum / count read from a device scalar)
 void vec_sub_mean(double* v, size_t n, const double* sum, double count, cudaStream_t s);
 void vec_copy_f64(double* dst, const double* src, size_t n, cudaStream_t s);
 void vec_to_f32(float* dst, const double* src, size_t n, cudaStream_t s);
+// dst = src * 2^shift rounded to binary32 (the FP64 residual kernels' scaled conversion)
+void vec_to_f32_pow2(float* dst, const double* src, size_t n, int shift, cudaStream_t s);
 void vec_to_f64(double* dst, const float* src, size_t n, cudaStream_t s);
 void vec_recip(double* dst, const double* src, size_t n, cudaStream_t s);
 // r32 = f / scale and partials of its squared norm: the residual of x = 0

@@ -86,15 +86,6 @@ __global__ void k_node_resid(NodeLevel<T> L, const T* __restrict__ x, const T* _
     r[t] = b[t] - fmadd(dg, x[t], off);
 }
 
-// fine lattice position q on an axis: wrapped when periodic; false outside
-__device__ __forceinline__ bool fine_pos(int q, int n, int bc, int& w)
-{
-    if (bc == BCP) { w = wrap(q, n); return true; }
-    if (q < 0 || q > n) return false;
-    w = q;
-    return true;
-}
-
 // full weighting, R = 2^-dim P^T
 template <int DIM, typename T>
 __global__ void k_node_restrict(NodeLevel<T> F, NodeLevel<T> C, const T* __restrict__ rf, T* __restrict__ bc)
@@ -118,7 +109,7 @@ __global__ void k_node_restrict(NodeLevel<T> F, NodeLevel<T> C, const T* __restr
                 int a;
                 if (!fine_pos(2 * i + ox, F.nx, F.bc.lo[0], a)) continue;
                 const T wx = (ox == 0) ? T(1) : T(0.5);
-                s += wz * wy * wx * rf[((size_t)c * F.Ny + b) * F.Nx + a];
+                s = fmadd(wz * wy * wx, rf[((size_t)c * F.Ny + b) * F.Nx + a], s);
             }
         }
     }
@@ -289,7 +280,7 @@ __global__ void k_node_resid64(NodeLevel<double> L, const double* __restrict__ x
                                double* __restrict__ partials)
 {
     const int total = L.Nx * L.Ny * L.Nz;
-    const double inv = 1.0 / *scale;
+    const int sh = pow2_shift(*scale);
     float acc = 0.f;
     const NodePhi<double> ph{x, L.Nx, L.Ny};
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
@@ -300,7 +291,7 @@ __global__ void k_node_resid64(NodeLevel<double> L, const double* __restrict__ x
             double off, dg;
             node_row<DIM>(L, i, j, k, ph, off, dg);
             const double d = HAS_DIAG ? L.diag[t] : dg;
-            rs = f64_to_f32_rn((b[t] - (off + d * x[t])) * inv);
+            rs = f64_to_f32_pow2(b[t] - (off + d * x[t]), sh);
         }
         acc = fmaf(rs, rs, acc);
         if (r32) r32[t] = rs;
@@ -395,7 +386,7 @@ k_node_resid64_sf(NodeLevel<double> L, NodeEdges E, const double* __restrict__ x
     const long long G = (long long)tx_n * ty_n * Nz;
     const long long g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    const double inv = 1.0 / *scale;
+    const int rsh = pow2_shift(*scale);
     const double c12 = L.ih2 / 12.0;
     const size_t nplane = (size_t)Nx * Ny, cplane = (size_t)nx * ny;
     float acc = 0.f;
@@ -531,7 +522,7 @@ k_node_resid64_sf(NodeLevel<double> L, NodeEdges E, const double* __restrict__ x
                     t = fmadd(-wz_prev, sh.xs[sm][ly + 1][lx + 1], t);
                     t = fmadd(-wz, sh.xs[sp][ly + 1][lx + 1], t);
                     const double Lx = fmadd(E.dq[row + i], xi, t * c12);
-                    rs = f64_to_f32_rn((b[row + i] - Lx) * inv);
+                    rs = f64_to_f32_pow2(b[row + i] - Lx, rsh);
                 }
                 wz_prev = wz;
                 acc = fmaf(rs, rs, acc);
@@ -666,6 +657,12 @@ void node_resid(int dim, const NodeLevel<T>& L, const T* x, const T* b, T* r, bo
 template <typename T>
 void node_restrict(int dim, const NodeLevel<T>& F, const NodeLevel<T>& C, const T* rf, T* bc, cudaStream_t s)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (node_restrict_v4_ok(dim, F, rf, bc)) {
+            node_restrict_v4(F, C, rf, bc, s);
+            return;
+        }
+    }
     if (dim == 2) MGP_LAUNCH(k_node_restrict<2, T><<<nb(nnod(C)), kThreads, 0, s>>>(F, C, rf, bc));
     else MGP_LAUNCH(k_node_restrict<3, T><<<nb(nnod(C)), kThreads, 0, s>>>(F, C, rf, bc));
 }

@@ -24,6 +24,15 @@ __device__ __forceinline__ bool cell_ok(int c, int n, int bc, int& w)
     return true;
 }
 
+// fine node position q on an axis of n cells: wrapped when periodic, absent outside 0 .. n otherwise
+__device__ __forceinline__ bool fine_pos(int q, int n, int bc, int& w)
+{
+    if (bc == BCP) { w = wrap(q, n); return true; }
+    if (q < 0 || q > n) return false;
+    w = q;
+    return true;
+}
+
 __device__ __forceinline__ int node_nb(int p, int N, int bc)  // periodic wrap of a node index
 {
     return bc == BCP ? wrap(p, N) : p;

@@ -259,3 +259,59 @@ void node_prolong_v4(const NodeLevel<float>& F, const NodeLevel<float>& C, float
 }
 
 }  // namespace mgp
+
+namespace mgp {
+
+// Full-weighting restriction b_c = 2^-3 sum w r_f of FP32 nodal levels, two
+// coarse nodes (2q, 2q+1) of a row per thread.  With x periodic their fine
+// x-positions 4q-1 .. 4q+3 are one 16-byte load and one scalar per fine row;
+// the (up to) 3 x 3 fine rows are visited in k_node_restrict's order (z, then
+// y, then x: -1, 0, +1) with the same weights and fused multiply-adds, so the
+// coarse values are identical.  Requirements: 3-D, x periodic, nx % 4 == 0.
+__global__ void __launch_bounds__(256)
+k_node_restrict_v4(NodeLevel<float> F, NodeLevel<float> C, const float* __restrict__ rf, float* __restrict__ bc)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;   // coarse nodes 2q, 2q + 1
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;   // coarse row
+    const int k = blockIdx.z;                              // coarse plane
+    if (2 * q >= C.Nx || j >= C.Ny) return;
+    const int f0 = 4 * q, fl = f0 > 0 ? f0 - 1 : F.Nx - 1;
+    float s0 = 0.f, s1 = 0.f;
+    for (int oz = -1; oz <= 1; ++oz) {
+        int c;
+        if (!fine_pos(2 * k + oz, F.nz, F.bc.lo[2], c)) continue;
+        const float wz = (oz == 0) ? 1.f : 0.5f;
+        for (int oy = -1; oy <= 1; ++oy) {
+            int b;
+            if (!fine_pos(2 * j + oy, F.ny, F.bc.lo[1], b)) continue;
+            const float wy = (oy == 0) ? 1.f : 0.5f;
+            const float* r = rf + ((size_t)c * F.Ny + b) * F.Nx;
+            const float4 v = nld4(r + f0);
+            const float vl = r[fl];
+            const float wh = wz * wy * 0.5f, w1 = wz * wy * 1.f;
+            s0 = fmadd(wh, v.y, fmadd(w1, v.x, fmadd(wh, vl, s0)));
+            s1 = fmadd(wh, v.w, fmadd(w1, v.z, fmadd(wh, v.y, s1)));
+        }
+    }
+    float2 o;
+    o.x = node_dirichlet(C, 2 * q, j, k, 3) ? 0.f : s0 * (1.f / 8.f);
+    o.y = node_dirichlet(C, 2 * q + 1, j, k, 3) ? 0.f : s1 * (1.f / 8.f);
+    *reinterpret_cast<float2*>(bc + ((size_t)k * C.Ny + j) * C.Nx + 2 * q) = o;
+}
+
+bool node_restrict_v4_ok(int dim, const NodeLevel<float>& F, const float* rf, const float* bc)
+{
+    return dim == 3 && F.bc.lo[0] == BCP && F.nx % 4 == 0 && F.Nx == F.nx && ((uintptr_t)rf & 15) == 0 &&
+           ((uintptr_t)bc & 7) == 0;
+}
+
+void node_restrict_v4(const NodeLevel<float>& F, const NodeLevel<float>& C, const float* rf, float* bc, cudaStream_t s)
+{
+    const int np = C.Nx / 2;
+    const int bx = np >= 32 ? 32 : np >= 16 ? 16 : np >= 8 ? 8 : np >= 4 ? 4 : np >= 2 ? 2 : 1;
+    const dim3 block(bx, 256 / bx);
+    const dim3 grid((np + bx - 1) / bx, (C.Ny + block.y - 1) / block.y, C.Nz);
+    MGP_LAUNCH(k_node_restrict_v4<<<grid, block, 0, s>>>(F, C, rf, bc));
+}
+
+}  // namespace mgp

@@ -101,6 +101,8 @@ SIGNATURES = [
                                           ctypes.c_void_p * 3, ctypes.c_void_p * 3, ctypes.c_void_p]),
     ("mg_convert_f64_to_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("mg_convert_f32_to_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("mg_convert_f64_to_f32_pow2", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     ("mg_reciprocal_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("mg_smoother_kind", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mg_prof_enable", None, [ctypes.c_int]),
@@ -280,6 +282,10 @@ def mg_convert_f64_to_f32(x_ptr, y_ptr, n, stream=None):
 
 def mg_convert_f32_to_f64(x_ptr, y_ptr, n, stream=None):
     check(load().mg_convert_f32_to_f64(x_ptr, y_ptr, n, stream), "mg_convert_f32_to_f64")
+
+
+def mg_convert_f64_to_f32_pow2(x_ptr, y_ptr, n, shift, stream=None):
+    check(load().mg_convert_f64_to_f32_pow2(x_ptr, y_ptr, n, shift, stream), "mg_convert_f64_to_f32_pow2")
 
 
 def mg_reciprocal_f64(x_ptr, y_ptr, n, stream=None):

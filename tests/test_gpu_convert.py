@@ -83,3 +83,19 @@ def test_reciprocal_within_one_ulp():
     assert torch.equal(torch.isnan(y), nan)
     yi, ri = y[~nan].view(torch.int64), ref[~nan].view(torch.int64)
     assert int((yi - ri).abs().max()) <= 1   # same sign, neighbouring bit patterns
+
+
+@pytest.mark.parametrize("shift", [-60, -13, 0, 7, 100])
+def test_f64_to_f32_pow2_matches_scaled_hardware_rounding(shift):
+    """The FP64 residual kernels fold their power-of-two scale into the
+    conversion: the result must equal converting the exactly scaled double."""
+    x = torch.from_numpy(_f64_cases(np.random.default_rng(1000 + shift))).to(DEV)
+    y = torch.empty(x.numel(), dtype=torch.float32, device=DEV)
+    N.mg_convert_f64_to_f32_pow2(x.data_ptr(), y.data_ptr(), x.numel(), shift, None)
+    ref = (x * 2.0 ** shift).float()
+    torch.cuda.synchronize()
+    nan = torch.isnan(ref)
+    assert torch.equal(torch.isnan(y), nan)
+    assert torch.equal(y[~nan].view(torch.int32), ref[~nan].view(torch.int32))
+    with pytest.raises(N.MGError):
+        N.mg_convert_f64_to_f32_pow2(x.data_ptr(), y.data_ptr(), x.numel(), 2000, None)

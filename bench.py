@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--nu", default="2,1",
                     help="pre,post smoothing sweeps of the MAC V-cycle (nodal: --nu-nodal)")
     ap.add_argument("--nu-nodal", default="2,2", help="pre,post smoothing sweeps of the nodal V-cycle")
+    ap.add_argument("--omega-nodal", type=float, default=0.9, help="damping of the nodal Jacobi smoother")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the smoother kernels of both hierarchies at setup (MG_FLAG_AUTOTUNE) and report "
+                         "the choices")
     ap.add_argument("--inner-nodal", type=int, default=0,
                     help="FP32 V-cycles per FP64 refinement step of the nodal solve (0: the library's choice)")
     ap.add_argument("--coarsest", type=int, default=0,
@@ -601,10 +605,14 @@ def main():
         cm = {"coarsest_max": args.coarsest} if args.coarsest > 0 else {}
         nu_c = [int(v) for v in args.nu.split(",")]
         nu_n = [int(v) for v in args.nu_nodal.split(",")]
+        if args.autotune:
+            fl |= N.MG_FLAG_AUTOTUNE
         mac = ProjectionSolver(p["geom"], sigma, loc="cell", prec=prec, stream=stream, flags=fl,
                                inner_cycles=args.inner_mac, nu1=nu_c[0], nu2=nu_c[1], **cm)
-        nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream, flags=N.MG_FLAG_ZERO_GUESS,
-                               inner_cycles=args.inner_nodal, nu1=nu_n[0], nu2=nu_n[1], **cm)
+        nod = ProjectionSolver(p["geom"], sigma, loc="nodal", prec=prec, stream=stream,
+                               flags=N.MG_FLAG_ZERO_GUESS | (N.MG_FLAG_AUTOTUNE if args.autotune else 0),
+                               inner_cycles=args.inner_nodal, nu1=nu_n[0], nu2=nu_n[1], omega=args.omega_nodal,
+                               **cm)
         phim = torch.zeros(mac.vec_shape, dtype=torch.float64, device=dev)
         phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)
         return mac, nod, phim, phin
@@ -701,7 +709,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": dict(workload_config(n, args.tol), parallelism=f"independent solves x{world}",
-                           cell_smoother=args.sweep, smoothing={"mac": args.nu, "nodal": args.nu_nodal}),
+                           cell_smoother=args.sweep, smoothing={"mac": args.nu, "nodal": args.nu_nodal},
+                           nodal_jacobi_omega=args.omega_nodal,
+                           **({"autotuned_kinds": {nm: [N.mg_smoother_kind(sv.handle, l) for l in range(10)
+                                                        if N.mg_smoother_kind(sv.handle, l) >= 0]
+                                                   for nm, sv in (("mac", mixed[0]), ("nodal", mixed[1]))}}
+                              if args.autotune else {})),
             "clocks": clocks, "gpu_launches": launches, "roofline": roof_line,
             "solver": {"mac": {k: st_mac[k] for k in ("iters", "vcycles", "rel_resid", "rel_constraint")},
                        "nodal": {k: st_nod[k] for k in ("iters", "vcycles", "rel_resid", "rel_constraint")}}}

@@ -660,7 +660,7 @@ int inner_cycles(const mg_handle* h)
     return 2;
 }
 
-// Mixed refinement step: a few FP32 V-cycles on A e = r / ||f|| from e = 0,
+// Mixed refinement step: a few FP32 V-cycles on A e = r / fscale from e = 0,
 // then phi += ||f|| e in FP64.
 void mixed_correction(mg_handle* h, double* phi, int cycles)
 {

@@ -661,7 +661,7 @@ int inner_cycles(const mg_handle* h)
 }
 
 // Mixed refinement step: a few FP32 V-cycles on A e = r / fscale from e = 0,
-// then phi += ||f|| e in FP64.
+// then phi += fscale e in FP64.
 void mixed_correction(mg_handle* h, double* phi, int cycles)
 {
     float* e = h->lev[0].x32;

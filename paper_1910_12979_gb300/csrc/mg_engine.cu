@@ -630,15 +630,36 @@ void vcycle_node(mg_handle* h, T* x0, const T* b0, bool zero_init)
     const int dim = h->dim, L = h->nlev;
     auto X = [&](int l) { return l == 0 ? x0 : lx<T>(h, l); };
     auto Bv = [&](int l) { return l == 0 ? b0 : (const T*)lb<T>(h, l); };
-    for (int l = 0; l < L - 1; ++l) {
+    // levels lc .. L-1 (at most kCoarseNodes stored nodes each) run as one launch
+    int lc = L;
+    if (!(h->opt.flags & MG_FLAG_NO_FUSED)) {
+        lc = L - 1;
+        while (lc > 0 && h->lev[lc - 1].nvec <= (size_t)kCoarseNodes && L - (lc - 1) <= kCoarseMaxLevels) --lc;
+        if (lc == L - 1) lc = L;   // a single level: nothing to fuse
+    }
+    for (int l = 0; l < lc && l < L - 1; ++l) {
         if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
         node_smooth<T>(h, l, X(l), Bv(l), h->opt.nu1);
         node_resid<T>(dim, nview<T>(h, l), X(l), Bv(l), lr<T>(h, l), !(h->opt.flags & MG_FLAG_NO_FUSED), s,
                       h->lev[l].kind);
         node_restrict<T>(dim, nview<T>(h, l), nview<T>(h, l + 1), lr<T>(h, l), lb<T>(h, l + 1), s);
     }
-    dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
-    for (int l = L - 2; l >= 0; --l) {
+    if (lc < L) {
+        NodeLevel<T> Ls[kCoarseMaxLevels];
+        T *xs[kCoarseMaxLevels], *bs[kCoarseMaxLevels], *ts[kCoarseMaxLevels], *rs[kCoarseMaxLevels];
+        for (int l = lc; l < L; ++l) {
+            Ls[l - lc] = nview<T>(h, l);
+            xs[l - lc] = X(l);
+            bs[l - lc] = const_cast<T*>(Bv(l));
+            ts[l - lc] = lt<T>(h, l);
+            rs[l - lc] = lr<T>(h, l);
+        }
+        node_coarse_cycle<T>(dim, L - lc, Ls, xs, bs, ts, rs, h->Minv, h->Nd, h->opt.nu1, h->opt.nu2,
+                             (T)h->opt.omega, lc > 0 || zero_init, s);
+    } else {
+        dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
+    }
+    for (int l = (lc < L ? lc : L - 1) - 1; l >= 0; --l) {
         node_prolong_add<T>(dim, nview<T>(h, l), nview<T>(h, l + 1), X(l), X(l + 1), s);
         node_smooth<T>(h, l, X(l), Bv(l), h->opt.nu2);
     }

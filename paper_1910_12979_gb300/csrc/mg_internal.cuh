@@ -152,6 +152,14 @@ constexpr int kCoarseMaxLevels = 8;
 template <typename T>
 void coarse_cycle(int dim, int nlev, const CellLevel<T>* L, T* const* x, T* const* b, const double* Minv, int Nd,
                   int nu1, int nu2, int order, bool zero_first, cudaStream_t s);
+// The coarse end of a nodal V-cycle in one CTA (levels of at most kCoarseNodes
+// stored nodes): zero, nu1 Jacobi sweeps (ping-pong with t), residual into r,
+// restriction, dense bottom solve, prolongation, nu2 sweeps; same arithmetic
+// as the launched kernels.
+constexpr int kCoarseNodes = 1024;
+template <typename T>
+void node_coarse_cycle(int dim, int nlev, const NodeLevel<T>* L, T* const* x, T* const* b, T* const* t, T* const* r,
+                       const double* Minv, int Nd, int nu1, int nu2, T omega, bool zero_first, cudaStream_t s);
 
 // Nodal system.
 void node_coarsen_sigma(int dim, const NodeLevel<double>& F, const NodeLevel<double>& C, double* sc,

@@ -64,12 +64,7 @@ __global__ void k_jacobi(NodeLevel<T> L, const T* __restrict__ x, T* __restrict_
     if (t >= total) return;
     int i, j, k;
     unflat(t, L.Nx, L.Ny, i, j, k);
-    if (node_dirichlet(L, i, j, k, DIM)) { xo[t] = T(0); return; }
-    T off, dg;
-    node_row<DIM>(L, i, j, k, NodePhi<T>{x, L.Nx, L.Ny}, off, dg);
-    const T xi = x[t];
-    const T id = L.invd ? L.invd[t] : recip(dg);
-    xo[t] = fmadd(omega * (b[t] - fmadd(dg, xi, off)), id, xi);
+    xo[t] = node_jacobi_value<DIM>(L, x, b, t, i, j, k, omega);
 }
 
 template <int DIM, typename T>
@@ -80,10 +75,7 @@ __global__ void k_node_resid(NodeLevel<T> L, const T* __restrict__ x, const T* _
     if (t >= total) return;
     int i, j, k;
     unflat(t, L.Nx, L.Ny, i, j, k);
-    if (node_dirichlet(L, i, j, k, DIM)) { r[t] = T(0); return; }
-    T off, dg;
-    node_row<DIM>(L, i, j, k, NodePhi<T>{x, L.Nx, L.Ny}, off, dg);
-    r[t] = b[t] - fmadd(dg, x[t], off);
+    r[t] = node_resid_value<DIM>(L, x, b, t, i, j, k);
 }
 
 // full weighting, R = 2^-dim P^T
@@ -95,25 +87,7 @@ __global__ void k_node_restrict(NodeLevel<T> F, NodeLevel<T> C, const T* __restr
     if (t >= total) return;
     int i, j, k;
     unflat(t, C.Nx, C.Ny, i, j, k);
-    if (node_dirichlet(C, i, j, k, DIM)) { bc[t] = T(0); return; }
-    T s = T(0);
-    for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz) {
-        int c = 0;
-        if (DIM == 3 && !fine_pos(2 * k + oz, F.nz, F.bc.lo[2], c)) continue;
-        const T wz = (oz == 0) ? T(1) : T(0.5);
-        for (int oy = -1; oy <= 1; ++oy) {
-            int b;
-            if (!fine_pos(2 * j + oy, F.ny, F.bc.lo[1], b)) continue;
-            const T wy = (oy == 0) ? T(1) : T(0.5);
-            for (int ox = -1; ox <= 1; ++ox) {
-                int a;
-                if (!fine_pos(2 * i + ox, F.nx, F.bc.lo[0], a)) continue;
-                const T wx = (ox == 0) ? T(1) : T(0.5);
-                s = fmadd(wz * wy * wx, rf[((size_t)c * F.Ny + b) * F.Nx + a], s);
-            }
-        }
-    }
-    bc[t] = s * (T(1) / T(1 << DIM));
+    bc[t] = node_restrict_value<DIM>(F, C, rf, i, j, k);
 }
 
 // trilinear prolongation and correction
@@ -126,22 +100,7 @@ __global__ void k_node_prolong(NodeLevel<T> F, NodeLevel<T> C, T* __restrict__ x
     int i, j, k;
     unflat(t, F.Nx, F.Ny, i, j, k);
     if (node_dirichlet(F, i, j, k, DIM)) return;
-    int lo[3] = {i >> 1, j >> 1, k >> 1}, cnt[3] = {1 + (i & 1), 1 + (j & 1), DIM == 3 ? 1 + (k & 1) : 1};
-    const int Nc[3] = {C.Nx, C.Ny, C.Nz};
-    T s = T(0);
-    for (int c = 0; c < cnt[2]; ++c)
-        for (int b = 0; b < cnt[1]; ++b)
-            for (int a = 0; a < cnt[0]; ++a) {
-                int q[3] = {lo[0] + a, lo[1] + b, lo[2] + c};
-                T w = T(1);
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) {
-                    if (cnt[d] == 2) w *= T(0.5);
-                    if (C.bc.lo[d] == BCP && q[d] >= Nc[d]) q[d] -= Nc[d];
-                }
-                s = fmadd(w, xc[((size_t)q[2] * C.Ny + q[1]) * C.Nx + q[0]], s);
-            }
-    xf[t] += s;
+    xf[t] += node_prolong_value<DIM>(F, C, xc, i, j, k);
 }
 
 // ------------------------------------------------------ tiled node sweeps

@@ -93,6 +93,83 @@ struct NodePhi {
     __device__ __forceinline__ T operator()(int i, int j, int k) const { return p[((size_t)k * Ny + j) * Nx + i]; }
 };
 
+// Per-node arithmetic shared by the plain kernels and the one-CTA coarse
+// cycle, so both compute the same bits.  t is the flat index of (i, j, k).
+
+// damped Jacobi value: x + omega (b - L x) / diag; Dirichlet nodes 0
+template <int DIM, typename T>
+__device__ __forceinline__ T node_jacobi_value(const NodeLevel<T>& L, const T* x, const T* b, size_t t, int i, int j,
+                                               int k, T omega)
+{
+    if (node_dirichlet(L, i, j, k, DIM)) return T(0);
+    T off, dg;
+    node_row<DIM>(L, i, j, k, NodePhi<T>{x, L.Nx, L.Ny}, off, dg);
+    const T xi = x[t];
+    const T id = L.invd ? L.invd[t] : recip(dg);
+    return fmadd(omega * (b[t] - fmadd(dg, xi, off)), id, xi);
+}
+
+// residual b - L x; Dirichlet nodes 0
+template <int DIM, typename T>
+__device__ __forceinline__ T node_resid_value(const NodeLevel<T>& L, const T* x, const T* b, size_t t, int i, int j,
+                                              int k)
+{
+    if (node_dirichlet(L, i, j, k, DIM)) return T(0);
+    T off, dg;
+    node_row<DIM>(L, i, j, k, NodePhi<T>{x, L.Nx, L.Ny}, off, dg);
+    return b[t] - fmadd(dg, x[t], off);
+}
+
+// full weighting R = 2^-dim P^T at coarse node (i, j, k); Dirichlet nodes 0
+template <int DIM, typename T>
+__device__ __forceinline__ T node_restrict_value(const NodeLevel<T>& F, const NodeLevel<T>& C, const T* rf, int i,
+                                                 int j, int k)
+{
+    if (node_dirichlet(C, i, j, k, DIM)) return T(0);
+    T s = T(0);
+    for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz) {
+        int c = 0;
+        if (DIM == 3 && !fine_pos(2 * k + oz, F.nz, F.bc.lo[2], c)) continue;
+        const T wz = (oz == 0) ? T(1) : T(0.5);
+        for (int oy = -1; oy <= 1; ++oy) {
+            int b;
+            if (!fine_pos(2 * j + oy, F.ny, F.bc.lo[1], b)) continue;
+            const T wy = (oy == 0) ? T(1) : T(0.5);
+            for (int ox = -1; ox <= 1; ++ox) {
+                int a;
+                if (!fine_pos(2 * i + ox, F.nx, F.bc.lo[0], a)) continue;
+                const T wx = (ox == 0) ? T(1) : T(0.5);
+                s = fmadd(wz * wy * wx, rf[((size_t)c * F.Ny + b) * F.Nx + a], s);
+            }
+        }
+    }
+    return s * (T(1) / T(1 << DIM));
+}
+
+// trilinear prolongation of the coarse correction to fine node (i, j, k)
+// (callers leave Dirichlet nodes unchanged)
+template <int DIM, typename T>
+__device__ __forceinline__ T node_prolong_value(const NodeLevel<T>& F, const NodeLevel<T>& C, const T* xc, int i,
+                                                int j, int k)
+{
+    int lo[3] = {i >> 1, j >> 1, k >> 1}, cnt[3] = {1 + (i & 1), 1 + (j & 1), DIM == 3 ? 1 + (k & 1) : 1};
+    const int Nc[3] = {C.Nx, C.Ny, C.Nz};
+    T s = T(0);
+    for (int c = 0; c < cnt[2]; ++c)
+        for (int b = 0; b < cnt[1]; ++b)
+            for (int a = 0; a < cnt[0]; ++a) {
+                int q[3] = {lo[0] + a, lo[1] + b, lo[2] + c};
+                T w = T(1);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    if (cnt[d] == 2) w *= T(0.5);
+                    if (C.bc.lo[d] == BCP && q[d] >= Nc[d]) q[d] -= Nc[d];
+                }
+                s = fmadd(w, xc[((size_t)q[2] * C.Ny + q[1]) * C.Nx + q[0]], s);
+            }
+    return s;
+}
+
 // tile of the shared-memory nodal kernels (nodes in x, y)
 constexpr int kNTX = 32, kNTY = 8;
 

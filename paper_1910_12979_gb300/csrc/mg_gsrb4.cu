@@ -102,8 +102,33 @@ k_gsrb_v4(CellLevel<float> L, float* __restrict__ x, const float* __restrict__ b
         }
         return (off - el(bb, p)) * recip(dg);
     };
+    // quads away from every non-periodic boundary: the same operations in the
+    // same order, without the per-face presence tests
+    const bool inner = hym && hyp && (DIM == 2 || (hzm && hzp)) && (px || (i0 > 0 && i0 + 4 < nx));
+    auto update_in = [&](int p, float bxl, float bxh, float xl, float xh) -> float {
+        float off = 0.f, dg = 0.f;
+        off = fmadd(bxl, xl, off); dg += bxl;
+        off = fmadd(bxh, xh, off); dg += bxh;
+        const float byl = el(fyl, p), byh = el(fyh, p);
+        off = fmadd(byl, el(xym, p), off); dg += byl;
+        off = fmadd(byh, el(xyp, p), off); dg += byh;
+        if (DIM == 3) {
+            const float bzl = el(fzl, p), bzh = el(fzh, p);
+            off = fmadd(bzl, el(xzm, p), off); dg += bzl;
+            off = fmadd(bzh, el(xzp, p), off); dg += bzh;
+        }
+        return (off - el(bb, p)) * recip(dg);
+    };
     float4 out = xc;
-    if (p0 == 0) {
+    if (inner) {
+        if (p0 == 0) {
+            out.x = update_in(0, fx0, fx1, xout, xc.y);
+            out.z = update_in(2, fx2, fx3, xc.y, xc.w);
+        } else {
+            out.y = update_in(1, fx0, fx1, xc.x, xc.z);
+            out.w = update_in(3, fx2, fx3, xc.z, xout);
+        }
+    } else if (p0 == 0) {
         out.x = update(0, fx0, fx1, xout, xc.y);
         out.z = update(2, fx2, fx3, xc.y, xc.w);
     } else {
@@ -193,6 +218,24 @@ k_resid_restrict_v4(CellLevel<float> F, const float* __restrict__ x, const float
     if (last) xr = i0 + 4 < nx ? x[row + i0 + 4] : (px ? x[row] : 0.f);
     const float xs[6] = {xl, xc.x, xc.y, xc.z, xc.w, xr};
     float r[4];
+    // quads away from every non-periodic boundary: the same operations in the
+    // same order, without the per-face presence tests
+    const bool inner = hym && hyp && hzm && hzp && (px || (i0 > 0 && i0 + 4 < nx));
+    if (inner) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            float off = 0.f, dg = 0.f;
+            off = fmadd(fx[p], xs[p], off); dg += fx[p];
+            off = fmadd(fx[p + 1], xs[p + 2], off); dg += fx[p + 1];
+            const float byl = el(fyl, p), byh = el(fyh, p);
+            off = fmadd(byl, el(xym, p), off); dg += byl;
+            off = fmadd(byh, el(xyp, p), off); dg += byh;
+            const float bzl = el(fzl, p), bzh = el(fzh, p);
+            off = fmadd(bzl, el(xzm, p), off); dg += bzl;
+            off = fmadd(bzh, el(xzp, p), off); dg += bzh;
+            r[p] = el(bb, p) - fmadd(-dg, xs[p + 1], off);
+        }
+    } else
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int i = i0 + p;

@@ -1433,12 +1433,15 @@ mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* b0, const
             cell_rhs(dim, cview<double>(h, 0), v0.h, Uc, b0->face, b0->cell, S, nullptr, h->partials, s);
         } else {
             node_project(dim, nview<double>(h, 0), v0.h[0], phi, b0->cell, U, s);
-            node_rhs(dim, nview<double>(h, 0), v0.h[0], Uc, b0->cell, S, nullptr, h->partials, s);
+            // the nodal projection is approximate: its constraint is a diagnostic,
+            // formed in FP32 where the tiled kernel applies (||S_N|| from the FP64 RHS)
+            if (!node_constraint32(dim, nview<double>(h, 0), v0.h[0], Uc, b0->cell, S, h->partials, s))
+                node_rhs(dim, nview<double>(h, 0), v0.h[0], Uc, b0->cell, S, nullptr, h->partials, s);
         }
         reduce_finalize(h->partials, 3, h->d->red, s);
         mg_status r2 = readback(h);
         if (r2 != MG_OK) return r2;
-        const double src2 = h->hs->red[1], con2 = h->hs->red[2];
+        const double src2 = h->loc == MG_LOC_CELL ? h->hs->red[1] : h->hs->src2, con2 = h->hs->red[2];
         local.src_norm = sqrt(src2);
         local.rel_constraint = src2 > 0.0 ? sqrt(con2 / src2) : sqrt(con2);
     }

@@ -210,6 +210,12 @@ void node_resid64_sf(const NodeLevel<double>& L, const NodeEdges& E, const doubl
 void node_apply64(int dim, const NodeLevel<double>& L, const double* x, double* out, cudaStream_t s);
 void node_rhs(int dim, const NodeLevel<double>& L, double h, const double* const U[3], const double* b0,
               const double* S, double* f, double* partials, cudaStream_t s);
+// the post-projection diagnostic D_N(beta0 U) - S_N of the nodal projection
+// with FP32 arithmetic (FP64 inputs rounded as loaded; partial sums in FP64):
+// partials {sum v, sum lump^2, sum v^2} like node_rhs; false (nothing
+// launched) where the tiled kernel does not apply
+bool node_constraint32(int dim, const NodeLevel<double>& L, double h, const double* const U[3], const double* b0,
+                       const double* S, double* partials, cudaStream_t s);
 void node_project(int dim, const NodeLevel<double>& L, double h, const double* phi, const double* b0,
                   double* const U[3], cudaStream_t s);
 template <typename T>

@@ -59,18 +59,24 @@ __global__ void k_node_rhs(NodeLevel<double> L, double h, CPtr3 U, const double*
 // 24 FP64 operations per node instead of about 41 for the 8-cell form.  The
 // fixed kRedBlocks grid splits the (tile, node plane) sequence into equal
 // contiguous shares, so the reduction is deterministic and balanced.
+template <typename C>
 struct NodeRhsShared {
-    double w[4][kNTY + 1][kNTX + 1];  // Wx, Wy, Wz, beta0 S of cells x0-1 .. x0+31, y0-1 .. y0+7
-    double ya[kNTY][kNTX + 1];        // Wx(cell col, row ly) + Wx(cell col, row ly+1)
-    double xa[3][kNTY + 1][kNTX];     // Wy, Wz, beta0 S: (col lx) + (col lx+1)
+    C w[4][kNTY + 1][kNTX + 1];  // Wx, Wy, Wz, beta0 S of cells x0-1 .. x0+31, y0-1 .. y0+7
+    C ya[kNTY][kNTX + 1];        // Wx(cell col, row ly) + Wx(cell col, row ly+1)
+    C xa[3][kNTY + 1][kNTX];     // Wy, Wz, beta0 S: (col lx) + (col lx+1)
 };
 
+// C: the arithmetic type.  double for the right-hand side of the solve; float
+// for the post-projection diagnostic of the (approximate) nodal projection,
+// whose FP64 inputs are rounded to binary32 on the integer pipe as they are
+// loaded (f must then be null).  The partial sums are accumulated in FP64.
+template <typename C>
 __global__ void __launch_bounds__(kNTX * kNTY)
 k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restrict__ b0, const double* __restrict__ S,
                  double* __restrict__ f, double* __restrict__ partials)
 {
     constexpr int TX = kNTX, TY = kNTY, NT = TX * TY, QN = (TX + 1) * (TY + 1);
-    __shared__ NodeRhsShared sh;
+    __shared__ NodeRhsShared<C> sh;
     const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
     const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
     const int tx_n = (Nx + TX - 1) / TX, ty_n = (Ny + TY - 1) / TY;
@@ -78,7 +84,7 @@ k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restric
     const long long g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int lx = threadIdx.x, ly = threadIdx.y;
-    const double wdiv = 1.0 / (4.0 * h), wl = 1.0 / 8.0;
+    const C wdiv = from_f64<C>(1.0 / (4.0 * h)), wl = C(1.0 / 8.0);
     double acc[3] = {0.0, 0.0, 0.0};
 
     for (long long g = g0; g < g1;) {
@@ -100,14 +106,14 @@ k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restric
                 if (gx < 0 || gx >= nx) { if (px) gx = gx < 0 ? gx + nx : gx - nx; else ok = false; }
                 if (gy < 0 || gy >= ny) { if (py) gy = gy < 0 ? gy + ny : gy - ny; else ok = false; }
                 if (gx >= nx || gy >= ny) ok = false;
-                double w0 = 0.0, w1 = 0.0, w2 = 0.0, ws = 0.0;
+                C w0 = C(0), w1 = C(0), w2 = C(0), ws = C(0);
                 if (ok) {
                     const size_t id = ((size_t)gz * ny + gy) * nx + gx;
-                    const double bb = b0[id];
-                    w0 = bb * U.p[0][id];
-                    w1 = bb * U.p[1][id];
-                    w2 = bb * U.p[2][id];
-                    ws = bb * S[id];
+                    const C bb = from_f64<C>(b0[id]);
+                    w0 = bb * from_f64<C>(U.p[0][id]);
+                    w1 = bb * from_f64<C>(U.p[1][id]);
+                    w2 = bb * from_f64<C>(U.p[2][id]);
+                    ws = bb * from_f64<C>(S[id]);
                 }
                 sh.w[0][qy][qx] = w0;
                 sh.w[1][qy][qx] = w1;
@@ -127,8 +133,8 @@ k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restric
             __syncthreads();
         };
         // the per-plane node terms: dx, dy (differences of pair sums), z and source pair sums
-        double pdx, pdy, pz2, ps;
-        auto terms = [&](double& dx, double& dy, double& bz, double& bs) {
+        C pdx, pdy, pz2, ps;
+        auto terms = [&](C& dx, C& dy, C& bz, C& bs) {
             dx = sh.ya[ly][lx + 1] - sh.ya[ly][lx];
             dy = sh.xa[0][ly + 1][lx] - sh.xa[0][ly][lx];
             bz = sh.xa[1][ly][lx] + sh.xa[1][ly + 1][lx];
@@ -140,19 +146,20 @@ k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restric
         const bool own = i < Nx && j < Ny;
         for (int k = z0; k < z1; ++k) {
             plane(k);  // (its first barrier follows every read of the previous plane's W)
-            double dx, dy, bz, bs;
+            C dx, dy, bz, bs;
             terms(dx, dy, bz, bs);
             if (own) {
                 const size_t id = ((size_t)k * Ny + j) * Nx + i;
-                double v = 0.0, lump = 0.0;
+                C v = C(0), lump = C(0);
                 if (!node_dirichlet(L, i, j, k, 3)) {
                     lump = (bs + ps) * wl;
                     v = fmadd(((dx + pdx) + (dy + pdy)) + (bz - pz2), wdiv, -lump);
                 }
-                if (f) f[id] = v;
-                acc[0] += v;
-                acc[1] = fmadd(lump, lump, acc[1]);
-                acc[2] = fmadd(v, v, acc[2]);
+                const double vd = to_f64(v), ld = to_f64(lump);
+                if (f) f[id] = vd;
+                acc[0] += vd;
+                acc[1] = fmadd(ld, ld, acc[1]);
+                acc[2] = fmadd(vd, vd, acc[2]);
             }
             pdx = dx;
             pdy = dy;
@@ -262,11 +269,20 @@ void node_rhs(int dim, const NodeLevel<double>& L, double h, const double* const
 {
     CPtr3 u{{U[0], U[1], dim == 3 ? U[2] : nullptr}};
     if (dim == 3 && L.Nx >= kNTX && L.Ny >= kNTY) {
-        MGP_LAUNCH(k_node_rhs_tiled<<<kRedBlocks, dim3(kNTX, kNTY), 0, s>>>(L, h, u, b0, S, f, partials));
+        MGP_LAUNCH(k_node_rhs_tiled<double><<<kRedBlocks, dim3(kNTX, kNTY), 0, s>>>(L, h, u, b0, S, f, partials));
         return;
     }
     if (dim == 2) MGP_LAUNCH(k_node_rhs<2><<<kRedBlocks, kThreads, 0, s>>>(L, h, u, b0, S, f, partials));
     else MGP_LAUNCH(k_node_rhs<3><<<kRedBlocks, kThreads, 0, s>>>(L, h, u, b0, S, f, partials));
+}
+
+bool node_constraint32(int dim, const NodeLevel<double>& L, double h, const double* const U[3], const double* b0,
+                       const double* S, double* partials, cudaStream_t s)
+{
+    if (!(dim == 3 && L.Nx >= kNTX && L.Ny >= kNTY)) return false;
+    CPtr3 u{{U[0], U[1], U[2]}};
+    MGP_LAUNCH(k_node_rhs_tiled<float><<<kRedBlocks, dim3(kNTX, kNTY), 0, s>>>(L, h, u, b0, S, nullptr, partials));
+    return true;
 }
 
 void node_project(int dim, const NodeLevel<double>& L, double h, const double* phi, const double* b0,

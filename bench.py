@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import math
 import json
 import os
 import statistics
@@ -738,15 +739,25 @@ def main():
     if not args.no_e2e:
         mac, nod, phim, phin = mixed
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        h_in = [pin(p["sigma"]), pin(p["beta0"]), pin(p["S"])] + [pin(b) for b in p["beta0_face"]] + \
-               [pin(u) for u in p["U_mac"]] + [pin(u) for u in p["U_cell"]]
+        # the base state of the plane-parallel atmosphere depends on height only: it is uploaded as
+        # radial tables every half cell (so every cell and face centre is a table point) and expanded
+        # to sigma, beta0 at cells and beta0 at faces on the device by mg_base_state_map
+        hz = p["geom"]["h"][2]
+        nr = 2 * n + 1
+        z_r = 0.5 * hz * np.arange(nr)
+        rho_r = np.exp(-math.log(1e3) * z_r)
+        beta_r = rho_r ** (1.0 / I.GAMMA1)
+        geo = N.mg_geometry(3, (n, n, n), tuple(p["geom"]["h"]), N.MG_LOC_CELL)
+        h_in = [pin(beta_r), pin(rho_r), pin(p["S"])] + [pin(u) for u in p["U_mac"]] + [pin(u) for u in p["U_cell"]]
         h2d = sum(t.numel() * t.element_size() for t in h_in)
         ustream = torch.cuda.Stream(device=dev)   # host -> device
         dstream = torch.cuda.Stream(device=dev)   # device -> host
         with torch.cuda.stream(stream):
-            d_sets = [[torch.empty_like(sigma) for _ in range(3)] + [torch.empty_like(b) for b in b0f] +
+            d_sets = [[torch.empty(nr, dtype=torch.float64, device=dev) for _ in range(2)] + [torch.empty_like(sigma)] +
                       [torch.empty_like(u) for u in U0m] + [torch.empty_like(u) for u in U0c] for _ in range(2)]
             w_sets = [[torch.empty_like(u) for u in Um + Uc] for _ in range(2)]
+            m_sig, m_b0 = torch.empty_like(sigma), torch.empty_like(sigma)
+            m_b0f = [torch.empty_like(b) for b in b0f]
         h_out = [[torch.empty_like(u, device="cpu").pin_memory() for u in Um + Uc] for _ in range(2)]
         d2h = sum(t.numel() * t.element_size() for t in h_out[0])
         h2d_done = [torch.cuda.Event() for _ in range(2)]
@@ -761,12 +772,16 @@ def main():
                 h2d_done[i].record(ustream)
 
         def compute(i):
-            sg, b0, Sv = d_sets[i][0], d_sets[i][1], d_sets[i][2]
-            bf, u0m, u0c = d_sets[i][3:6], d_sets[i][6:9], d_sets[i][9:12]
+            br, rr, Sv = d_sets[i][0], d_sets[i][1], d_sets[i][2]
+            u0m, u0c = d_sets[i][3:6], d_sets[i][6:9]
             um, uc = w_sets[i][:3], w_sets[i][3:]
             stream.wait_event(h2d_done[i])
             stream.wait_event(d2h_done[i])   # output set i has been read back
             with torch.cuda.stream(stream):
+                N.mg_base_state_map(geo, 0, (0.5, 0.5, 0.5), 0.0, 0.5 * hz, nr, br.data_ptr(), rr.data_ptr(),
+                                    m_sig.data_ptr(), m_b0.data_ptr(), [b.data_ptr() for b in m_b0f],
+                                    stream.cuda_stream)
+                sg, b0, bf = m_sig, m_b0, m_b0f
                 mac.update_coeff(sg)
                 nod.update_coeff(sg)
                 for a_, b_ in zip(um + uc, u0m + u0c):
@@ -820,8 +835,10 @@ def main():
                        "d2h_bytes_per_step": d2h, "ms_per_step": mse / Ke,
                        "note": "pinned host inputs copied and results read back every step on an upload and "
                                "a read-back stream, overlapping the solves of the neighbouring steps "
-                               "(double-buffered device inputs and outputs); each step also rebuilds both "
-                               "hierarchies' coefficients from the uploaded sigma"}
+                               "(double-buffered device inputs and outputs). The height-dependent base state "
+                               "travels as its radial beta0 and rho0 tables (every half cell) and is expanded "
+                               "to sigma and beta0 at cells and faces on the device (mg_base_state_map); each "
+                               "step then rebuilds both hierarchies' coefficients from that sigma"}
 
     # plain FP64 GPU multigrid on the same workload (graph path, like graph_path above)
     if not args.no_fp64:

@@ -121,9 +121,10 @@ typedef struct {
  *   stream        cudaStream_t (NULL: the legacy default stream)
  *   flags         MG_FLAG_* bits (0 by default)
  *   inner_cycles  mixed precision: FP32 V-cycles per FP64 refinement step
- *                 (0: automatic -- two, or one when the last step's rate per
- *                 V-cycle brings the residual below half the tolerance in one;
- *                 the graph path decides this on the device with the same rule) */
+ *                 (0: automatic -- three, or the fewest (one or two) that the
+ *                 last step's rate per V-cycle predicts to bring the residual
+ *                 below half the tolerance; the graph path decides this on the
+ *                 device with the same rule) */
 typedef struct {
     int prec;
     int nu1;

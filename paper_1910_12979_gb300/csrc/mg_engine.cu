@@ -695,16 +695,33 @@ void mixed_correction(mg_handle* h, double* phi, int cycles)
 
 bool adaptive_cycles(const mg_handle* h) { return h->prec == MG_PREC_MIXED && h->opt.inner_cycles == 0; }
 
-// Automatic inner cycles of mixed refinement: after a step, one V-cycle is
-// enough for the next step when the last step's rate per V-cycle, applied once
-// to the current relative residual, lands below half the tolerance; otherwise
-// two.  The first step runs two.  Host loop and graph use this same function.
-__host__ __device__ inline int next_two(bool first, bool last_two, double prev_rel, double rel, double tol)
+// Automatic inner cycles of mixed refinement.  The first step runs
+// kMaxInner V-cycles.  After a step of m V-cycles that took the relative
+// residual from prev_rel to rel, the rate per V-cycle is q^(1/m) with
+// q = rel / prev_rel, and the next step runs the fewest V-cycles k <= kMaxInner
+// that this rate predicts to reach half the tolerance:
+//   rel q^(k/m) <= tol / 2   <=>   rel^m q^k <= (tol / 2)^m,
+// tested in that second form, with products only, so that the host loop and
+// the graph (k_check) take the same decision bit for bit.  Each outer step
+// costs an FP64 residual about as long as an FP32 V-cycle, and an FP32 inner
+// solve that runs on loses its rate to FP32 rounding, so more than three
+// V-cycles per step do not pay (four per step needed one step more at 256^3).
+constexpr int kMaxInner = 3;
+
+__host__ __device__ inline int next_cycles(bool first, int last_m, double prev_rel, double rel, double tol)
 {
-    if (first || !(prev_rel > 0.0) || !(rel > 0.0)) return 1;
-    double rho = rel / prev_rel;
-    if (last_two) rho = sqrt(rho);
-    return rel * rho > 0.5 * tol ? 1 : 0;
+    if (first || last_m < 1 || !(prev_rel > 0.0) || !(rel > 0.0) || !(rel < prev_rel)) return kMaxInner;
+    const double q = rel / prev_rel, t = 0.5 * tol;
+    double lhs = 1.0, rhs = 1.0;
+    for (int i = 0; i < last_m; ++i) {
+        lhs *= rel;
+        rhs *= t;
+    }
+    for (int k = 1; k < kMaxInner; ++k) {
+        lhs *= q;
+        if (lhs <= rhs) return k;
+    }
+    return kMaxInner;
 }
 
 
@@ -741,12 +758,11 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st, bool c
     int stall = 0, it = 0;
     mg_status status = MG_OK;
     const bool adaptive = adaptive_cycles(h);
-    int two = next_two(true, true, 0.0, rel, tol), vcyc = 0;
+    int m = adaptive ? next_cycles(true, 0, 0.0, rel, tol) : inner_cycles(h), vcyc = 0;
     double prev = rel;
     while (rel > tol) {
         if (it >= h->opt.max_iters) { status = MG_ERR_NOT_CONVERGED; break; }
         if (mixed) {
-            const int m = adaptive ? (two ? 2 : 1) : inner_cycles(h);
             mixed_correction(h, phi, m);
             vcyc += m;
         } else {
@@ -763,7 +779,7 @@ mg_status solve_core(mg_handle* h, double* phi, double tol, mg_stats* st, bool c
         if (rel < 0.9 * best) { best = rel; stall = 0; }
         else if (++stall >= 4) { status = rel <= tol ? MG_OK : MG_ERR_NOT_CONVERGED; break; }
         if (rel < best) best = rel;
-        two = next_two(false, two != 0, prev, rel, tol);   // as k_check
+        if (adaptive) m = next_cycles(false, m, prev, rel, tol);   // as k_check
         prev = rel;
     }
     if (h->singular) gauge(h, phi);
@@ -796,8 +812,8 @@ __global__ void k_set_io(DevScalars* d, const double* rhs, double* phi, double t
     d->phi_io = phi;
     d->tol = tol;
     d->maxit = maxit;
-    d->two = 1;
-    d->n_two = 0;
+    d->ncyc = kMaxInner;
+    d->n_extra = 0;
 }
 
 // MAC projection: the constraint after the update equals the solver residual
@@ -860,29 +876,30 @@ __global__ void k_check(DevScalars* d, cudaGraphConditionalHandle c, int first)
         if (!stop && rel > d->tol && d->iters >= d->maxit) { st = MG_ERR_NOT_CONVERGED; stop = 1; }
         d->status = st;
         cont = (!stop && rel > d->tol) ? 1u : 0u;
-        const int two = next_two(first != 0, d->two != 0, d->prev_rel, rel, d->tol);
-        if (first) d->n_two = 0;
-        d->two = two;
+        const int m = next_cycles(first != 0, d->ncyc, d->prev_rel, rel, d->tol);
+        if (first) d->n_extra = 0;
+        d->ncyc = m;
         d->prev_rel = rel;
     }
     cudaGraphSetConditional(c, cont);
 }
 
-// the IF node of the second V-cycle of a refinement step
-__global__ void k_set_two(DevScalars* d, cudaGraphConditionalHandle c)
+// the IF node of V-cycle k + 1 (k >= 1) of a refinement step
+__global__ void k_set_cycle(DevScalars* d, cudaGraphConditionalHandle c, int k)
 {
     if (threadIdx.x != 0) return;
-    if (d->two) d->n_two += 1;
-    cudaGraphSetConditional(c, d->two ? 1u : 0u);
+    const bool run = d->ncyc > k;
+    if (run) d->n_extra += 1;
+    cudaGraphSetConditional(c, run ? 1u : 0u);
 }
 
 // One refinement iteration (mixed) or V-cycle (FP64) on phi, then the residual.
 mg_status capture_deps(cudaStream_t s, cudaGraph_t* g, std::vector<cudaGraphNode_t>& deps);
 
 // One refinement step inside the graph's WHILE body (h->stream is capturing).
-// With automatic inner cycles the second V-cycle sits in an IF node whose
-// condition k_set_two takes from the scalar block (set by k_check); its
-// launches are counted into if_launches.
+// With automatic inner cycles, V-cycles 2 .. kMaxInner of the step sit in IF
+// nodes whose conditions k_set_cycle takes from the scalar block (set by
+// k_check); the launches of one such V-cycle are counted into if_launches.
 mg_status iterate_once(mg_handle* h, double* phi, float* r32, cudaStream_t if_stream, long long& if_launches)
 {
     const bool nodal = h->loc == MG_LOC_NODAL;
@@ -892,32 +909,34 @@ mg_status iterate_once(mg_handle* h, double* phi, float* r32, cudaStream_t if_st
         float* e = h->lev[0].x32;
         if (nodal) vcycle_node<float>(h, e, h->lev[0].b32, true);
         else vcycle_cell<float>(h, e, h->lev[0].b32, true);
-        cudaGraph_t g;
-        std::vector<cudaGraphNode_t> deps;
-        mg_status rc = capture_deps(s, &g, deps);
-        if (rc != MG_OK) return rc;
-        cudaGraphConditionalHandle ifh;
-        MG_CK(cudaGraphConditionalHandleCreate(&ifh, g, 0, 0));
-        MGP_LAUNCH(k_set_two<<<1, 32, 0, s>>>(h->d, ifh));
-        rc = capture_deps(s, &g, deps);
-        if (rc != MG_OK) return rc;
-        cudaGraphNodeParams prm = {};
-        prm.type = cudaGraphNodeTypeConditional;
-        prm.conditional.handle = ifh;
-        prm.conditional.type = cudaGraphCondTypeIf;
-        prm.conditional.size = 1;
-        cudaGraphNode_t ifnode;
-        MG_CK(cudaGraphAddNode(&ifnode, g, deps.data(), nullptr, deps.size(), &prm));
-        MG_CK(cudaStreamUpdateCaptureDependencies(s, &ifnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-        cudaGraph_t ifg = prm.conditional.phGraph_out[0];
-        MG_CK(cudaStreamBeginCaptureToGraph(if_stream, ifg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-        const long long c0 = launch_count();
-        h->stream = if_stream;
-        if (nodal) vcycle_node<float>(h, e, h->lev[0].b32, false);
-        else vcycle_cell<float>(h, e, h->lev[0].b32, false);
-        h->stream = s;
-        if_launches = launch_count() - c0;
-        MG_CK(cudaStreamEndCapture(if_stream, &ifg));
+        for (int k = 1; k < kMaxInner; ++k) {
+            cudaGraph_t g;
+            std::vector<cudaGraphNode_t> deps;
+            mg_status rc = capture_deps(s, &g, deps);
+            if (rc != MG_OK) return rc;
+            cudaGraphConditionalHandle ifh;
+            MG_CK(cudaGraphConditionalHandleCreate(&ifh, g, 0, 0));
+            MGP_LAUNCH(k_set_cycle<<<1, 32, 0, s>>>(h->d, ifh, k));
+            rc = capture_deps(s, &g, deps);
+            if (rc != MG_OK) return rc;
+            cudaGraphNodeParams prm = {};
+            prm.type = cudaGraphNodeTypeConditional;
+            prm.conditional.handle = ifh;
+            prm.conditional.type = cudaGraphCondTypeIf;
+            prm.conditional.size = 1;
+            cudaGraphNode_t ifnode;
+            MG_CK(cudaGraphAddNode(&ifnode, g, deps.data(), nullptr, deps.size(), &prm));
+            MG_CK(cudaStreamUpdateCaptureDependencies(s, &ifnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+            cudaGraph_t ifg = prm.conditional.phGraph_out[0];
+            MG_CK(cudaStreamBeginCaptureToGraph(if_stream, ifg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            const long long c0 = launch_count();
+            h->stream = if_stream;
+            if (nodal) vcycle_node<float>(h, e, h->lev[0].b32, false);
+            else vcycle_cell<float>(h, e, h->lev[0].b32, false);
+            h->stream = s;
+            if_launches = launch_count() - c0;   // the same V-cycle in every IF node
+            MG_CK(cudaStreamEndCapture(if_stream, &ifg));
+        }
         vec_axpy_f32(phi, e, &h->d->fscale, h->lev[0].nvec, s);
         residual64(h, phi, r32);
         return MG_OK;
@@ -1079,7 +1098,7 @@ mg_status ensure_graph(mg_handle* h, int which)
 mg_status graph_result(mg_handle* h, long long fixed, long long body, long long ifb, mg_stats* st)
 {
     const DevScalars& r = *h->hs;
-    add_launches(fixed + body * r.iters + ifb * r.n_two);
+    add_launches(fixed + body * r.iters + ifb * r.n_extra);
     if (r.async_err) return fail(MG_ERR_CUDA, "an asynchronous shared-memory copy did not complete in time");
     if (r.info != 0) return fail(MG_ERR_UNSUPPORTED, "the coarsest-level operator is singular");
     if (st) {
@@ -1087,7 +1106,7 @@ mg_status graph_result(mg_handle* h, long long fixed, long long body, long long 
         st->rel_resid = r.rel;
         st->rhs_norm = sqrt(r.fnorm2);
         st->vcycles = h->prec == MG_PREC_MIXED
-                          ? (adaptive_cycles(h) ? r.iters + r.n_two : r.iters * inner_cycles(h))
+                          ? (adaptive_cycles(h) ? r.iters + r.n_extra : r.iters * inner_cycles(h))
                           : r.iters;
     }
     if (r.status != MG_OK) {

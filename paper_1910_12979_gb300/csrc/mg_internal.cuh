@@ -67,12 +67,11 @@ struct DevScalars {
     int info;                  // dense coarsest factorisation: 0 ok, k > 0 zero pivot
     int iters, stall, status;  // iteration count, stalled iterations, mg_status
     int maxit;
-    int adaptive;              // mixed, automatic inner cycles: one or two V-cycles per step
     const double* rhs_in;      // caller rhs of the current call (graph mode)
     double* phi_io;            // caller phi of the current call (graph mode)
     double prev_rel;           // relative residual before the last refinement step
-    int two;                   // the next refinement step runs a second V-cycle
-    int n_two;                 // refinement steps that ran a second V-cycle (launch accounting)
+    int ncyc;                  // V-cycles of the next refinement step (automatic inner cycles)
+    int n_extra;               // V-cycles run beyond the first of each refinement step (launch accounting)
     int async_err;             // set by a kernel whose bounded wait for an asynchronous copy gave up
 };
 

@@ -71,11 +71,12 @@ struct NodeRhsShared {
 // whose FP64 inputs are rounded to binary32 on the integer pipe as they are
 // loaded (f must then be null).  The partial sums are accumulated in FP64.
 template <typename C>
-__global__ void __launch_bounds__(kNTX * kNTY)
+__global__ void __launch_bounds__(kNTX * kNTY, 4)
 k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restrict__ b0, const double* __restrict__ S,
                  double* __restrict__ f, double* __restrict__ partials)
 {
     constexpr int TX = kNTX, TY = kNTY, NT = TX * TY, QN = (TX + 1) * (TY + 1);
+    static_assert(QN <= 2 * NT, "each thread stages at most two cells of a plane");
     __shared__ NodeRhsShared<C> sh;
     const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
     const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
@@ -94,31 +95,48 @@ k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restric
         g += z1 - z0;
         const int x0 = (tile % tx_n) * TX, y0 = (tile / tx_n) * TY;
 
-        // cell plane c: W into shared memory, then the shared pair sums
-        auto plane = [&](int c) {
+        // cell plane c: each thread loads the FP64 fields of the (up to two)
+        // staged cells it owns into registers -- a plane ahead of their use, so
+        // the loads are in flight during the previous plane's barriers and
+        // arithmetic -- then stage() forms W in shared memory and the shared
+        // pair sums.  Absent cells (outside a non-periodic boundary) load 0.
+        double rb[2], ru0[2], ru1[2], ru2[2], rs[2];
+        auto load = [&](int c) {
             int gz = c;
             bool zok = true;
             if (gz < 0 || gz >= nz) { if (pz) gz = gz < 0 ? gz + nz : gz - nz; else zok = false; }
-            for (int q = tid; q < QN; q += NT) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int q = tid + e * NT;
+                rb[e] = ru0[e] = ru1[e] = ru2[e] = rs[e] = 0.0;
+                if (q >= QN) continue;
                 const int qy = q / (TX + 1), qx = q - qy * (TX + 1);
                 int gx = x0 - 1 + qx, gy = y0 - 1 + qy;
                 bool ok = zok;
                 if (gx < 0 || gx >= nx) { if (px) gx = gx < 0 ? gx + nx : gx - nx; else ok = false; }
                 if (gy < 0 || gy >= ny) { if (py) gy = gy < 0 ? gy + ny : gy - ny; else ok = false; }
                 if (gx >= nx || gy >= ny) ok = false;
-                C w0 = C(0), w1 = C(0), w2 = C(0), ws = C(0);
                 if (ok) {
                     const size_t id = ((size_t)gz * ny + gy) * nx + gx;
-                    const C bb = from_f64<C>(b0[id]);
-                    w0 = bb * from_f64<C>(U.p[0][id]);
-                    w1 = bb * from_f64<C>(U.p[1][id]);
-                    w2 = bb * from_f64<C>(U.p[2][id]);
-                    ws = bb * from_f64<C>(S[id]);
+                    rb[e] = b0[id];
+                    ru0[e] = U.p[0][id];
+                    ru1[e] = U.p[1][id];
+                    ru2[e] = U.p[2][id];
+                    rs[e] = S[id];
                 }
-                sh.w[0][qy][qx] = w0;
-                sh.w[1][qy][qx] = w1;
-                sh.w[2][qy][qx] = w2;
-                sh.w[3][qy][qx] = ws;
+            }
+        };
+        auto stage = [&]() {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int q = tid + e * NT;
+                if (q >= QN) continue;
+                const int qy = q / (TX + 1), qx = q - qy * (TX + 1);
+                const C bb = from_f64<C>(rb[e]);
+                sh.w[0][qy][qx] = bb * from_f64<C>(ru0[e]);
+                sh.w[1][qy][qx] = bb * from_f64<C>(ru1[e]);
+                sh.w[2][qy][qx] = bb * from_f64<C>(ru2[e]);
+                sh.w[3][qy][qx] = bb * from_f64<C>(rs[e]);
             }
             __syncthreads();
             for (int q = tid; q < TY * (TX + 1); q += NT) {
@@ -140,12 +158,15 @@ k_node_rhs_tiled(NodeLevel<double> L, double h, CPtr3 U, const double* __restric
             bz = sh.xa[1][ly][lx] + sh.xa[1][ly + 1][lx];
             bs = sh.xa[2][ly][lx] + sh.xa[2][ly + 1][lx];
         };
-        plane(z0 - 1);
+        load(z0 - 1);
+        stage();
         terms(pdx, pdy, pz2, ps);
+        load(z0);
         const int i = x0 + lx, j = y0 + ly;
         const bool own = i < Nx && j < Ny;
         for (int k = z0; k < z1; ++k) {
-            plane(k);  // (its first barrier follows every read of the previous plane's W)
+            stage();   // plane k (its first barrier follows every read of the previous plane's W)
+            if (k + 1 < z1) load(k + 1);
             C dx, dy, bz, bs;
             terms(dx, dy, bz, bs);
             if (own) {
@@ -206,26 +227,43 @@ struct NodeProjShared {
     double ax[kNTY + 1][kNTX];      // phi(x) + phi(x+1)
 };
 
-__global__ void __launch_bounds__(kNTX * kNTY)
+__global__ void __launch_bounds__(kNTX * kNTY, 4)
 k_node_project_tiled(NodeLevel<double> L, double h, const double* __restrict__ phi, const double* __restrict__ b0,
                      MPtr3n U, int kz)
 {
-    constexpr int TX = kNTX, TY = kNTY, NT = TX * TY;
+    constexpr int TX = kNTX, TY = kNTY, NT = TX * TY, QN = (TX + 1) * (TY + 1);
+    static_assert(QN <= 2 * NT, "each thread stages at most two nodes of a plane");
     __shared__ NodeProjShared sh;
     const int Nx = L.Nx, Ny = L.Ny, Nz = L.Nz, nx = L.nx, ny = L.ny, nz = L.nz;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * kz, z1 = min(z0 + kz, nz);
     const int tid = threadIdx.y * TX + threadIdx.x, lx = threadIdx.x, ly = threadIdx.y;
     const double w4 = 1.0 / (4.0 * h);
-    // node plane p -> shared partial sums (nodes past the grid edge of a partial tile read as 0)
-    auto plane = [&](int p) {
+    // node plane p: phi of the (up to two) staged nodes a thread owns, loaded
+    // into registers a plane ahead of use (nodes past the grid edge of a
+    // partial tile read as 0); stage() forms the shared partial sums
+    double rx[2];
+    auto load = [&](int p) {
         const int pn = p >= Nz ? p - Nz : p;  // p == Nz only when z is periodic (node nz is node 0)
-        for (int q = tid; q < (TX + 1) * (TY + 1); q += NT) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int q = tid + e * NT;
+            rx[e] = 0.0;
+            if (q >= QN) continue;
             const int r = q / (TX + 1), c = q - r * (TX + 1);
             int gx = x0 + c, gy = y0 + r;
             if (gx >= Nx) gx = L.bc.lo[0] == BCP ? gx - Nx : -1;
             if (gy >= Ny) gy = L.bc.lo[1] == BCP ? gy - Ny : -1;
-            sh.xs[r][c] = (gx >= 0 && gy >= 0) ? phi[((size_t)pn * Ny + gy) * Nx + gx] : 0.0;
+            if (gx >= 0 && gy >= 0) rx[e] = phi[((size_t)pn * Ny + gy) * Nx + gx];
+        }
+    };
+    auto stage = [&]() {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int q = tid + e * NT;
+            if (q >= QN) continue;
+            const int r = q / (TX + 1), c = q - r * (TX + 1);
+            sh.xs[r][c] = rx[e];
         }
         __syncthreads();
         for (int q = tid; q < (TY + 1) * TX; q += NT) {
@@ -241,20 +279,37 @@ k_node_project_tiled(NodeLevel<double> L, double h, const double* __restrict__ p
         gyp = sh.ax[ly + 1][lx] - sh.ax[ly][lx];
         bp = sh.ax[ly][lx] + sh.ax[ly + 1][lx];
     };
-    plane(z0);
-    terms(gxl, gyl, bl);
     const int i = x0 + lx, j = y0 + ly;
     const bool own = i < nx && j < ny;
+    // the owned cell's sigma, beta0 and U, also loaded a plane ahead
+    double cs = 0.0, cb = 1.0, cu[3] = {0.0, 0.0, 0.0};
+    auto load_cell = [&](int k) {
+        if (!own) return;
+        const size_t t = ((size_t)k * ny + j) * nx + i;
+        cs = L.sigma[t];
+        cb = b0[t];
+        cu[0] = U.p[0][t];
+        cu[1] = U.p[1][t];
+        cu[2] = U.p[2][t];
+    };
+    load(z0);
+    stage();
+    terms(gxl, gyl, bl);
+    load(z0 + 1);
+    load_cell(z0);
     for (int k = z0; k < z1; ++k) {
-        plane(k + 1);  // (its first barrier follows every read of the previous plane's sums)
+        stage();  // node plane k + 1 (its first barrier follows every read of the previous plane's sums)
+        if (k + 2 <= z1) load(k + 2);
+        const double s0 = cs, b0k = cb, u0 = cu[0], u1 = cu[1], u2 = cu[2];
+        if (k + 1 < z1) load_cell(k + 1);
         double gxu, gyu, bu;
         terms(gxu, gyu, bu);
         if (own) {
             const size_t t = ((size_t)k * ny + j) * nx + i;
-            const double w = L.sigma[t] * recip_nr(b0[t]) * w4;
-            U.p[0][t] = fmadd(-w, gxl + gxu, U.p[0][t]);
-            U.p[1][t] = fmadd(-w, gyl + gyu, U.p[1][t]);
-            U.p[2][t] = fmadd(-w, bu - bl, U.p[2][t]);
+            const double w = s0 * recip_nr(b0k) * w4;
+            U.p[0][t] = fmadd(-w, gxl + gxu, u0);
+            U.p[1][t] = fmadd(-w, gyl + gyu, u1);
+            U.p[2][t] = fmadd(-w, bu - bl, u2);
         }
         gxl = gxu;
         gyl = gyu;

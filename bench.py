@@ -822,7 +822,7 @@ def main():
             torch.cuda.synchronize(dev)
 
         run(2)
-        Ke = max(2, min(args.steps, 6))
+        Ke = max(2, args.steps)
         if dist is not None:
             dist.barrier()
         run(Ke, timed=True)

@@ -71,29 +71,89 @@ __device__ __forceinline__ double radius(const MapArgs& A, double x, double y, d
     return sqrt(dx * dx + dy * dy + dz * dz);
 }
 
-__global__ void k_map_cells(MapArgs A, double* __restrict__ sigma, double* __restrict__ b0c)
+// One warp per kWarpRows x-rows of the target array (row = j + my * k),
+// kMapWarps warps per block.  The radius of a plane-parallel base state is the
+// height, constant along a row, so lane q interpolates the values of the
+// warp's row q once and the warp broadcasts them by shuffles (the
+// interpolation and the divisions are latency-bound FP64 work, done for the
+// warp's rows in parallel; the coalesced stores are the per-cell cost); a
+// spherical base state is interpolated cell by cell.
+constexpr int kMapWarps = 8, kWarpRows = 4;
+
+__global__ void __launch_bounds__(32 * kMapWarps) k_map_cells(MapArgs A, long long rows, double* __restrict__ sigma,
+                                                              double* __restrict__ b0c)
 {
-    const int total = A.nx * A.ny * A.nz;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    int i, j, k;
-    unflat(t, A.nx, A.ny, i, j, k);
-    const double r = radius(A, (i + 0.5) * A.hx, (j + 0.5) * A.hy, (k + 0.5) * A.hz);
-    const double b = interp(A.beta0_r, A.nr, A.r0, A.dr, r);
-    if (sigma) sigma[t] = b / interp(A.rho0_r, A.nr, A.r0, A.dr, r);
-    if (b0c) b0c[t] = b;
+    const long long row0 = ((long long)blockIdx.x * kMapWarps + threadIdx.y) * kWarpRows;
+    if (row0 >= rows) return;   // whole warp
+    const int lane = threadIdx.x;
+    auto values = [&](double r, double& b, double& sg) {
+        b = interp(A.beta0_r, A.nr, A.r0, A.dr, r);
+        sg = b / interp(A.rho0_r, A.nr, A.r0, A.dr, r);
+    };
+    double bq = 0.0, sq = 0.0;   // lane q < kWarpRows: the values of row row0 + q
+    if (!A.spherical && lane < kWarpRows && row0 + lane < rows) {
+        const long long row = row0 + lane;
+        const int j = (int)(row % A.ny), k = (int)(row / A.ny);
+        values(radius(A, 0.0, (j + 0.5) * A.hy, (k + 0.5) * A.hz), bq, sq);
+    }
+#pragma unroll
+    for (int q = 0; q < kWarpRows; ++q) {
+        const long long row = row0 + q;
+        const double b = __shfl_sync(0xffffffffu, bq, q), sg = __shfl_sync(0xffffffffu, sq, q);
+        if (row >= rows) break;   // warp-uniform
+        const size_t base = (size_t)row * A.nx;
+        if (!A.spherical) {
+            for (int i = lane; i < A.nx; i += 32) {
+                if (sigma) sigma[base + i] = sg;
+                if (b0c) b0c[base + i] = b;
+            }
+            continue;
+        }
+        const int j = (int)(row % A.ny), k = (int)(row / A.ny);
+        for (int i = lane; i < A.nx; i += 32) {
+            double bc, sc;
+            values(radius(A, (i + 0.5) * A.hx, (j + 0.5) * A.hy, (k + 0.5) * A.hz), bc, sc);
+            if (sigma) sigma[base + i] = sc;
+            if (b0c) b0c[base + i] = bc;
+        }
+    }
 }
 
-__global__ void k_map_faces(MapArgs A, int d, double* __restrict__ out)
+__global__ void __launch_bounds__(32 * kMapWarps) k_map_faces(MapArgs A, int d, long long rows,
+                                                              double* __restrict__ out)
 {
-    const int mx = A.nx + (d == 0), my = A.ny + (d == 1), mz = A.nz + (d == 2);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= mx * my * mz) return;
-    int i, j, k;
-    unflat(t, mx, my, i, j, k);
-    const double x = (i + (d == 0 ? 0.0 : 0.5)) * A.hx, y = (j + (d == 1 ? 0.0 : 0.5)) * A.hy,
-                 z = (k + (d == 2 ? 0.0 : 0.5)) * A.hz;
-    out[t] = interp(A.beta0_r, A.nr, A.r0, A.dr, radius(A, x, y, z));
+    const long long row0 = ((long long)blockIdx.x * kMapWarps + threadIdx.y) * kWarpRows;
+    if (row0 >= rows) return;   // whole warp
+    const int mx = A.nx + (d == 0), my = A.ny + (d == 1);
+    const int lane = threadIdx.x;
+    auto yz = [&](long long row, double& y, double& z) {
+        const int j = (int)(row % my), k = (int)(row / my);
+        y = (j + (d == 1 ? 0.0 : 0.5)) * A.hy;
+        z = (k + (d == 2 ? 0.0 : 0.5)) * A.hz;
+    };
+    double bq = 0.0;
+    if (!A.spherical && lane < kWarpRows && row0 + lane < rows) {
+        double y, z;
+        yz(row0 + lane, y, z);
+        bq = interp(A.beta0_r, A.nr, A.r0, A.dr, radius(A, 0.0, y, z));
+    }
+#pragma unroll
+    for (int q = 0; q < kWarpRows; ++q) {
+        const long long row = row0 + q;
+        const double b = __shfl_sync(0xffffffffu, bq, q);
+        if (row >= rows) break;   // warp-uniform
+        const size_t base = (size_t)row * mx;
+        if (!A.spherical) {
+            for (int i = lane; i < mx; i += 32) out[base + i] = b;
+            continue;
+        }
+        double y, z;
+        yz(row, y, z);
+        for (int i = lane; i < mx; i += 32) {
+            const double x = (i + (d == 0 ? 0.0 : 0.5)) * A.hx;
+            out[base + i] = interp(A.beta0_r, A.nr, A.r0, A.dr, radius(A, x, y, z));
+        }
+    }
 }
 
 }  // namespace
@@ -142,13 +202,21 @@ extern "C" mg_status mg_base_state_map(const mg_geometry* g, int spherical, cons
     A.beta0_r = beta0_r;
     A.rho0_r = rho0_r;
     cudaStream_t s = (cudaStream_t)stream;
-    const long long cells = (long long)A.nx * A.ny * A.nz;
-    if (sigma || beta0_cell)
-        MGP_LAUNCH(k_map_cells<<<ceil_div(cells, kThreads), kThreads, 0, s>>>(A, sigma, beta0_cell));
+    const dim3 block(32, kMapWarps);
+    constexpr long long per = (long long)kMapWarps * kWarpRows;
+    auto blocks = [](long long rows) { return (unsigned)((rows + per - 1) / per); };
+    if ((long long)(A.ny + 1) * (A.nz + 1) > 0x7fffffffLL * per) {
+        set_last_error("mg_base_state_map: too many grid rows");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (sigma || beta0_cell) {
+        const long long rows = (long long)A.ny * A.nz;
+        MGP_LAUNCH(k_map_cells<<<blocks(rows), block, 0, s>>>(A, rows, sigma, beta0_cell));
+    }
     for (int d = 0; d < g->dim; ++d) {
         if (!beta0_face || !beta0_face[d]) continue;
-        const long long m = (long long)(A.nx + (d == 0)) * (A.ny + (d == 1)) * (A.nz + (d == 2));
-        MGP_LAUNCH(k_map_faces<<<ceil_div(m, kThreads), kThreads, 0, s>>>(A, d, beta0_face[d]));
+        const long long rows = (long long)(A.ny + (d == 1)) * (A.nz + (d == 2));
+        MGP_LAUNCH(k_map_faces<<<blocks(rows), block, 0, s>>>(A, d, rows, beta0_face[d]));
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); return MG_ERR_CUDA; }

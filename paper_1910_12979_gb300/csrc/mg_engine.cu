@@ -704,8 +704,9 @@ bool adaptive_cycles(const mg_handle* h) { return h->prec == MG_PREC_MIXED && h-
 // tested in that second form, with products only, so that the host loop and
 // the graph (k_check) take the same decision bit for bit.  Each outer step
 // costs an FP64 residual about as long as an FP32 V-cycle, and an FP32 inner
-// solve that runs on loses its rate to FP32 rounding, so more than three
-// V-cycles per step do not pay (four per step needed one step more at 256^3).
+// solve that runs on loses rate late in a step, so more than three V-cycles
+// per step do not pay (at 256^3 a fixed four per step took 16 MAC and 12 nodal
+// V-cycles, a fixed three 15 and 9, this rule 13 and 8).
 constexpr int kMaxInner = 3;
 
 __host__ __device__ inline int next_cycles(bool first, int last_m, double prev_rel, double rel, double tol)

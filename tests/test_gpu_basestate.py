@@ -61,3 +61,31 @@ def test_map_matches_oracle(oracle, spherical):
     np.testing.assert_allclose(bc.cpu().numpy(), ref[1], rtol=1e-14)
     for d in range(3):
         np.testing.assert_allclose(bf[d].cpu().numpy(), ref[2][d], rtol=1e-14)
+
+
+@pytest.mark.parametrize("spherical", [True, False])
+def test_map_2d_matches_oracle(oracle, spherical):
+    # 2-D: the plane-parallel radius is y; rows of 40 cells (41 x-faces) leave lanes idle and the
+    # 25 y-face rows end in a partial group of rows
+    O = oracle
+    n = (40, 24)
+    g = O.Grid.make(n, ("periodic", "neumann"), ("periodic", "dirichlet"))
+    nr = 700
+    dr = 1.2 / (nr - 1)
+    rt = dr * np.arange(nr)
+    rho_r = np.exp(-4.0 * rt) * (1.0 + 0.05 * np.cos(9.0 * rt))
+    beta_r = rho_r ** 0.6
+    center = (0.4, 0.55)
+    ref = O.map_radial(g, spherical, center, 0.0, dr, beta_r, rho_r)
+    geo = N.mg_geometry(2, n, tuple(1.0 / v for v in n), N.MG_LOC_CELL)
+    sig = torch.zeros(g.cell_shape, dtype=torch.float64, device=DEV)
+    bc = torch.zeros_like(sig)
+    bf = [torch.zeros(g.face_shape(d), dtype=torch.float64, device=DEV) for d in range(2)]
+    br, rr = T(beta_r), T(rho_r)
+    N.mg_base_state_map(geo, spherical, center + (0.0,), 0.0, dr, nr, br.data_ptr(), rr.data_ptr(), sig.data_ptr(),
+                        bc.data_ptr(), [b.data_ptr() for b in bf] + [None])
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(sig.cpu().numpy(), ref[0], rtol=1e-14)
+    np.testing.assert_allclose(bc.cpu().numpy(), ref[1], rtol=1e-14)
+    for d in range(2):
+        np.testing.assert_allclose(bf[d].cpu().numpy(), ref[2][d], rtol=1e-14)

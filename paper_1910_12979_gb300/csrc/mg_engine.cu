@@ -152,6 +152,11 @@ struct mg_handle {
     // graph-resident solve loops: [0] rhs taken from the caller, [1] rhs already in f64
     cudaGraphExec_t gx[2];
     long long g_fixed[2], g_body[2], g_if[2];  // kernel launches outside the loop / per iteration / per IF
+    // host-driven loop: the V-cycle below the finest level, captured once per
+    // arithmetic type ([0] FP32, [1] FP64) and replayed as one graph launch
+    cudaGraphExec_t cg[2];
+    long long cg_launches[2];
+    bool cg_failed[2];
 };
 
 void mgp::handle_info(const mg_handle* h, mg_geometry* g, mg_bc* bc, cudaStream_t* s)
@@ -553,22 +558,28 @@ void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, i
         }
 }
 
-// One V-cycle on L x0 = b0 (level 0 arrays given), cell-centred.
+// First level of the one-launch coarse end of a cell V-cycle: levels lc .. L-1
+// (at most kCoarseCells cells each) run as one launch; L when nothing is fused.
+int cell_coarse_start(const mg_handle* h)
+{
+    const int L = h->nlev;
+    if (h->opt.flags & MG_FLAG_NO_FUSED) return L;
+    int lc = L - 1;
+    while (lc > 0 && h->lev[lc - 1].ncell <= (size_t)kCoarseCells && L - (lc - 1) <= kCoarseMaxLevels) --lc;
+    return lc == L - 1 ? L : lc;   // a single level: nothing to fuse
+}
+
+// Levels first .. L-1 of a cell V-cycle on L x = b: the down legs of levels
+// first .. lc-1, the coarse end, and the up legs back to level first.  Level 0
+// uses x0 and b0; the other levels their stored arrays.
 template <typename T>
-void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
+void vcycle_cell_range(mg_handle* h, int first, T* x0, const T* b0, bool zero_init)
 {
     cudaStream_t s = h->stream;
-    const int dim = h->dim, L = h->nlev;
+    const int dim = h->dim, L = h->nlev, lc = cell_coarse_start(h);
     auto X = [&](int l) { return l == 0 ? x0 : lx<T>(h, l); };
     auto Bv = [&](int l) { return l == 0 ? b0 : (const T*)lb<T>(h, l); };
-    // levels lc .. L-1 (at most kCoarseCells cells each) run as one launch
-    int lc = L;
-    if (!(h->opt.flags & MG_FLAG_NO_FUSED)) {
-        lc = L - 1;
-        while (lc > 0 && h->lev[lc - 1].ncell <= (size_t)kCoarseCells && L - (lc - 1) <= kCoarseMaxLevels) --lc;
-        if (lc == L - 1) lc = L;   // a single level: nothing to fuse
-    }
-    for (int l = 0; l < lc && l < L - 1; ++l) {
+    for (int l = first; l < lc && l < L - 1; ++l) {
         if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
         const CellLevel<T> V = cview<T>(h, l);
         cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu1);
@@ -599,11 +610,95 @@ void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
     } else {
         dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
     }
-    for (int l = (lc < L ? lc : L - 1) - 1; l >= 0; --l) {
+    for (int l = (lc < L ? lc : L - 1) - 1; l >= first; --l) {
         const CellLevel<T> V = cview<T>(h, l);
         cell_prolong_add<T>(dim, V, cview<T>(h, l + 1), X(l), X(l + 1), h->opt.interp_order, s);
         cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu2);
     }
+}
+
+template <typename T>
+void vcycle_node_range(mg_handle* h, int first, T* x0, const T* b0, bool zero_init);
+int node_coarse_start(const mg_handle* h);
+
+// The levels below the finest of a V-cycle (levels 1 .. L-1, which read the
+// restricted residual in level 1's b and leave level 1's x for the
+// prolongation) touch only arrays of the hierarchy, so in the host-driven loop
+// they are captured once into a graph and replayed as one launch per V-cycle
+// instead of some 30-40 stream launches of mostly small kernels.  Null when
+// the hierarchy is too shallow for this to pay, while h->stream is itself
+// being captured (a graph-resident solve records the levels inline), or if the
+// capture failed (the caller then launches the levels one by one).
+template <typename T>
+cudaGraphExec_t coarse_graph(mg_handle* h)
+{
+    const bool nodal = h->loc == MG_LOC_NODAL;
+    if ((nodal ? node_coarse_start(h) : cell_coarse_start(h)) < 2 || h->nlev < 3) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    const int i = std::is_same<T, float>::value ? 0 : 1;
+    if (h->cg[i] || h->cg_failed[i]) return h->cg[i];
+    h->cg_failed[i] = true;
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    const cudaStream_t saved = h->stream;
+    const long long c0 = launch_count();
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        h->stream = cap;
+        if (nodal) vcycle_node_range<T>(h, 1, nullptr, nullptr, false);
+        else vcycle_cell_range<T>(h, 1, nullptr, nullptr, false);
+        h->stream = saved;
+        ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && g;
+    }
+    const long long n = launch_count() - c0;
+    add_launches(-n);   // capture enqueues nothing; replays are counted
+    cudaGraphExec_t ex = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (!ok) {
+        cudaGetLastError();   // clear a capture error: the levels run as plain launches
+        return nullptr;
+    }
+    h->cg[i] = ex;
+    h->cg_launches[i] = n;
+    h->cg_failed[i] = false;
+    return ex;
+}
+
+// One V-cycle on L x0 = b0 (level 0 arrays given), cell-centred.
+template <typename T>
+void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
+{
+    cudaGraphExec_t cg = coarse_graph<T>(h);
+    if (!cg) {
+        vcycle_cell_range<T>(h, 0, x0, b0, zero_init);
+        return;
+    }
+    cudaStream_t s = h->stream;
+    const int dim = h->dim;
+    // level 0 down leg, as in vcycle_cell_range
+    if (zero_init) zero(x0, h->lev[0].nvec, s);
+    const CellLevel<T> V = cview<T>(h, 0);
+    cell_smooth<T>(h, 0, V, x0, b0, h->opt.nu1);
+    const int pr = prof_begin(MG_PROF_CELL_RESTRICT_FINE, (3.0 + 1.0 / (1 << dim)) * sizeof(T) * h->lev[0].ncell, s);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (!(h->opt.flags & (MG_FLAG_NO_FUSED | MG_FLAG_SWEEP_PIPE)) &&
+            cell_resid_restrict_v4_ok(dim, V, x0, b0, lb<T>(h, 1))) {
+            cell_resid_restrict_v4(V, x0, b0, lb<T>(h, 1), s);
+            done = true;
+        }
+    }
+    if (!done) cell_resid_restrict<T>(dim, V, x0, b0, lb<T>(h, 1), s);
+    prof_end(pr, s);
+    cudaGraphLaunch(cg, s);
+    add_launches(h->cg_launches[std::is_same<T, float>::value ? 0 : 1]);
+    // level 0 up leg
+    cell_prolong_add<T>(dim, V, cview<T>(h, 1), x0, lx<T>(h, 1), h->opt.interp_order, s);
+    cell_smooth<T>(h, 0, V, x0, b0, h->opt.nu2);
 }
 
 template <typename T>
@@ -623,21 +718,26 @@ void node_smooth(mg_handle* h, int l, T* x, const T* b, int sweeps)
     if (sweeps % 2 == 1) cudaMemcpyAsync(x, t, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
 }
 
+// First level of the one-launch coarse end of a nodal V-cycle (levels of at
+// most kCoarseNodes stored nodes); L when nothing is fused.
+int node_coarse_start(const mg_handle* h)
+{
+    const int L = h->nlev;
+    if (h->opt.flags & MG_FLAG_NO_FUSED) return L;
+    int lc = L - 1;
+    while (lc > 0 && h->lev[lc - 1].nvec <= (size_t)kCoarseNodes && L - (lc - 1) <= kCoarseMaxLevels) --lc;
+    return lc == L - 1 ? L : lc;   // a single level: nothing to fuse
+}
+
+// Levels first .. L-1 of a nodal V-cycle (as vcycle_cell_range).
 template <typename T>
-void vcycle_node(mg_handle* h, T* x0, const T* b0, bool zero_init)
+void vcycle_node_range(mg_handle* h, int first, T* x0, const T* b0, bool zero_init)
 {
     cudaStream_t s = h->stream;
-    const int dim = h->dim, L = h->nlev;
+    const int dim = h->dim, L = h->nlev, lc = node_coarse_start(h);
     auto X = [&](int l) { return l == 0 ? x0 : lx<T>(h, l); };
     auto Bv = [&](int l) { return l == 0 ? b0 : (const T*)lb<T>(h, l); };
-    // levels lc .. L-1 (at most kCoarseNodes stored nodes each) run as one launch
-    int lc = L;
-    if (!(h->opt.flags & MG_FLAG_NO_FUSED)) {
-        lc = L - 1;
-        while (lc > 0 && h->lev[lc - 1].nvec <= (size_t)kCoarseNodes && L - (lc - 1) <= kCoarseMaxLevels) --lc;
-        if (lc == L - 1) lc = L;   // a single level: nothing to fuse
-    }
-    for (int l = 0; l < lc && l < L - 1; ++l) {
+    for (int l = first; l < lc && l < L - 1; ++l) {
         if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
         node_smooth<T>(h, l, X(l), Bv(l), h->opt.nu1);
         node_resid<T>(dim, nview<T>(h, l), X(l), Bv(l), lr<T>(h, l), !(h->opt.flags & MG_FLAG_NO_FUSED), s,
@@ -659,10 +759,30 @@ void vcycle_node(mg_handle* h, T* x0, const T* b0, bool zero_init)
     } else {
         dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
     }
-    for (int l = (lc < L ? lc : L - 1) - 1; l >= 0; --l) {
+    for (int l = (lc < L ? lc : L - 1) - 1; l >= first; --l) {
         node_prolong_add<T>(dim, nview<T>(h, l), nview<T>(h, l + 1), X(l), X(l + 1), s);
         node_smooth<T>(h, l, X(l), Bv(l), h->opt.nu2);
     }
+}
+
+template <typename T>
+void vcycle_node(mg_handle* h, T* x0, const T* b0, bool zero_init)
+{
+    cudaGraphExec_t cg = coarse_graph<T>(h);
+    if (!cg) {
+        vcycle_node_range<T>(h, 0, x0, b0, zero_init);
+        return;
+    }
+    cudaStream_t s = h->stream;
+    const int dim = h->dim;
+    if (zero_init) zero(x0, h->lev[0].nvec, s);
+    node_smooth<T>(h, 0, x0, b0, h->opt.nu1);
+    node_resid<T>(dim, nview<T>(h, 0), x0, b0, lr<T>(h, 0), !(h->opt.flags & MG_FLAG_NO_FUSED), s, h->lev[0].kind);
+    node_restrict<T>(dim, nview<T>(h, 0), nview<T>(h, 1), lr<T>(h, 0), lb<T>(h, 1), s);
+    cudaGraphLaunch(cg, s);
+    add_launches(h->cg_launches[std::is_same<T, float>::value ? 0 : 1]);
+    node_prolong_add<T>(dim, nview<T>(h, 0), nview<T>(h, 1), x0, lx<T>(h, 1), s);
+    node_smooth<T>(h, 0, x0, b0, h->opt.nu2);
 }
 
 // Remove the mean of phi (singular problems).
@@ -1571,8 +1691,10 @@ void mg_destroy(mg_handle* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     drop_batches_of(h);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (h->gx[i]) cudaGraphExecDestroy(h->gx[i]);
+        if (h->cg[i]) cudaGraphExecDestroy(h->cg[i]);
+    }
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->hs) cudaFreeHost(h->hs);
     delete h;

@@ -273,19 +273,22 @@ const char* mg_strerror(mg_status s);
 const char* mg_last_error(void);
 
 /* Live per-kernel timing (diagnostics, used by the benchmark's roofline).
- * mg_prof_enable(1) clears the record and starts bracketing every launch of
- * the kernels below with a pair of CUDA events on the launching stream (solves
- * then use the host-driven loop: a graph replay cannot be bracketed per
- * launch); mg_prof_enable(0) stops.  mg_prof_query (call after the stream has
- * been synchronised) returns, for one kernel class, the summed event time, the
- * launch count and the summed ALGORITHMIC bytes and FP64 flops of those
- * launches (what the method must move and compute, see each class).  Returns
- * MG_ERR_INVALID_ARG for an unknown class.  Recording stops silently after
- * 65536 launches. */
+ * mg_prof_enable(1) clears the record and starts bracketing the launches of
+ * the kernels below with pairs of CUDA events on the launching stream: one
+ * pair per launch, or per run of consecutive launches of one class (the colour
+ * passes or sweeps of one smoothing step), which then counts as that many
+ * launches (solves use the host-driven loop meanwhile: a graph replay cannot
+ * be bracketed per launch); mg_prof_enable(0) stops.  mg_prof_query (call
+ * after the stream has been synchronised) returns, for one kernel class, the
+ * summed event time, the launch count and the summed ALGORITHMIC bytes and
+ * FP64 flops of those launches (what the method must move and compute, see
+ * each class).  Returns MG_ERR_INVALID_ARG for an unknown class.  Recording
+ * stops silently after 65536 brackets. */
 typedef enum {
-    MG_PROF_CELL_SMOOTH_FINE = 0, /* one fused red-black sweep on the finest cell level
-                                     (phi, f, sigma read, phi written: 4 words/cell), or one
-                                     colour pass where the level does not tile (2 words/cell) */
+    MG_PROF_CELL_SMOOTH_FINE = 0, /* on the finest cell level, one colour pass of the
+                                     vectorised or plain smoother (half a sweep: 2 words/cell),
+                                     or one red-black sweep of the pipelined or TMA-staged
+                                     smoother (phi, f, sigma read, phi written: 4 words/cell) */
     MG_PROF_RESID64 = 1,          /* FP64 fine residual of a cell system (+ FP32 copy in mixed
                                      mode): phi, f, sigma in FP64 (+ r in FP32) per cell;
                                      15 FP64 flops per cell (6 face FMAs, the diagonal FMA,

@@ -62,7 +62,7 @@ struct Bump {
 
 // ---- live per-kernel event timing (mg_prof_*)
 struct ProfRec {
-    int id;
+    int id, count;   // kernel class; launches inside the bracket
     double bytes, flops;
     cudaEvent_t a, b;
 };
@@ -79,8 +79,10 @@ Prof& prof()
 }
 constexpr size_t kProfMax = 65536;
 
-// Returns a record index (or -1) after recording the start event on s.
-int prof_begin(int id, double bytes, cudaStream_t s, double flops = 0.0)
+// Returns a record index (or -1) after recording the start event on s.  The
+// bracket holds count consecutive launches of the class; bytes and flops are
+// their totals.
+int prof_begin(int id, double bytes, cudaStream_t s, double flops = 0.0, int count = 1)
 {
     Prof& P = prof();
     if (!P.on) return -1;
@@ -93,6 +95,7 @@ int prof_begin(int id, double bytes, cudaStream_t s, double flops = 0.0)
     }
     ProfRec& r = P.recs[P.used];
     r.id = id;
+    r.count = count;
     r.bytes = bytes;
     r.flops = flops;
     cudaEventRecord(r.a, s);
@@ -514,48 +517,52 @@ void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, i
             cell_gsrb_tma_fits(V.nx)) {
             T* src = x;
             T* dst = t;
+            const int pr =
+                l == 0 && nu > 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 4.0 * sizeof(T) * cells * nu, s, 0.0, nu) : -1;
             for (int k = 0; k < nu; ++k) {
-                const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 4.0 * sizeof(T) * cells, s) : -1;
                 cell_gsrb_tma(V, src, dst, b, &h->d->async_err, s);
-                prof_end(pr, s);
                 T* tmp = src;
                 src = dst;
                 dst = tmp;
             }
+            prof_end(pr, s);
             if (src != x) cudaMemcpyAsync(x, src, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
             return;
         }
         const bool pipe = kind == 4 || (kind == 0 && (h->opt.flags & MG_FLAG_SWEEP_PIPE));
         if (!(h->opt.flags & MG_FLAG_NO_FUSED) && !pipe && cell_gsrb_v4_ok(h->dim, V, x, b)) {
+            const int pr =
+                l == 0 && nu > 0
+                    ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * cells * 2 * nu, s, 0.0, 2 * nu)
+                    : -1;
             for (int k = 0; k < nu; ++k)
-                for (int color = 0; color < 2; ++color) {
-                    const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * cells, s) : -1;
+                for (int color = 0; color < 2; ++color)
                     cell_gsrb_v4(h->dim, V, x, b, color, s, kind >= 1 && kind <= 3 ? 4 << kind : 0);
-                    prof_end(pr, s);
-                }
+            prof_end(pr, s);
             return;
         }
     }
     if (!(h->opt.flags & MG_FLAG_NO_FUSED) && cell_gsrb_fused_ok<T>(h->dim, V) && a16(x) && a16(t) && a16(b)) {
         T* src = x;
         T* dst = t;
+        const int pr =
+            l == 0 && nu > 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 4.0 * sizeof(T) * cells * nu, s, 0.0, nu) : -1;
         for (int k = 0; k < nu; ++k) {
-            const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 4.0 * sizeof(T) * cells, s) : -1;
             cell_gsrb_sweep<T>(h->dim, V, src, dst, b, s);
-            prof_end(pr, s);
             T* tmp = src;
             src = dst;
             dst = tmp;
         }
+        prof_end(pr, s);
         if (src != x) cudaMemcpyAsync(x, src, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
         return;
     }
+    const int pr =
+        l == 0 && nu > 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * cells * 2 * nu, s, 0.0, 2 * nu)
+                         : -1;
     for (int k = 0; k < nu; ++k)
-        for (int color = 0; color < 2; ++color) {
-            const int pr = l == 0 ? prof_begin(MG_PROF_CELL_SMOOTH_FINE, 2.0 * sizeof(T) * cells, s) : -1;
-            cell_gsrb<T>(h->dim, V, x, b, color, s);
-            prof_end(pr, s);
-        }
+        for (int color = 0; color < 2; ++color) cell_gsrb<T>(h->dim, V, x, b, color, s);
+    prof_end(pr, s);
 }
 
 // First level of the one-launch coarse end of a cell V-cycle: levels lc .. L-1
@@ -708,13 +715,15 @@ void node_smooth(mg_handle* h, int l, T* x, const T* b, int sweeps)
     const NodeLevel<T> V = nview<T>(h, l);
     T* t = lt<T>(h, l);
     const T om = (T)h->opt.omega;
+    const int pr = l == 0 && sweeps > 0
+                       ? prof_begin(MG_PROF_NODE_SMOOTH_FINE, 4.0 * sizeof(T) * h->lev[0].nvec * sweeps, s, 0.0, sweeps)
+                       : -1;
     for (int k = 0; k < sweeps; ++k) {
-        const int pr = l == 0 ? prof_begin(MG_PROF_NODE_SMOOTH_FINE, 4.0 * sizeof(T) * h->lev[0].nvec, s) : -1;
         const bool tiled = !(h->opt.flags & MG_FLAG_NO_FUSED);
         if (k % 2 == 0) node_jacobi<T>(h->dim, V, x, t, b, om, tiled, s, h->lev[l].kind);
         else node_jacobi<T>(h->dim, V, t, x, b, om, tiled, s, h->lev[l].kind);
-        prof_end(pr, s);
     }
+    prof_end(pr, s);
     if (sweeps % 2 == 1) cudaMemcpyAsync(x, t, h->lev[l].nvec * sizeof(T), cudaMemcpyDeviceToDevice, s);
 }
 
@@ -1020,11 +1029,13 @@ mg_status capture_deps(cudaStream_t s, cudaGraph_t* g, std::vector<cudaGraphNode
 // One refinement step inside the graph's WHILE body (h->stream is capturing).
 // With automatic inner cycles, V-cycles 2 .. kMaxInner of the step sit in IF
 // nodes whose conditions k_set_cycle takes from the scalar block (set by
-// k_check); the launches of one such V-cycle are counted into if_launches.
-mg_status iterate_once(mg_handle* h, double* phi, float* r32, cudaStream_t if_stream, long long& if_launches)
+// k_check); the launches of one such V-cycle are counted into if_launches,
+// those of all of them into if_total.
+mg_status iterate_once(mg_handle* h, double* phi, float* r32, cudaStream_t if_stream, long long& if_launches,
+                       long long& if_total)
 {
     const bool nodal = h->loc == MG_LOC_NODAL;
-    if_launches = 0;
+    if_launches = if_total = 0;
     if (h->prec == MG_PREC_MIXED && adaptive_cycles(h)) {
         cudaStream_t s = h->stream;
         float* e = h->lev[0].x32;
@@ -1056,6 +1067,7 @@ mg_status iterate_once(mg_handle* h, double* phi, float* r32, cudaStream_t if_st
             else vcycle_cell<float>(h, e, h->lev[0].b32, false);
             h->stream = s;
             if_launches = launch_count() - c0;   // the same V-cycle in every IF node
+            if_total += if_launches;
             MG_CK(cudaStreamEndCapture(if_stream, &ifg));
         }
         vec_axpy_f32(phi, e, &h->d->fscale, h->lev[0].nvec, s);
@@ -1128,7 +1140,8 @@ mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream
     cudaGraph_t bodyg = prm.conditional.phGraph_out[0];
     MG_CK(cudaStreamBeginCaptureToGraph(body_stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     h->stream = body_stream;
-    rc = iterate_once(h, phi, r32, if_stream, if_body);
+    long long if_total = 0;
+    rc = iterate_once(h, phi, r32, if_stream, if_body, if_total);
     if (rc != MG_OK) { h->stream = s; cudaStreamEndCapture(body_stream, &bodyg); return rc; }
     MGP_LAUNCH(k_check<<<1, 32, 0, body_stream>>>(h->d, cond, 0));
     h->stream = s;
@@ -1140,7 +1153,7 @@ mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream
     MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     const long long c3 = launch_count();
     fixed = (c1 - c0) + (c3 - c2);
-    body = (c2 - c1) - if_body;
+    body = (c2 - c1) - if_total;
     MG_CK(cudaGetLastError());
     return MG_OK;
 }
@@ -1172,6 +1185,7 @@ mg_status build_graph(mg_handle* const* hs, int count, bool rhs_from_io, cudaGra
     fixed.assign(count, 0);
     body.assign(count, 0);
     ifb.assign(count, 0);
+    const long long cap0 = launch_count();
     MG_CK(cudaStreamBeginCapture(cs.main, cudaStreamCaptureModeRelaxed));
     std::vector<cudaGraphNode_t> join;
     for (int i = 0; i < count && rc == MG_OK; ++i) {
@@ -1190,9 +1204,7 @@ mg_status build_graph(mg_handle* const* hs, int count, bool rhs_from_io, cudaGra
         cudaStreamUpdateCaptureDependencies(cs.main, join.data(), nullptr, join.size(), cudaStreamSetCaptureDependencies);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs.main, &graph);
-    long long captured = 0;
-    for (int i = 0; i < count; ++i) captured += fixed[i] + body[i] + ifb[i];
-    add_launches(-captured);  // capture enqueues nothing; replays are counted after each run
+    add_launches(-(launch_count() - cap0));  // capture enqueues nothing; replays are counted after each run
     if (rc != MG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(exec, graph, 0);
@@ -1788,7 +1800,7 @@ mg_status mg_prof_query(int kernel, double* total_ms, int* launches, double* byt
         ms += t;
         by += r.bytes;
         fl += r.flops;
-        ++cnt;
+        cnt += r.count;
     }
     if (total_ms) *total_ms = ms;
     if (launches) *launches = cnt;

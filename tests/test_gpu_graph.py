@@ -124,3 +124,28 @@ def test_zero_guess_flag(loc):
         s.close()
     for phi, it in res[1:]:
         assert it == res[0][1] and torch.equal(phi, res[0][0])
+
+
+@pytest.mark.parametrize("loc", ["cell", "nodal"])
+def test_graph_launch_count_matches_host_loop(loc):
+    # the graph path counts its replayed kernels (the loop body per iteration, each conditional
+    # extra V-cycle when it ran); the host loop counts its launches one by one.  The two run the
+    # same kernels plus a few control kernels on the graph side.
+    p = I.stratified(48, seed=5, contrast=1e3)
+    counts = []
+    for flags in (0, N.MG_FLAG_NO_GRAPH):
+        s = ProjectionSolver(p["geom"], T(p["sigma"]), loc=loc, prec="mixed", flags=flags)
+        f = T(np.random.default_rng(2).normal(size=s.vec_shape))
+        phi = torch.zeros_like(f)
+        s.solve(f, phi, tol=1e-10)   # builds the graph and the cached sub-graphs
+        torch.cuda.synchronize()
+        phi.zero_()
+        c0 = N.mg_launch_count()
+        st = s.solve(f, phi, tol=1e-10)
+        torch.cuda.synchronize()
+        counts.append((N.mg_launch_count() - c0, st["vcycles"], st["iters"]))
+        s.close()
+    (g, vg, ig), (h, vh, ih) = counts
+    assert vg == vh and ig == ih
+    # a check kernel and two condition kernels per refinement step, a few per solve
+    assert abs(g - h) <= 4 * (ih + 1) + 12, (g, h)

@@ -322,6 +322,35 @@ def test_config3_256_properties(oracle):
     assert np.linalg.norm(div) / src == pytest.approx(st["rel_constraint"], rel=1e-3)
 
 
+def test_config3_256_nodal_properties(oracle):
+    """256^3 mixed nodal projection in the benchmark's configuration: the oracle's
+    operators confirm the residual of the GPU phi, the velocity update from that
+    phi and the post-projection constraint."""
+    O = oracle
+    p = I.stratified(256, seed=3, contrast=1e3)
+    g = ogrid(O, p["geom"])
+    s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="nodal", prec="mixed")
+    U = [T(u) for u in p["U_cell"]]
+    phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=DEV)
+    st = s.project(U, T(p["beta0"]), T(p["S"]), phi=phi, tol=1e-10, allow_not_converged=True)
+    s.close()
+    ph = H(phi)
+    live = ~g.dirichlet_node_mask()
+    f = O.nodal_rhs(g, p["beta0"], p["U_cell"], p["S"])
+    r = f - O.nodal_apply(g, p["sigma"], ph)
+    rel = np.linalg.norm(r[live]) / np.linalg.norm(f[live])
+    assert rel <= 1e-10 * 1.01 and abs(rel - st["rel_resid"]) <= max(1e-3 * rel, 1e-15)
+    G = O.nodal_grad(g, ph)
+    w = p["sigma"] / p["beta0"]
+    for d in range(3):
+        want = p["U_cell"][d] - w * G[d]
+        assert relerr(H(U[d]), want) <= 1e-12
+    div = O.nodal_rhs(g, p["beta0"], [H(u) for u in U], p["S"])
+    src = O.nodal_lump(g, p["beta0"] * p["S"])
+    con = np.linalg.norm(div[live]) / np.linalg.norm(src[live])
+    assert st["rel_constraint"] == pytest.approx(con, rel=1e-6)
+
+
 # ------------------------------------------------------------- edge cases
 
 def test_zero_rhs_and_determinism():

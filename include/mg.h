@@ -394,8 +394,9 @@ mg_status mg_reciprocal_f64(const double* x, double* y, size_t n, void* stream);
 /* The smoother kernel a level uses: 0 the default rule, 1..3 the vectorised
  * passes with 8/16/32 quads per block row, 4 the shared-memory kernel, 5..7
  * (nodal levels) the vectorised passes with 8/16/32 quads per block row
- * marching four node planes per thread, 8 (cell levels) the TMA-staged
- * one-pass sweep; -1 for a null handle or a level out of range. */
+ * marching four node planes per thread, 9..11 (nodal) the same marching eight
+ * planes, 8 (cell levels) the TMA-staged one-pass sweep; -1 for a null handle
+ * or a level out of range. */
 int mg_smoother_kind(const mg_handle* h, int level);
 
 void mg_prof_enable(int on);

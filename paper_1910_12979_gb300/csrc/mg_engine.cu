@@ -1339,6 +1339,7 @@ mg_status autotune(mg_handle* h)
                     if ((4 << k) <= v.N[0] / 4) {
                         cand.push_back(k);
                         cand.push_back(k + 4);   // the same shape marching four planes
+                        cand.push_back(k + 8);   // and eight
                     }
             if (h->dim == 3 && v.N[0] >= 32 && v.N[1] >= 8) cand.push_back(4);
         } else {

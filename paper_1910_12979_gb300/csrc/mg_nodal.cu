@@ -573,8 +573,17 @@ static void launch_node_tiled(const NodeLevel<T>& L, const T* x, T* out, const T
 }
 
 // quads per block row and planes per thread of the four-node kernel for a smoother kind
-static int v4_width(int kind) { return kind >= 1 && kind <= 3 ? 4 << kind : kind >= 5 && kind <= 7 ? 4 << (kind - 4) : 0; }
-static int v4_planes(int kind) { return kind >= 1 && kind <= 3 ? 1 : kind >= 5 && kind <= 7 ? 4 : 0; }
+// autotuned kinds of the vectorised nodal kernel: 1..3 one node plane per thread, 5..7 four, 9..11
+// eight, with 8/16/32 quads per block row; 0: the launcher's default shape
+static int v4_width(int kind)
+{
+    return kind >= 1 && kind <= 3 ? 4 << kind : kind >= 5 && kind <= 7 ? 4 << (kind - 4)
+                                              : kind >= 9 && kind <= 11 ? 4 << (kind - 8) : 0;
+}
+static int v4_planes(int kind)
+{
+    return kind >= 1 && kind <= 3 ? 1 : kind >= 5 && kind <= 7 ? 4 : kind >= 9 && kind <= 11 ? 8 : 0;
+}
 
 template <typename T>
 void node_jacobi(int dim, const NodeLevel<T>& L, const T* x, T* xo, const T* b, T omega, bool tiled, cudaStream_t s,

@@ -47,10 +47,8 @@ def test_reference_arm_other_ranks_do_nothing():
 def test_reference_arm_under_torchrun_two_ranks():
     # the launch the benchmark's N > 1 runs use, with gloo on the CPU: rank 0 prints one line,
     # rank 1 prints nothing, both exit 0 after the barrier
-    port = 29500 + os.getpid() % 2000
-    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
-                        "--master-addr", "127.0.0.1", "--master-port", str(port),
-                        os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--standalone", "--local-addr", "127.0.0.1",
+                        "--nnodes=1", "--nproc-per-node", "2", os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
                         "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]

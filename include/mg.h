@@ -185,32 +185,45 @@ typedef struct {
 
 typedef struct mg_handle mg_handle;
 
-/* Fill *opt with defaults (mixed precision, V(2,2), linear interpolation). */
+/* Fill *opt with defaults (mixed precision, V(2,2), linear interpolation).  The
+ * paper names multigrid for the projections (S3) but none of its parameters;
+ * these defaults are this library's. */
 void mg_default_options(mg_options* opt);
 
 /* Device bytes that mg_setup needs for this problem (hierarchy, work arrays,
- * dense coarsest inverse, reduction scratch).  Used for admission control. */
+ * dense coarsest inverse, reduction scratch).  Used for admission control.  No
+ * counterpart in the paper (its solver ran on the host, S4); the hierarchy sized
+ * here is the one S3's multigrid needs.  MG_ERR_INVALID_ARG for a null or
+ * invalid argument, MG_ERR_UNSUPPORTED for a grid that does not coarsen. */
 mg_status mg_hierarchy_bytes(const mg_geometry* geom, const mg_bc* bc, const mg_options* opt, size_t* bytes);
 
-/* Build a resident multigrid hierarchy (step a1): face or nodal coefficients on
- * every level, FP32 copies in mixed mode, the dense inverse of the coarsest
- * operator.  workspace: optional caller-owned device buffer of at least
+/* Build a resident multigrid hierarchy for the projection solves of S3 (the
+ * pressure projections are solved by multigrid): the coefficient sigma = beta0/rho
+ * of Eq. 6 (beta0 from Eq. 5, the 1/rho from the gradient term of Eq. 2), face or
+ * nodal coefficients on every level, FP32 copies in mixed mode, the dense inverse
+ * of the coarsest operator.  workspace: optional caller-owned device buffer of at least
  * mg_hierarchy_bytes() bytes (e.g. from the PyTorch caching allocator); NULL
  * makes the library cudaMalloc its own, freed by mg_destroy.  The handle owns
  * nothing else on the device. */
 mg_status mg_setup(const mg_coeff* coeff, const mg_geometry* geom, const mg_bc* bc, const mg_options* opt,
                    void* workspace, size_t workspace_bytes, mg_handle** out);
 
-/* Recompute every level's coefficients from new sigma (same grid), in place. */
+/* Recompute every level's coefficients from new sigma = beta0/rho (Eq. 6; the
+ * base state and density change from one time step to the next, S2-S3) on the
+ * same grid, in place.  Asynchronous on the handle's stream. */
 mg_status mg_update_coeff(mg_handle* h, const mg_coeff* coeff);
 
-/* Solve L phi = rhs to ||rhs - L phi|| <= tol ||rhs||.  rhs: device, unknown
+/* Solve L phi = rhs, the elliptic problem of the projection (S3: multigrid
+ * V-cycles; L = div(sigma grad) discretised as above), to
+ * ||rhs - L phi|| <= tol ||rhs||.  rhs: device, unknown
  * layout (cells or nodes; Dirichlet nodes ignored).  phi: device, in: initial
  * guess, out: solution (Dirichlet nodes set to 0).  stats may be NULL. */
 mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_stats* stats);
 
-/* Projection (steps a2-a10): f = D(beta0 U) - beta0 S, solve to tol, update U
- * in place, report the constraint.  MAC: U[d] face arrays, beta0->face required;
+/* Projection enforcing the constraint div(beta0 U) = beta0 S of Eq. 6 (S2, with
+ * dp0/dt = 0) by the projection method of S3: f = D(beta0 U) - beta0 S, solve
+ * L phi = f by multigrid to tol, update U <- U - (sigma/beta0) G phi in place (the
+ * gradient form -(beta0/rho) grad(pi/beta0) of Eq. 2), report the constraint.  MAC: U[d] face arrays, beta0->face required;
  * the constraint after the update equals the solver residual, and the solve
  * stops when ||f - L phi|| <= tol * min(||f||, ||beta0 S||), so that
  * ||D(beta0 U) - beta0 S|| <= tol ||beta0 S|| holds as well.  Nodal: U[d] cell
@@ -220,7 +233,8 @@ mg_status mg_solve(mg_handle* h, const double* rhs, double* phi, double tol, mg_
 mg_status mg_project(mg_handle* h, double* const U[3], const mg_beta0* beta0, const double* S, double* phi,
                      double tol, mg_stats* stats);
 
-/* Right-hand side of the projection system (step a2) into a caller buffer f
+/* Right-hand side of the projection system (Eq. 6: the divergence of beta0 U
+ * minus beta0 S) into a caller buffer f
  * (device, unknown layout: cells for MAC, nodes for nodal):
  *   MAC    f = D(beta0 U) - beta0 S     (beta0->face required)
  *   nodal  f = D_N(beta0 U) - S_N       (Dirichlet nodes 0)
@@ -248,8 +262,9 @@ mg_status mg_base_state_map(const mg_geometry* geom, int spherical, const double
                             int nr, const double* beta0_r, const double* rho0_r, double* sigma, double* beta0_cell,
                             double* const beta0_face[3], void* stream);
 
-/* Solve count independent problems (any mix of grids, precisions and
- * locations; each handle at most once) as ONE CUDA graph launch on the first
+/* Solve count independent problems of the kind mg_solve solves (S3 multigrid;
+ * batching many of them has no counterpart in the paper) -- any mix of grids,
+ * precisions and locations, each handle at most once -- as ONE CUDA graph launch on the first
  * handle's stream: every solve is a branch of the graph with its own
  * device-side convergence loop, so the branches run concurrently and each
  * stops on its own tolerance tol[i].  The graph is captured on the first call
@@ -260,15 +275,24 @@ mg_status mg_base_state_map(const mg_geometry* geom, int spherical, const double
 mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double* const* phi, const double* tol,
                          int count, mg_stats* stats);
 
-/* Change the handle's stream. */
+/* Change the handle's stream (cudaStream_t; NULL: the legacy default stream).
+ * No counterpart in the paper.  Work already enqueued stays on the old stream:
+ * synchronise it first if the new stream does not wait for it.
+ * MG_ERR_INVALID_ARG for a null handle. */
 mg_status mg_set_stream(mg_handle* h, void* stream);
 
-/* out = L phi with the FP64 fine-level operator (diagnostics and tests). */
+/* out = L phi with the FP64 fine-level operator of the projection system (S3,
+ * Eq. 6's elliptic operator; diagnostics and tests).  Device arrays in the
+ * unknown layout; synchronises the handle's stream. */
 mg_status mg_apply(mg_handle* h, const double* phi, double* out);
 
-/* Free the handle (and its workspace when the library allocated it). */
+/* Free the handle (and its workspace when the library allocated it).  No
+ * counterpart in the paper.  Null is ignored. */
 void mg_destroy(mg_handle* h);
 
+/* Static text naming a status (never NULL; "unknown status" for other values),
+ * and the calling thread's message for its last failing call ("" if none).
+ * No counterpart in the paper. */
 const char* mg_strerror(mg_status s);
 const char* mg_last_error(void);
 
@@ -325,7 +349,9 @@ typedef enum {
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  The first call on a device looks up the array's
  * device address (once per device, with that device current): make that first
- * call before any stream capture. */
+ * call before any stream capture.  The address is kept for the life of the
+ * process, so a cudaDeviceReset of that device after the first call is not
+ * supported (later calls would write through the stale address). */
 #define MG_NOALLOC_MAX_CELLS (1 << 25)
 mg_status mg_mac_constraint_noalloc(const mg_geometry* geom, const double* const U[3], const mg_beta0* beta0,
                                     const double* S, double* out, void* stream);
@@ -398,6 +424,17 @@ mg_status mg_reciprocal_f64(const double* x, double* y, size_t n, void* stream);
  * planes, 8 (cell levels) the TMA-staged one-pass sweep; -1 for a null handle
  * or a level out of range. */
 int mg_smoother_kind(const mg_handle* h, int level);
+
+/* FP64 throughput probe (measurement support; no counterpart in the paper).
+ * Launches blocks x 256 threads, each running eight independent chains of iters
+ * FP64 fused multiply-adds, on stream (cudaStream_t; NULL: the legacy default
+ * stream), asynchronously, and stores the flop count of the launch (2 per FMA)
+ * in *flops (host).  The caller times the launch with CUDA events on the same
+ * stream; flops / time is the FP64 rate the solver's FP64 kernels are judged
+ * against.  sink: device, one double, written only in a case that never occurs.
+ * Reads no memory and changes no GPU setting.  MG_ERR_INVALID_ARG for
+ * non-positive sizes or null pointers. */
+mg_status mg_fp64_fma_probe(int blocks, int iters, double* sink, void* stream, double* flops);
 
 void mg_prof_enable(int on);
 /* Total number of CUDA kernels this library has launched in the process. */

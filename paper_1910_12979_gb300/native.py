@@ -104,6 +104,8 @@ SIGNATURES = [
     ("mg_convert_f64_to_f32_pow2", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     ("mg_reciprocal_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("mg_fp64_fma_probe", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_double)]),
     ("mg_smoother_kind", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mg_prof_enable", None, [ctypes.c_int]),
     ("mg_launch_count", ctypes.c_longlong, []),
@@ -290,6 +292,13 @@ def mg_convert_f64_to_f32_pow2(x_ptr, y_ptr, n, shift, stream=None):
 
 def mg_reciprocal_f64(x_ptr, y_ptr, n, stream=None):
     check(load().mg_reciprocal_f64(x_ptr, y_ptr, n, stream), "mg_reciprocal_f64")
+
+
+def mg_fp64_fma_probe(blocks, iters, sink_ptr, stream=None):
+    """Launch the FP64 FMA probe; returns its flop count (time it with CUDA events)."""
+    fl = ctypes.c_double()
+    check(load().mg_fp64_fma_probe(blocks, iters, sink_ptr, stream, ctypes.byref(fl)), "mg_fp64_fma_probe")
+    return fl.value
 
 
 def mg_smoother_kind(h, level):

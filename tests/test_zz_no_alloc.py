@@ -7,7 +7,13 @@ its reduction scratch in a fixed device array instead of calling cudaMalloc.
 This test projects a velocity field with mg_project, then asks the new entry
 point for the constraint of the projected field twice in a row: both calls
 must agree with the constraint mg_project reported, to the 1e-9 relative
-tolerance of the FP64 parity tests.  This file is collected last on purpose.
+tolerance of the FP64 parity tests.  Grids that do not fill the kernel's blocks
+evenly, a 2-D grid, and a grid with more partial sums than the final reduction
+has threads are checked against the CPU oracle's own right-hand side.
+
+The file is named to be collected last so that a run stopping at its first
+failure has already run every other test when this one fails; nothing in it
+depends on the other tests (each case passes in a fresh process too).
 """
 import ctypes
 
@@ -72,3 +78,46 @@ def test_noalloc_rejects_oversize_grid():
     rc = N.load().mg_mac_constraint_noalloc(ctypes.byref(g), U, ctypes.byref(beta0), ptr, ptr, None)
     assert rc == N.MG_ERR_UNSUPPORTED
     assert "scratch" in N.mg_last_error()
+
+
+@pytest.mark.parametrize("n", [(63, 47), (97, 96, 96)])
+def test_noalloc_ragged_grids_match_oracle(oracle, n):
+    """63 x 47 (2-D; 2961 cells, the last block partly filled) and 97 x 96 x 96
+    (894,048 cells: 437 partial sums, more than the 256 threads of the final
+    reduction, and a partial last block) against sums formed from the oracle's
+    D(beta0 U) - beta0 S."""
+    O = oracle
+    dim = len(n)
+    rng = np.random.default_rng(7)
+    lo = ("neumann", "periodic", "neumann")[:dim]
+    hi = ("dirichlet", "periodic", "dirichlet")[:dim]
+    g = O.Grid.make(n, lo, hi)
+    U = [rng.normal(scale=1e-2, size=g.face_shape(d)) for d in range(dim)]
+    b0f = [np.exp(rng.normal(scale=0.3, size=g.face_shape(d))) for d in range(dim)]
+    b0c = np.exp(rng.normal(scale=0.3, size=g.cell_shape))
+    S = rng.random(g.cell_shape)
+    v = O.mac_rhs(g, b0c, b0f, U, S)
+    want = np.array([v.sum(), ((b0c * S) ** 2).sum(), (v ** 2).sum()])
+
+    geo = N.mg_geometry(dim, tuple(n) + (1,) * (3 - dim), tuple(1.0 / m for m in n) + (1.0,) * (3 - dim),
+                        N.MG_LOC_CELL)
+    Ut = [_T(u) for u in U] + [None] * (3 - dim)
+    bft = [_T(b) for b in b0f] + [None] * (3 - dim)
+    b0ct, St = _T(b0c), _T(S)
+    beta0 = N.mg_beta0()
+    beta0.cell = b0ct.data_ptr()
+    for d in range(dim):
+        beta0.face[d] = bft[d].data_ptr()
+    Uptr = (ctypes.c_void_p * 3)(*[(u.data_ptr() if u is not None else None) for u in Ut])
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda:0")
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        out.fill_(float("nan"))
+        rc = N.load().mg_mac_constraint_noalloc(ctypes.byref(geo), Uptr, ctypes.byref(beta0),
+                                                ctypes.c_void_p(St.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                                ctypes.c_void_p(stream))
+        assert rc == N.MG_OK, N.mg_last_error()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert abs(got[0] - want[0]) <= 1e-9 * np.abs(v).sum()
+        np.testing.assert_allclose(got[1:], want[1:], rtol=1e-9)

@@ -62,9 +62,11 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=24.0, help="serve: device-memory budget of the slots")
     ap.add_argument("--inflight", type=int, default=8, help="serve: concurrent solves")
     ap.add_argument("--serve-count", type=int, default=256, help="serve: requests per arrival rate")
-    ap.add_argument("--sweep", default="v4", choices=["v4", "pipe", "tma"],
+    ap.add_argument("--sweep", default="v4", choices=["v4", "pipe", "tma", "legs"],
                     help="FP32 cell smoother: two vectorised colour passes (v4), the pipelined one-launch "
-                         "sweep (pipe, MG_FLAG_SWEEP_PIPE) or the TMA-staged one-pass sweep (tma, MG_FLAG_SWEEP_TMA)")
+                         "sweep (pipe, MG_FLAG_SWEEP_PIPE), the TMA-staged one-pass sweep (tma, MG_FLAG_SWEEP_TMA) "
+                         "or whole V-cycle legs of the finest level as one L2-pipelined launch each (legs, "
+                         "MG_FLAG_CELL_PIPE)")
     ap.add_argument("--inner-mac", type=int, default=0,
                     help="FP32 V-cycles per FP64 refinement step of the MAC solve (0: the library's choice)")
     ap.add_argument("--nu", default="2,1",
@@ -144,17 +146,81 @@ def oracle_sample(n_sample, seed=3):
     return time.perf_counter() - t0, [a["relres"], b["relres"]]
 
 
-def cpu_baseline(n_full, n_sample=48):
-    dt, _ = oracle_sample(n_sample)
-    scale = (n_full / n_sample) ** 3
-    value = 2.0 / (dt * scale)
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full MAC + nodal oracle projection at {n_sample}^3 of the same recipe "
-                      f"({dt:.2f} s), scaled by the cell-count ratio {scale:.0f} to {n_full}^3 "
-                      f"(multigrid work is linear in cells at fixed iteration counts)"}
+def oracle_cpu_leg(n_full, n_small=48, n_large=128, seed=3, tol=1e-10):
+    """The FP64 oracle timed on this host, one thread: a full MAC + nodal
+    projection of the stratified recipe at n_small^3 and at n_large^3, each to
+    the workload's tolerance.  The n_large^3 time is the baseline (scaled to
+    n_full^3 by the cell count); the two per-cell times check that the work is
+    linear in the cells.  The n_large^3 solutions are then carried on, untimed,
+    to the oracle's round-off floor and returned as the reference for the GPU's
+    error at that size."""
+    import inputs as I
+    import oracle as O
+    O.build()
+    times, ref = {}, None
+    for n in (n_small, n_large):
+        p = I.stratified(n, seed=seed, contrast=1e3)
+        g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+        t0 = time.perf_counter()
+        a = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=tol)
+        b = O.nodal_project(g, p["sigma"], p["beta0"], p["U_cell"], p["S"], tol=tol)
+        times[n] = time.perf_counter() - t0
+        if n == n_large:
+            fm = O.mac_rhs(g, p["beta0"], p["beta0_face"], p["U_mac"], p["S"])
+            phm, _ = O.mac_solve_mg(g, O.mac_faces(g, p["sigma"]), fm, tol=1e-13, phi0=a["phi"])
+            fn = O.nodal_rhs(g, p["beta0"], p["U_cell"], p["S"])
+            phn, _ = O.nodal_solve_mg(g, p["sigma"], fn, tol=1e-13, phi0=b["phi"])
+            ref = {"p": p, "g": g, "mac_phi": phm, "nodal_phi": phn, "live": ~g.dirichlet_node_mask()}
+    scale = (n_full / n_large) ** 3
+    per_cell = {n: times[n] / n ** 3 for n in times}
+    base = {"value": 2.0 / (times[n_large] * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full MAC + nodal oracle projection of the same recipe at {n_large}^3 "
+                      f"({times[n_large]:.1f} s, measured) scaled by the cell-count ratio {scale:.0f} to "
+                      f"{n_full}^3; at {n_small}^3 it took {times[n_small]:.2f} s: "
+                      f"{1e6 * per_cell[n_small]:.2f} vs {1e6 * per_cell[n_large]:.2f} us per cell "
+                      f"(ratio {per_cell[n_large] / per_cell[n_small]:.2f}), so the scaling is checked, not assumed",
+            "measured_s": {f"{n}^3": times[n] for n in times}}
+    return base, ref
+
+
+def gpu_error_vs_oracle(ref, dev, tol):
+    """The GPU's mixed MAC and nodal projections of the oracle's reference
+    problem, in the benchmark's solver configuration, against the oracle's
+    solutions: rel-L2 of phi (nodal: over the unknown nodes)."""
+    import numpy as np
+    import torch
+    from paper_1910_12979_gb300 import ProjectionSolver
+    from paper_1910_12979_gb300 import native as N
+    p = ref["p"]
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    mac = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", flags=N.MG_FLAG_ZERO_GUESS,
+                           nu1=2, nu2=1)
+    nod = ProjectionSolver(p["geom"], T(p["sigma"]), loc="nodal", prec="mixed", flags=N.MG_FLAG_ZERO_GUESS)
+    phim = torch.zeros(mac.vec_shape, dtype=torch.float64, device=dev)
+    phin = torch.zeros(nod.vec_shape, dtype=torch.float64, device=dev)
+    mac.project([T(u) for u in p["U_mac"]], T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]],
+                phi=phim, tol=tol, allow_not_converged=True)
+    nod.project([T(u) for u in p["U_cell"]], T(p["beta0"]), T(p["S"]), phi=phin, tol=tol, allow_not_converged=True)
+    pm, pn = phim.cpu().numpy(), phin.cpu().numpy()
+    mac.close()
+    nod.close()
+    live = ref["live"]
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"grid": f"{p['geom']['n'][0]}^3 (the benchmark's recipe and solver settings at the size the oracle "
+                    f"solves within the run; the GPU to the workload's tol {tol:g}, the oracle to its floor)",
+            "mac_phi_rel_l2_vs_oracle": rel(pm, ref["mac_phi"]),
+            "nodal_phi_rel_l2_vs_oracle": rel(pn[live], ref["nodal_phi"][live]), "bound": 1e-8}
 
 
 def run_reference(args, rank):
+    """The reference arm: the FP64 oracle, as it stands, on this host's cores.
+    Each step is one MAC + nodal oracle projection of a 32^3 instance of the
+    same recipe (a bounded sample of the 256^3 workload: 1/512 of its cells).
+    ms_per_step is the measured time of such a step, so steps x ms_per_step is
+    the time this run spent; value is the throughput on the workload's size,
+    the sample's time scaled by the cell-count ratio (multigrid work is linear
+    in the cells at a fixed iteration count -- the default GPU line's
+    cpu_baseline checks that with a 48^3 and a 128^3 run)."""
     if rank != 0:
         return
     n_sample = 32
@@ -167,13 +233,17 @@ def run_reference(args, rank):
     scale = (args.n / n_sample) ** 3
     total = sum(times) * scale
     value = 2.0 * args.steps / total
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "ms_per_step_at_workload_size": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.n, args.tol),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "host_cores_available": cores,
                              "sample": f"each step: one MAC + nodal oracle projection at {n_sample}^3 of the same "
-                                       f"recipe, scaled by the cell-count ratio {scale:.0f} to {args.n}^3"},
+                                       f"recipe (measured: ms_per_step), scaled by the cell-count ratio "
+                                       f"{scale:.0f} to {args.n}^3 for value"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -327,6 +397,21 @@ def run_batch(args, dev, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = len(solvers) * args.steps * world / (ms / 1e3)
+    errs = None
+    if not args.no_cpu:
+        # three entries (the first 32^3, 96^3 and 128^3 of the batch) against oracle solves of their systems;
+        # the solves of the last timed launch are re-run to leave their phi in place
+        import oracle as O
+        st = step()
+        errs = {"quantity": f"rel-L2 of phi, GPU at tol {args.tol:g} (batch launch), oracle to its floor"}
+        for n in (32, 96, 128):
+            i = next(k for k, sp in enumerate(specs) if sp["n"] == n)
+            p = I.batch_problem(specs[i])
+            g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+            fo = O.mac_rhs(g, p["beta0"], p["beta0_face"], p["U_mac"], p["S"])
+            ref, _ = O.mac_solve_mg(g, O.mac_faces(g, p["sigma"]), fo, tol=1e-13)
+            ph = phis[i].cpu().numpy()
+            errs[f"entry {i} ({n}^3)"] = float(np.linalg.norm(ph - ref) / np.linalg.norm(ref))
     return {"metric": "independent projection solves/s, uneven batch in one graph launch", "value": value,
             "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -339,7 +424,8 @@ def run_batch(args, dev, world, dist):
             "iters": {"min": min(x["iters"] for x in st), "max": max(x["iters"] for x in st)},
             "worst_rel_resid": max(x["rel_resid"] for x in st),
             "sequential": {"value": len(solvers) / (t_seq / 1e3), "unit": "solves/s",
-                           "note": "the same 64 solves issued one mg_solve at a time"}}
+                           "note": "the same 64 solves issued one mg_solve at a time"},
+            "rel_l2_vs_oracle": errs}
 
 
 def run_serve(args, dev, rank, world, dist):
@@ -349,34 +435,37 @@ def run_serve(args, dev, rank, world, dist):
 
     import inputs as I
     from paper_1910_12979_gb300 import native as N
-    from paper_1910_12979_gb300.serve import GpuBackend, Scheduler, device_problem, latency_stats, make_requests, shard
+    from paper_1910_12979_gb300.serve import GpuBackend, Scheduler, host_problem, latency_stats, make_requests, shard
 
     sizes = (64, 96, 128, 192, 256)
-    problems = {n: [device_problem(I.polytrope_star(n, seed=500 + n + k), dev) for k in range(2)] for n in sizes}
+    per_size = 3   # distinct problems per size, in pinned host memory; requests cycle through them
+    raw = {n: [I.polytrope_star(n, seed=500 + n + k) for k in range(per_size)] for n in sizes}
+    problems = {n: [host_problem(p) for p in raw[n]] for n in sizes}
     budget = int(args.budget_gb * 2 ** 30)
     l0 = N.mg_launch_count()
 
     def serve(reqs):
         sch = Scheduler(GpuBackend(problems, device=str(dev), tol=args.tol), budget, max_inflight=args.inflight)
         done = sch.run_stream(reqs, timeout=900)
-        ev = sch.evictions
+        ev, batches = sch.evictions, list(sch.batches)
         sch.close()
-        return done, ev
+        return done, ev, batches
 
     rng = np.random.default_rng(5)
     # saturation: every request present at t = 0
     sat_n = args.serve_count // 4
     ns = [int(x) for x in rng.choice(sizes, size=sat_n)]
-    serve(make_requests([0.0] * 8, ns[:8], 2))                     # warm-up: slot creation, graphs
-    done, _ = serve(shard(make_requests([0.0] * sat_n, ns, 2), rank, world))
+    serve(make_requests([0.0] * 8, ns[:8], per_size))              # warm-up: slot creation, graphs
+    done, _, _ = serve(shard(make_requests([0.0] * sat_n, ns, per_size), rank, world))
     mu = latency_stats(done)["solves_per_s"]
     rates = {}
     for frac in (0.5, 0.8, 0.95):
         t, ns2 = I.poisson_arrivals(frac * mu * world, args.serve_count, seed=5, sizes=sizes)
-        reqs = shard(make_requests(t, ns2, 2, seed=5), rank, world)
-        done, ev = serve(reqs)
+        reqs = shard(make_requests(t, ns2, per_size, seed=5), rank, world)
+        done, ev, batches = serve(reqs)
         bad = sum(isinstance(r.status, Exception) for r in done)
-        rates[str(frac)] = dict(latency_stats(done), evictions=ev, failed=bad)
+        rates[str(frac)] = dict(latency_stats(done), evictions=ev, failed=bad,
+                                batched_requests=sum(b for b in batches if b > 1), mean_batch=float(np.mean(batches)))
     launches = N.mg_launch_count() - l0
     head = rates["0.8"]
     out = {"metric": "serving: projection solves/s and p50/p99 latency at 0.8 x saturation", "value":
@@ -385,9 +474,36 @@ def run_serve(args, dev, rank, world, dist):
            "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
            "config": {"workload": "Poisson arrivals of polytrope (n=3) star MAC projections, Dirichlet, "
                                   "sizes {64,96,128,192,256}^3 (seed 5)", "budget_gb": args.budget_gb,
-                      "max_inflight": args.inflight, "tol": args.tol},
+                      "max_inflight": args.inflight, "tol": args.tol,
+                      "io": f"every request uploads its problem (sigma, beta0 at cells and faces, S, U) from pinned "
+                            f"host memory and reads the projected U back: latency includes both; {per_size} "
+                            f"distinct problems per size", "batching": "requests admitted together run as one "
+                                                                     "mg_project_batch (solves in one graph launch)"},
            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "saturation_solves_per_s": mu * world,
            "rates": rates, "gpu_launches": launches}
+    if rank == 0 and not args.no_cpu:
+        out["rel_l2_vs_oracle"] = served_error_vs_oracle(raw, dev, args.tol)
+    return out
+
+
+def served_error_vs_oracle(raw, dev, tol):
+    """Two served requests (64^3 and 128^3 polytrope stars) through the serving
+    backend, their projected velocities against oracle projections."""
+    import numpy as np
+    import oracle as O
+    from paper_1910_12979_gb300.serve import GpuBackend, Request, Scheduler, host_problem
+    out = {}
+    for n in (64, 128):
+        p = raw[n][0]
+        sch = Scheduler(GpuBackend({n: [host_problem(p)]}, device=str(dev), tol=tol), 8 * 2 ** 30, max_inflight=1)
+        r = sch.run_stream([Request(0, n, 0.0, (n, 0), keep=True)], timeout=600)[0]
+        sch.close()
+        g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+        ref = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-13)
+        num = math.sqrt(sum(float(np.sum((u.numpy() - v) ** 2)) for u, v in zip(r.result, ref["U"])))
+        den = math.sqrt(sum(float(np.sum(v ** 2)) for v in ref["U"]))
+        out[f"{n}^3"] = num / den
+    out["quantity"] = f"rel-L2 of the projected face velocity, GPU at tol {tol:g}, oracle to its floor"
     return out
 
 
@@ -549,21 +665,26 @@ def run_config2(args, dev):
             out[prec] = {"solves_per_s": 2 * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
                          "mac": {k: a[k] for k in ("iters", "rel_resid", "rel_constraint")},
                          "nodal": {k: b[k] for k in ("iters", "rel_resid", "rel_constraint")},
-                         "phi_mac": phim.cpu().numpy()}
+                         "phi_mac": phim.cpu().numpy(), "phi_nodal": phin.cpu().numpy()}
     line = {"metric": "128^3 MAC + nodal projection step, FP64 plain multigrid, solves/s",
             "value": out["fp64"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "stratified atmosphere 128^3 (contrast 1e3, seed 2), MAC + nodal, tol %g" % args.tol},
             "mixed_vs_fp64": out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]}
-    if args.parity:
+    check = not args.no_cpu
+    if check:
         import oracle as O
         g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
         ref = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-13)
+        refn = O.nodal_project(g, p["sigma"], p["beta0"], p["U_cell"], p["S"], tol=1e-13)
+        live = ~g.dirichlet_node_mask()
     for prec in ("fp64", "mixed"):
-        ph = out[prec].pop("phi_mac")
-        if args.parity:
+        ph, pn = out[prec].pop("phi_mac"), out[prec].pop("phi_nodal")
+        if check:
             out[prec]["mac"]["rel_l2_vs_oracle"] = float(np.linalg.norm(ph - ref["phi"]) / np.linalg.norm(ref["phi"]))
+            out[prec]["nodal"]["rel_l2_vs_oracle"] = float(np.linalg.norm(pn[live] - refn["phi"][live]) /
+                                                           np.linalg.norm(refn["phi"][live]))
         line[prec] = out[prec]
     return line
 
@@ -629,7 +750,8 @@ def main():
 
     def make(prec):
         # every step starts the solves from phi = 0 (the step zeroes phi anyway)
-        fl = N.MG_FLAG_ZERO_GUESS | {"v4": 0, "pipe": N.MG_FLAG_SWEEP_PIPE, "tma": N.MG_FLAG_SWEEP_TMA}[args.sweep]
+        fl = N.MG_FLAG_ZERO_GUESS | {"v4": 0, "pipe": N.MG_FLAG_SWEEP_PIPE, "tma": N.MG_FLAG_SWEEP_TMA,
+                                     "legs": N.MG_FLAG_CELL_PIPE}[args.sweep]
         cm = {"coarsest_max": args.coarsest} if args.coarsest > 0 else {}
         nu_c = [int(v) for v in args.nu.split(",")]
         nu_n = [int(v) for v in args.nu_nodal.split(",")]
@@ -747,8 +869,9 @@ def main():
                               if args.autotune else {})),
             "clocks": clocks, "gpu_launches": launches, "roofline": roof_line,
             "fp64_tflops_measured": fp64_peak, "fp64_probe_clocks": fp64_clocks,
-            "solver": {"mac": {k: st_mac[k] for k in ("iters", "vcycles", "rel_resid", "rel_constraint")},
-                       "nodal": {k: st_nod[k] for k in ("iters", "vcycles", "rel_resid", "rel_constraint")}}}
+            "solver": {nm: dict({k: st[k] for k in ("iters", "vcycles", "rel_resid", "rel_constraint")},
+                                rel_constraint_before=st["rhs_norm"] / st["src_norm"] if st["src_norm"] > 0 else None)
+                       for nm, st in (("mac", st_mac), ("nodal", st_nod))}}
 
     if args.only_mixed:
         args.no_fp64 = args.no_e2e = args.no_cpu = True
@@ -897,7 +1020,8 @@ def main():
                           "oracle_relres": ref["relres"], "tol": args.tol}
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(n)
+        line["cpu_baseline"], ref = oracle_cpu_leg(n)
+        line["parity"] = dict(line.get("parity", {}), **gpu_error_vs_oracle(ref, dev, args.tol))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

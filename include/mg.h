@@ -166,6 +166,14 @@ typedef struct {
  * in one pass over memory (same arithmetic).  A stage copy that does not
  * complete within about two seconds makes the solve return MG_ERR_CUDA. */
 #define MG_FLAG_SWEEP_TMA 32
+/* flags (mixed precision, 3-D cell grids of at least 2^14 cells, z not
+ * periodic): run each leg of a V-cycle on the finest level -- the nu1 sweeps
+ * with the residual restriction, and the prolongation with the nu2 sweeps --
+ * as ONE persistent launch whose colour passes are pipelined through L2 (same
+ * results as the pass-by-pass kernels, which are the default).  A pipelined
+ * pass that waits for its predecessor longer than about a second makes the
+ * solve return MG_ERR_CUDA. */
+#define MG_FLAG_CELL_PIPE 64
 
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
@@ -275,6 +283,30 @@ mg_status mg_base_state_map(const mg_geometry* geom, int spherical, const double
 mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double* const* phi, const double* tol,
                          int count, mg_stats* stats);
 
+/* count projections (as mg_project; any mix of grids, precisions and locations,
+ * each handle at most once) whose elliptic solves run as ONE CUDA graph launch:
+ * the right-hand side of each (Eq. 6, a2) is formed on its handle's own stream,
+ * after whatever the caller has queued there (uploads of its inputs, a
+ * coefficient update), the solves (S3 multigrid) run as the branches of one
+ * graph on the first handle's stream, and each projection update (Eq. 2's
+ * gradient form) and constraint is then applied on its handle's stream.
+ * Batching projections has no counterpart in the paper; it serves many
+ * independent requests at once.
+ *   hs      count handles
+ *   U       3 * count device pointers: U[3 i + d] is component d of entry i
+ *           (faces for MAC, cells for nodal; unused entries of 2-D grids NULL);
+ *           updated in place
+ *   beta0   count entries, as for mg_project
+ *   S       count device pointers (cells)
+ *   phi     NULL, or count device pointers (each NULL: internal buffer)
+ *   tol     count tolerances (> 0), as for mg_project
+ *   stats   NULL or count entries (ms: wall time of the whole batch)
+ * The graph of an ordered list of handles is captured on first use and cached
+ * (at most 64 batch graphs; the least recently used is dropped first).
+ * Returns the first non-OK status; synchronises the handles' streams. */
+mg_status mg_project_batch(mg_handle* const* hs, double* const* U, const mg_beta0* beta0, const double* const* S,
+                           double* const* phi, const double* tol, int count, mg_stats* stats);
+
 /* Change the handle's stream (cudaStream_t; NULL: the legacy default stream).
  * No counterpart in the paper.  Work already enqueued stays on the old stream:
  * synchronise it first if the new stream does not wait for it.
@@ -325,7 +357,13 @@ typedef enum {
                                      per node of the form evaluated: 44 for the row assembled
                                      from 8 sigma (2-D, small 3-D grids), about 25.8 for the
                                      sum-factorised 3-D form (edge sigma sums set up once) */
-    MG_PROF_COUNT = 5
+    MG_PROF_CELL_PIPE_DOWN = 5,   /* down leg of a V-cycle on the finest cell level as one
+                                     pipelined launch: nu1 sweeps (4 words/cell each) and the
+                                     residual + restriction (3 + 1/8 words/cell) */
+    MG_PROF_CELL_PIPE_UP = 6,     /* up leg as one pipelined launch: the prolongation fused
+                                     into the first of nu2 sweeps (4 + 1/8 words/cell), 4 words
+                                     per further sweep */
+    MG_PROF_COUNT = 7
 } mg_prof_kernel;
 
 /* Allocation-free check of the MAC constraint.  The paper has no counterpart:

@@ -7,6 +7,6 @@ is the thin Python binding: ``native`` wraps the C entry points one to one,
 ``solver`` adds a torch-tensor convenience class.
 """
 from . import native  # noqa: F401
-from .solver import ProjectionSolver, solve_batch  # noqa: F401
+from .solver import ProjectionSolver, project_batch, solve_batch  # noqa: F401
 
-__all__ = ["native", "ProjectionSolver", "solve_batch"]
+__all__ = ["native", "ProjectionSolver", "project_batch", "solve_batch"]

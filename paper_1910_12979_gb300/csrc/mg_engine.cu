@@ -160,6 +160,11 @@ struct mg_handle {
     cudaGraphExec_t cg[2];
     long long cg_launches[2];
     bool cg_failed[2];
+    // pipelined legs of the finest FP32 cell level (mg_cellpipe.cu): ticket,
+    // exit and epoch counters and the work-item flags; null when not used
+    unsigned* pipe_ctr;
+    unsigned* pipe_flags;
+    cudaEvent_t ev;   // batch projections: the handle's right-hand side is ready
 };
 
 void mgp::handle_info(const mg_handle* h, mg_geometry* g, mg_bc* bc, cudaStream_t* s)
@@ -276,6 +281,17 @@ mg_status plan(mg_handle* h, Bump& B)
     h->Minv = B.take<double>((size_t)h->Nd * h->Nd);
     h->partials = B.take<double>((size_t)kRedSlots * kRedBlocks);
     h->d = B.take<DevScalars>(1);
+    h->pipe_ctr = nullptr;
+    h->pipe_flags = nullptr;
+    {
+        const Level& v0 = h->lev[0];
+        if ((h->opt.flags & MG_FLAG_CELL_PIPE) && mixed && !nodal && dim == 3 && h->nlev >= 2 &&
+            v0.ncell >= kPipeMinCells && v0.n[0] % 4 == 0 &&
+            v0.n[1] % 2 == 0 && v0.n[2] % 2 == 0 && h->bc.lo[2] != BCP) {
+            h->pipe_ctr = B.take<unsigned>(4);
+            h->pipe_flags = B.take<unsigned>(cell_pipe_flag_words(v0.n[1], v0.n[2], kPipeMaxNu));
+        }
+    }
     return MG_OK;
 }
 
@@ -390,7 +406,7 @@ mg_status readback(mg_handle* h)
 {
     MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
     MG_CK(cudaStreamSynchronize(h->stream));
-    if (h->hs->async_err) return fail(MG_ERR_CUDA, "an asynchronous shared-memory copy did not complete in time");
+    if (h->hs->async_err) return fail(MG_ERR_CUDA, "a bounded wait inside a kernel (an asynchronous copy or a pipelined pass) gave up");
     return MG_OK;
 }
 
@@ -565,6 +581,76 @@ void cell_smooth(mg_handle* h, int l, const CellLevel<T>& V, T* x, const T* b, i
     prof_end(pr, s);
 }
 
+// The pipelined legs (mg_cellpipe.cu) apply, when MG_FLAG_CELL_PIPE asks for
+// them, to the finest FP32 level of a handle that laid out their counters.
+bool pipe_on(const mg_handle* h)
+{
+    return h->pipe_ctr && (h->opt.flags & MG_FLAG_CELL_PIPE) &&
+           !(h->opt.flags & (MG_FLAG_NO_FUSED | MG_FLAG_SWEEP_PIPE | MG_FLAG_SWEEP_TMA));
+}
+
+PipeSync pipe_sync(mg_handle* h) { return PipeSync{h->pipe_ctr, h->pipe_flags, &h->d->async_err}; }
+
+// Down leg of the finest cell level: (x0 = 0 if zero_init,) nu1 sweeps, and the
+// residual restricted into level 1's b.  One pipelined launch where it
+// applies; else the smoother passes and the residual + restriction kernel.
+template <typename T>
+void cell_down0(mg_handle* h, T* x0, const T* b0, bool zero_init)
+{
+    cudaStream_t s = h->stream;
+    const int dim = h->dim;
+    const CellLevel<T> V = cview<T>(h, 0);
+    if constexpr (std::is_same<T, float>::value) {
+        const int nu = h->opt.nu1;
+        if (pipe_on(h) && nu >= 1 && nu <= kPipeMaxNu && cell_pipe_ok(V, x0, b0)) {
+            // algorithmic words per cell: 4 per sweep, 3 + 1/8 for the residual + restriction
+            const int pr = prof_begin(MG_PROF_CELL_PIPE_DOWN,
+                                      (4.0 * nu + 3.0 + 0.125) * sizeof(T) * (double)h->lev[0].ncell, s);
+            cell_pipe_down(V, x0, b0, lb<T>(h, 1), nu, zero_init, pipe_sync(h), s);
+            prof_end(pr, s);
+            return;
+        }
+    }
+    if (zero_init) zero(x0, h->lev[0].nvec, s);
+    cell_smooth<T>(h, 0, V, x0, b0, h->opt.nu1);
+    const int pr = prof_begin(MG_PROF_CELL_RESTRICT_FINE, (3.0 + 1.0 / (1 << dim)) * sizeof(T) * h->lev[0].ncell, s);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (!(h->opt.flags & (MG_FLAG_NO_FUSED | MG_FLAG_SWEEP_PIPE)) &&
+            cell_resid_restrict_v4_ok(dim, V, x0, b0, lb<T>(h, 1))) {
+            cell_resid_restrict_v4(V, x0, b0, lb<T>(h, 1), s);
+            done = true;
+        }
+    }
+    if (!done) cell_resid_restrict<T>(dim, V, x0, b0, lb<T>(h, 1), s);
+    prof_end(pr, s);
+}
+
+// Up leg of the finest cell level: x0 += P x1, then nu2 sweeps; one pipelined
+// launch where it applies (linear prolongation).
+template <typename T>
+void cell_up0(mg_handle* h, T* x0, const T* b0)
+{
+    cudaStream_t s = h->stream;
+    const int dim = h->dim;
+    const CellLevel<T> V = cview<T>(h, 0);
+    if constexpr (std::is_same<T, float>::value) {
+        const int nu = h->opt.nu2;
+        if (pipe_on(h) && nu >= 1 && nu <= kPipeMaxNu && h->opt.interp_order == 1 && cell_pipe_ok(V, x0, b0) &&
+            cell_prolong_v4_ok(dim, V, x0, lx<T>(h, 1))) {
+            // algorithmic words per cell: the prolongation fused into the first
+            // sweep 4 + 1/8, then 4 per further sweep
+            const int pr =
+                prof_begin(MG_PROF_CELL_PIPE_UP, (4.0 * nu + 0.125) * sizeof(T) * (double)h->lev[0].ncell, s);
+            cell_pipe_up(V, cview<T>(h, 1), x0, b0, lx<T>(h, 1), nu, pipe_sync(h), s);
+            prof_end(pr, s);
+            return;
+        }
+    }
+    cell_prolong_add<T>(dim, V, cview<T>(h, 1), x0, lx<T>(h, 1), h->opt.interp_order, s);
+    cell_smooth<T>(h, 0, V, x0, b0, h->opt.nu2);
+}
+
 // First level of the one-launch coarse end of a cell V-cycle: levels lc .. L-1
 // (at most kCoarseCells cells each) run as one launch; L when nothing is fused.
 int cell_coarse_start(const mg_handle* h)
@@ -587,7 +673,11 @@ void vcycle_cell_range(mg_handle* h, int first, T* x0, const T* b0, bool zero_in
     auto X = [&](int l) { return l == 0 ? x0 : lx<T>(h, l); };
     auto Bv = [&](int l) { return l == 0 ? b0 : (const T*)lb<T>(h, l); };
     for (int l = first; l < lc && l < L - 1; ++l) {
-        if (l > 0 || zero_init) zero(X(l), h->lev[l].nvec, s);
+        if (l == 0) {
+            cell_down0<T>(h, x0, b0, zero_init);
+            continue;
+        }
+        zero(X(l), h->lev[l].nvec, s);
         const CellLevel<T> V = cview<T>(h, l);
         cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu1);
         const int pr = l == 0 ? prof_begin(MG_PROF_CELL_RESTRICT_FINE,
@@ -618,6 +708,10 @@ void vcycle_cell_range(mg_handle* h, int first, T* x0, const T* b0, bool zero_in
         dense_apply<T>(h->Minv, h->Nd, Bv(L - 1), X(L - 1), s);
     }
     for (int l = (lc < L ? lc : L - 1) - 1; l >= first; --l) {
+        if (l == 0) {
+            cell_up0<T>(h, x0, b0);
+            continue;
+        }
         const CellLevel<T> V = cview<T>(h, l);
         cell_prolong_add<T>(dim, V, cview<T>(h, l + 1), X(l), X(l + 1), h->opt.interp_order, s);
         cell_smooth<T>(h, l, V, X(l), Bv(l), h->opt.nu2);
@@ -685,27 +779,10 @@ void vcycle_cell(mg_handle* h, T* x0, const T* b0, bool zero_init)
         return;
     }
     cudaStream_t s = h->stream;
-    const int dim = h->dim;
-    // level 0 down leg, as in vcycle_cell_range
-    if (zero_init) zero(x0, h->lev[0].nvec, s);
-    const CellLevel<T> V = cview<T>(h, 0);
-    cell_smooth<T>(h, 0, V, x0, b0, h->opt.nu1);
-    const int pr = prof_begin(MG_PROF_CELL_RESTRICT_FINE, (3.0 + 1.0 / (1 << dim)) * sizeof(T) * h->lev[0].ncell, s);
-    bool done = false;
-    if constexpr (std::is_same<T, float>::value) {
-        if (!(h->opt.flags & (MG_FLAG_NO_FUSED | MG_FLAG_SWEEP_PIPE)) &&
-            cell_resid_restrict_v4_ok(dim, V, x0, b0, lb<T>(h, 1))) {
-            cell_resid_restrict_v4(V, x0, b0, lb<T>(h, 1), s);
-            done = true;
-        }
-    }
-    if (!done) cell_resid_restrict<T>(dim, V, x0, b0, lb<T>(h, 1), s);
-    prof_end(pr, s);
+    cell_down0<T>(h, x0, b0, zero_init);
     cudaGraphLaunch(cg, s);
     add_launches(h->cg_launches[std::is_same<T, float>::value ? 0 : 1]);
-    // level 0 up leg
-    cell_prolong_add<T>(dim, V, cview<T>(h, 1), x0, lx<T>(h, 1), h->opt.interp_order, s);
-    cell_smooth<T>(h, 0, V, x0, b0, h->opt.nu2);
+    cell_up0<T>(h, x0, b0);
 }
 
 template <typename T>
@@ -1232,7 +1309,7 @@ mg_status graph_result(mg_handle* h, long long fixed, long long body, long long 
 {
     const DevScalars& r = *h->hs;
     add_launches(fixed + body * r.iters + ifb * r.n_extra);
-    if (r.async_err) return fail(MG_ERR_CUDA, "an asynchronous shared-memory copy did not complete in time");
+    if (r.async_err) return fail(MG_ERR_CUDA, "a bounded wait inside a kernel (an asynchronous copy or a pipelined pass) gave up");
     if (r.info != 0) return fail(MG_ERR_UNSUPPORTED, "the coarsest-level operator is singular");
     if (st) {
         st->iters = r.iters;
@@ -1254,9 +1331,11 @@ mg_status graph_result(mg_handle* h, long long fixed, long long body, long long 
 // Batch graphs, cached by the exact ordered list of handles.
 struct BatchGraph {
     std::vector<mg_handle*> hs;
+    bool rhs_io = true;   // right-hand sides from the callers (solves) or already in f64 (projections)
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> fixed, body, ifb;
 };
+constexpr size_t kMaxBatchGraphs = 64;   // cached batch graphs; the least recently used goes first
 std::mutex g_batch_mu;
 std::vector<BatchGraph*> g_batches;
 
@@ -1275,6 +1354,48 @@ void drop_batches_of(mg_handle* h)
             ++i;
         }
     }
+}
+
+// The cached batch graph of this ordered list of handles and mode (built on
+// first use); the list keeps the most recently used last and at most
+// kMaxBatchGraphs entries.
+mg_status batch_graph(mg_handle* const* hs, int count, bool rhs_io, BatchGraph** out)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (size_t i = 0; i < g_batches.size(); ++i) {
+            BatchGraph* b = g_batches[i];
+            if (b->rhs_io == rhs_io && (int)b->hs.size() == count && std::equal(b->hs.begin(), b->hs.end(), hs)) {
+                g_batches.erase(g_batches.begin() + i);
+                g_batches.push_back(b);
+                *out = b;
+                return MG_OK;
+            }
+        }
+    }
+    std::unique_ptr<BatchGraph> nb(new BatchGraph());
+    nb->hs.assign(hs, hs + count);
+    nb->rhs_io = rhs_io;
+    mg_status rc = build_graph(hs, count, rhs_io, &nb->exec, nb->fixed, nb->body, nb->ifb);
+    if (rc != MG_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    // evict from the least recently used end, skipping graphs whose handles are
+    // in use (their caller may be launching the graph right now)
+    for (size_t i = 0; g_batches.size() >= kMaxBatchGraphs && i < g_batches.size();) {
+        BatchGraph* old = g_batches[i];
+        bool busy = false;
+        for (mg_handle* x : old->hs) busy = busy || x->busy.load() != 0;
+        if (busy) {
+            ++i;
+            continue;
+        }
+        if (old->exec) cudaGraphExecDestroy(old->exec);
+        delete old;
+        g_batches.erase(g_batches.begin() + i);
+    }
+    *out = nb.release();
+    g_batches.push_back(*out);
+    return MG_OK;
 }
 
 struct BusyGuard {
@@ -1482,6 +1603,7 @@ mg_status mg_setup(const mg_coeff* c, const mg_geometry* g, const mg_bc* bc, con
     // one-time limits of the TMA-staged sweep, here rather than inside a stream capture
     if (rc == MG_OK && h->prec == MG_PREC_MIXED && h->loc == MG_LOC_CELL && h->dim == 3)
         (void)cell_gsrb_tma_fits(h->lev[0].n[0]);
+    if (rc == MG_OK && h->pipe_ctr) (void)cell_pipe_grid();
     if (rc == MG_OK && (h->opt.flags & MG_FLAG_AUTOTUNE)) rc = autotune(h);
     if (rc != MG_OK) { mg_destroy(h); return rc; }
     *out = h;
@@ -1656,20 +1778,8 @@ mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double*
     }
     const double t0 = now_ms();
     BatchGraph* bg = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_batch_mu);
-        for (BatchGraph* b : g_batches)
-            if ((int)b->hs.size() == count && std::equal(b->hs.begin(), b->hs.end(), hs)) bg = b;
-    }
-    if (!bg) {
-        std::unique_ptr<BatchGraph> nb(new BatchGraph());
-        nb->hs.assign(hs, hs + count);
-        mg_status rc = build_graph(hs, count, true, &nb->exec, nb->fixed, nb->body, nb->ifb);
-        if (rc != MG_OK) return rc;
-        std::lock_guard<std::mutex> lk(g_batch_mu);
-        bg = nb.release();
-        g_batches.push_back(bg);
-    }
+    mg_status brc = batch_graph(hs, count, true, &bg);
+    if (brc != MG_OK) return brc;
     cudaStream_t s = hs[0]->stream;
     for (int i = 0; i < count; ++i)
         MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(hs[i]->d, rhs[i], phi[i], tol[i], hs[i]->opt.max_iters));
@@ -1684,6 +1794,115 @@ mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double*
         local.status = rc;
         if (st) st[i] = local;
         if (rc != MG_OK && worst == MG_OK) worst = rc;
+    }
+    return worst;
+}
+
+mg_status mg_project_batch(mg_handle* const* hs, double* const* U, const mg_beta0* b0, const double* const* S,
+                           double* const* phi, const double* tol, int count, mg_stats* st)
+{
+    if (count < 0 || (count > 0 && (!hs || !U || !b0 || !S || !tol))) return fail(MG_ERR_INVALID_ARG, "bad batch");
+    if (count == 0) return MG_OK;
+    bool graph = true;
+    for (int i = 0; i < count; ++i) {
+        mg_handle* h = hs[i];
+        if (!h || !S[i] || !b0[i].cell || !(tol[i] > 0.0)) return fail(MG_ERR_INVALID_ARG, "bad batch entry");
+        for (int d = 0; d < h->dim; ++d) {
+            if (!U[3 * i + d]) return fail(MG_ERR_INVALID_ARG, "U[d] is null");
+            if (h->loc == MG_LOC_CELL && !b0[i].face[d]) return fail(MG_ERR_INVALID_ARG, "beta0 faces are required (MAC)");
+        }
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) return fail(MG_ERR_INVALID_ARG, "a handle appears twice in the batch");
+        graph = graph && use_graph(h);
+    }
+    mg_status worst = MG_OK;
+    if (!graph) {
+        for (int i = 0; i < count; ++i) {
+            mg_status rc = mg_project(hs[i], U + 3 * i, &b0[i], S[i], phi ? phi[i] : nullptr, tol[i], st ? &st[i] : nullptr);
+            if (rc != MG_OK && worst == MG_OK) worst = rc;
+        }
+        return worst;
+    }
+    std::vector<std::unique_ptr<BusyGuard>> guards;
+    for (int i = 0; i < count; ++i) {
+        guards.emplace_back(new BusyGuard(hs[i]));
+        if (!guards.back()->ok) return fail(MG_ERR_BUSY, "handle in use");
+    }
+    const double t0 = now_ms();
+    BatchGraph* bg = nullptr;
+    mg_status rc = batch_graph(hs, count, false, &bg);
+    if (rc != MG_OK) return rc;
+    cudaStream_t s = hs[0]->stream;
+    std::vector<double*> ph(count);
+    // a2 on each handle's own stream (after whatever the caller queued there:
+    // uploads, a coefficient update); the batch stream waits for all of them
+    for (int i = 0; i < count; ++i) {
+        mg_handle* h = hs[i];
+        cudaStream_t hsx = h->stream;
+        const Level& v0 = h->lev[0];
+        const double* Uc[3] = {U[3 * i], U[3 * i + 1], h->dim == 3 ? U[3 * i + 2] : nullptr};
+        ph[i] = phi && phi[i] ? phi[i] : h->phi_int;
+        if (ph[i] == h->phi_int) zero(ph[i], v0.nvec, hsx);
+        if (h->loc == MG_LOC_CELL)
+            cell_rhs(h->dim, cview<double>(h, 0), v0.h, Uc, b0[i].face, b0[i].cell, S[i], h->f64, h->partials, hsx);
+        else
+            node_rhs(h->dim, nview<double>(h, 0), v0.h[0], Uc, b0[i].cell, S[i], h->f64, h->partials, hsx);
+        reduce_finalize(h->partials, 3, h->d->red, hsx);
+        finish_rhs(h, 2, 1);
+        if (hsx != s) {
+            if (!h->ev) MG_CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
+            MG_CK(cudaEventRecord(h->ev, hsx));
+            MG_CK(cudaStreamWaitEvent(s, h->ev, 0));
+        }
+    }
+    // a3-a8: every solve a branch of one graph
+    for (int i = 0; i < count; ++i) {
+        MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(hs[i]->d, nullptr, ph[i], tol[i], hs[i]->opt.max_iters));
+        if (hs[i]->loc == MG_LOC_CELL) MGP_LAUNCH(k_constraint_tol<<<1, 1, 0, s>>>(hs[i]->d));
+    }
+    MG_CK(cudaGraphLaunch(bg->exec, s));
+    MG_CK(cudaStreamSynchronize(s));
+    // a9-a10 on each handle's stream (concurrently), then the read-backs
+    std::vector<mg_stats> local(count);
+    std::vector<mg_status> rcs(count);
+    for (int i = 0; i < count; ++i) {
+        mg_handle* h = hs[i];
+        memset(&local[i], 0, sizeof(mg_stats));
+        rcs[i] = graph_result(h, bg->fixed[i], bg->body[i], bg->ifb[i], &local[i]);
+        if (rcs[i] != MG_OK && rcs[i] != MG_ERR_NOT_CONVERGED) continue;
+        cudaStream_t hsx = h->stream;
+        const Level& v0 = h->lev[0];
+        double* const Ui[3] = {U[3 * i], U[3 * i + 1], h->dim == 3 ? U[3 * i + 2] : nullptr};
+        const double* Uc[3] = {Ui[0], Ui[1], Ui[2]};
+        if (h->loc == MG_LOC_CELL) {
+            cell_project(h->dim, cview<double>(h, 0), v0.h, ph[i], b0[i].face, Ui, hsx);
+            cell_rhs(h->dim, cview<double>(h, 0), v0.h, Uc, b0[i].face, b0[i].cell, S[i], nullptr, h->partials, hsx);
+        } else {
+            node_project(h->dim, nview<double>(h, 0), v0.h[0], ph[i], b0[i].cell, Ui, hsx);
+            if (!node_constraint32(h->dim, nview<double>(h, 0), v0.h[0], Uc, b0[i].cell, S[i], h->partials, hsx))
+                node_rhs(h->dim, nview<double>(h, 0), v0.h[0], Uc, b0[i].cell, S[i], nullptr, h->partials, hsx);
+        }
+        reduce_finalize(h->partials, 3, h->d->red, hsx);
+    }
+    for (int i = 0; i < count; ++i) {
+        mg_handle* h = hs[i];
+        if (rcs[i] == MG_OK || rcs[i] == MG_ERR_NOT_CONVERGED) {
+            const mg_status r2 = readback(h);
+            if (r2 != MG_OK) {
+                rcs[i] = r2;
+            } else {
+                const double src2 = h->loc == MG_LOC_CELL ? h->hs->red[1] : h->hs->src2, con2 = h->hs->red[2];
+                local[i].src_norm = sqrt(src2);
+                local[i].rel_constraint = src2 > 0.0 ? sqrt(con2 / src2) : sqrt(con2);
+            }
+        }
+        if (rcs[i] != MG_OK && worst == MG_OK) worst = rcs[i];
+    }
+    const double ms = now_ms() - t0;
+    for (int i = 0; i < count; ++i) {
+        local[i].ms = ms;
+        local[i].status = rcs[i];
+        if (st) st[i] = local[i];
     }
     return worst;
 }
@@ -1708,6 +1927,7 @@ void mg_destroy(mg_handle* h)
         if (h->gx[i]) cudaGraphExecDestroy(h->gx[i]);
         if (h->cg[i]) cudaGraphExecDestroy(h->cg[i]);
     }
+    if (h->ev) cudaEventDestroy(h->ev);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->hs) cudaFreeHost(h->hs);
     delete h;

@@ -18,7 +18,7 @@
 // the diagonal -- is that of k_gsrb (cell_row), so two passes of this kernel
 // equal two passes of k_gsrb bit for bit.  Requirements (checked by the
 // launcher): FP32, nx % 4 == 0.
-#include "mg_cellops.cuh"
+#include "mg_cellquad.cuh"
 
 namespace mgp {
 
@@ -34,108 +34,11 @@ template <int DIM>
 __global__ void __launch_bounds__(256)
 k_gsrb_v4(CellLevel<float> L, float* __restrict__ x, const float* __restrict__ b, int color)
 {
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = DIM == 3 ? (int)blockIdx.z : 0;
-    if (4 * q >= nx || j >= ny) return;
-    const int i0 = 4 * q;
-    const size_t plane = (size_t)nx * ny;
-    const size_t row = (size_t)k * plane + (size_t)j * nx;
-    const bool px = L.bc.lo[0] == BCP, py = L.bc.lo[1] == BCP, pz = L.bc.lo[2] == BCP;
-
-    const float4 xc = ld4(x + row + i0);
-    const float4 bb = ld4s(b + row + i0);
-    // neighbour rows / planes (present: inside, or wrapped on a periodic axis)
-    const bool hym = j > 0 || py, hyp = j < ny - 1 || py;
-    const bool hzm = DIM == 3 && (k > 0 || pz), hzp = DIM == 3 && (k < nz - 1 || pz);
-    const size_t rym = j > 0 ? row - nx : row + (size_t)(ny - 1) * nx;
-    const size_t ryp = j < ny - 1 ? row + nx : row - (size_t)(ny - 1) * nx;
-    const size_t rzm = k > 0 ? row - plane : row + (size_t)(nz - 1) * plane;
-    const size_t rzp = k < nz - 1 ? row + plane : row - (size_t)(nz - 1) * plane;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 xym = hym ? ld4(x + rym + i0) : zero4;
-    const float4 xyp = hyp ? ld4(x + ryp + i0) : zero4;
-    const float4 xzm = hzm ? ld4(x + rzm + i0) : zero4;
-    const float4 xzp = hzp ? ld4(x + rzp + i0) : zero4;
-    // the cells of this colour are p0 and p0 + 2 (i0 is even)
-    const int p0 = (color + j + k) & 1;
-    // x-neighbour outside the quad: left of cell 0 (p0 == 0) or right of cell 3 (p0 == 1)
-    float xout = 0.f;
-    if (p0 == 0) {
-        if (i0 > 0) xout = x[row + i0 - 1];
-        else if (px) xout = x[row + nx - 1];
-    } else {
-        if (i0 + 4 < nx) xout = x[row + i0 + 4];
-        else if (px) xout = x[row];
-    }
-    // face coefficients: x-faces i0+p0 .. i0+p0+3; y-faces of rows j, j+1; z-faces of planes k, k+1
-    const size_t fxb = ((size_t)k * ny + j) * (nx + 1) + i0 + p0;
-    const float fx0 = __ldcs(L.bx + fxb), fx1 = __ldcs(L.bx + fxb + 1), fx2 = __ldcs(L.bx + fxb + 2),
-                fx3 = __ldcs(L.bx + fxb + 3);
-    const size_t fyb = ((size_t)k * (ny + 1) + j) * nx + i0;
-    const float4 fyl = ld4s(L.by + fyb), fyh = ld4s(L.by + fyb + nx);
-    float4 fzl = zero4, fzh = zero4;
-    if (DIM == 3) {
-        fzl = ld4s(L.bz + row + i0);
-        fzh = ld4s(L.bz + row + plane + i0);
-    }
-
-    auto update = [&](int p, float bxl, float bxh, float xl, float xh) -> float {
-        const int i = i0 + p;
-        float off = 0.f, dg = 0.f;
-        if (i > 0 || px) { off = fmadd(bxl, xl, off); dg += bxl; }
-        else if (L.bc.lo[0] == BCD) { dg += 2.f * bxl; }
-        if (i < nx - 1 || px) { off = fmadd(bxh, xh, off); dg += bxh; }
-        else if (L.bc.hi[0] == BCD) { dg += 2.f * bxh; }
-        const float byl = el(fyl, p), byh = el(fyh, p);
-        if (hym) { off = fmadd(byl, el(xym, p), off); dg += byl; }
-        else if (L.bc.lo[1] == BCD) { dg += 2.f * byl; }
-        if (hyp) { off = fmadd(byh, el(xyp, p), off); dg += byh; }
-        else if (L.bc.hi[1] == BCD) { dg += 2.f * byh; }
-        if (DIM == 3) {
-            const float bzl = el(fzl, p), bzh = el(fzh, p);
-            if (hzm) { off = fmadd(bzl, el(xzm, p), off); dg += bzl; }
-            else if (L.bc.lo[2] == BCD) { dg += 2.f * bzl; }
-            if (hzp) { off = fmadd(bzh, el(xzp, p), off); dg += bzh; }
-            else if (L.bc.hi[2] == BCD) { dg += 2.f * bzh; }
-        }
-        return (off - el(bb, p)) * recip(dg);
-    };
-    // quads away from every non-periodic boundary: the same operations in the
-    // same order, without the per-face presence tests
-    const bool inner = hym && hyp && (DIM == 2 || (hzm && hzp)) && (px || (i0 > 0 && i0 + 4 < nx));
-    auto update_in = [&](int p, float bxl, float bxh, float xl, float xh) -> float {
-        float off = 0.f, dg = 0.f;
-        off = fmadd(bxl, xl, off); dg += bxl;
-        off = fmadd(bxh, xh, off); dg += bxh;
-        const float byl = el(fyl, p), byh = el(fyh, p);
-        off = fmadd(byl, el(xym, p), off); dg += byl;
-        off = fmadd(byh, el(xyp, p), off); dg += byh;
-        if (DIM == 3) {
-            const float bzl = el(fzl, p), bzh = el(fzh, p);
-            off = fmadd(bzl, el(xzm, p), off); dg += bzl;
-            off = fmadd(bzh, el(xzp, p), off); dg += bzh;
-        }
-        return (off - el(bb, p)) * recip(dg);
-    };
-    float4 out = xc;
-    if (inner) {
-        if (p0 == 0) {
-            out.x = update_in(0, fx0, fx1, xout, xc.y);
-            out.z = update_in(2, fx2, fx3, xc.y, xc.w);
-        } else {
-            out.y = update_in(1, fx0, fx1, xc.x, xc.z);
-            out.w = update_in(3, fx2, fx3, xc.z, xout);
-        }
-    } else if (p0 == 0) {
-        out.x = update(0, fx0, fx1, xout, xc.y);
-        out.z = update(2, fx2, fx3, xc.y, xc.w);
-    } else {
-        out.y = update(1, fx0, fx1, xc.x, xc.z);
-        out.w = update(3, fx2, fx3, xc.z, xout);
-    }
-    *reinterpret_cast<float4*>(x + row + i0) = out;
+    if (4 * q >= L.nx || j >= L.ny) return;
+    gsrb4_quad<DIM, false>(L, x, b, color, q, j, k, false);
 }
 
 bool cell_gsrb_v4_ok(int dim, const CellLevel<float>& L, const float* x, const float* b)
@@ -304,40 +207,7 @@ k_prolong_add_v4(CellLevel<float> F, CellLevel<float> C, float* __restrict__ xf,
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (4 * q >= F.nx || j >= F.ny) return;
-    const int i0 = 4 * q, c0 = 2 * q;
-    const Lin1D l0 = lin1d(i0, C.nx, F.bc.lo[0], F.bc.hi[0]);       // p = c0, q: left neighbour
-    const Lin1D l3 = lin1d(i0 + 3, C.nx, F.bc.lo[0], F.bc.hi[0]);   // p = c0 + 1, q: right neighbour
-    const Lin1D ly = lin1d(j, C.ny, F.bc.lo[1], F.bc.hi[1]);
-    const Lin1D lz = lin1d(k, C.nz, F.bc.lo[2], F.bc.hi[2]);
-    const float w1 = 0.75f, w2 = 0.25f;
-    const float a0 = w2 * l0.sq, a3 = w2 * l3.sq, ay = w2 * ly.sq, az = w2 * lz.sq;
-    // prolong_value's lo / hi of one coarse row for the four cells
-    auto xint = [&](int cb, int cc, float (&o)[4]) {
-        const float* r = xc + ((size_t)cc * C.ny + cb) * C.nx;
-        const float2 m = *reinterpret_cast<const float2*>(r + c0);
-        const float vl = r[l0.q], vr = r[l3.q];
-        o[0] = fmadd(a0, vl, w1 * m.x);   // cell i0:     P = c0,     Q = l0.q
-        o[1] = fmadd(w2, m.y, w1 * m.x);  // cell i0 + 1: P = c0,     Q = c0 + 1
-        o[2] = fmadd(w2, m.x, w1 * m.y);  // cell i0 + 2: P = c0 + 1, Q = c0
-        o[3] = fmadd(a3, vr, w1 * m.y);   // cell i0 + 3: P = c0 + 1, Q = l3.q
-    };
-    float pl[2][4];   // prolong_value's plane(lz.p), plane(lz.q)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int cc = e ? lz.q : lz.p;
-        float lo[4], hi[4];
-        xint(ly.p, cc, lo);
-        xint(ly.q, cc, hi);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) pl[e][p] = fmadd(ay, hi[p], w1 * lo[p]);
-    }
-    float* px = xf + ((size_t)k * F.ny + j) * F.nx + i0;
-    float4 v = *reinterpret_cast<const float4*>(px);
-    v.x += fmadd(az, pl[1][0], w1 * pl[0][0]);
-    v.y += fmadd(az, pl[1][1], w1 * pl[0][1]);
-    v.z += fmadd(az, pl[1][2], w1 * pl[0][2]);
-    v.w += fmadd(az, pl[1][3], w1 * pl[0][3]);
-    *reinterpret_cast<float4*>(px) = v;
+    prolong4_quad<false>(F, C, xf, xc, q, j, k);
 }
 
 bool cell_prolong_v4_ok(int dim, const CellLevel<float>& F, const float* xf, const float* xc)

@@ -114,6 +114,37 @@ bool cell_gsrb_tma_ok(int dim, const CellLevel<float>& L, const float* xin, cons
 bool cell_gsrb_tma_fits(int nx);
 void cell_gsrb_tma(const CellLevel<float>& L, const float* xin, float* xout, const float* b, int* err,
                    cudaStream_t s);
+// The down leg (nu1 sweeps, residual, restriction) or the up leg (linear
+// prolongation, nu2 sweeps) of a cell V-cycle on a 3-D FP32 level as one
+// persistent launch whose passes are pipelined through L2 (mg_cellpipe.cu);
+// same results as the pass-by-pass kernels.  S: per-handle ticket / exit /
+// epoch counters (3 words) and cell_pipe_flag_words() item flags, zeroed once
+// at setup; S.err is set if a bounded wait gave up.
+enum { PIPE_RED = 0, PIPE_BLACK = 1, PIPE_RESTRICT = 2, PIPE_PROLONG = 3 };
+constexpr int kPipeBand = 8;       // fine rows per work item
+constexpr int kPipeZ = 2;          // planes per step
+constexpr int kPipeMaxNu = 4;      // sweeps per leg
+constexpr int kPipeMaxPass = 2 * kPipeMaxNu + 1;
+constexpr size_t kPipeMinCells = (size_t)1 << 14;   // finest levels of 2^14 cells and more
+constexpr int kPipeK = 3;          // slots between a pass and the next one (steps in flight)
+struct CellPipe {
+    int npass, Z, nband, nstep, zero_first, yper, K, nslot;
+    int op[kPipeMaxPass];
+    int lag[kPipeMaxPass];
+    int dep[kPipeMaxPass];
+};
+struct PipeSync {
+    unsigned* ctr;
+    unsigned* flags;
+    int* err;
+};
+bool cell_pipe_ok(const CellLevel<float>& F, const float* x, const float* b);
+int cell_pipe_grid();   // resident CTAs of the pipelined kernel (first call: outside stream capture)
+size_t cell_pipe_flag_words(int ny, int nz, int nu_max);
+void cell_pipe_down(const CellLevel<float>& F, float* x, const float* b, float* bc, int nu1, bool zero_first,
+                    const PipeSync& S, cudaStream_t s);
+void cell_pipe_up(const CellLevel<float>& F, const CellLevel<float>& C, float* x, const float* b, const float* xc,
+                  int nu2, const PipeSync& S, cudaStream_t s);
 // 3-D residual + restriction, vectorised like cell_gsrb_v4; same results as cell_resid_restrict
 bool cell_resid_restrict_v4_ok(int dim, const CellLevel<float>& F, const float* x, const float* b, const float* bc);
 void cell_resid_restrict_v4(const CellLevel<float>& F, const float* x, const float* b, float* bc, cudaStream_t s);

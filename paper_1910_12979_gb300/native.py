@@ -23,6 +23,7 @@ MG_FLAG_SWEEP_PIPE = 4
 MG_FLAG_AUTOTUNE = 8
 MG_FLAG_ZERO_GUESS = 16
 MG_FLAG_SWEEP_TMA = 32
+MG_FLAG_CELL_PIPE = 64
 
 BC = {"periodic": MG_BC_PERIODIC, "neumann": MG_BC_NEUMANN, "dirichlet": MG_BC_DIRICHLET}
 
@@ -84,6 +85,10 @@ SIGNATURES = [
     ("mg_solve_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                       ctypes.POINTER(mg_stats)]),
+    ("mg_project_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(mg_beta0), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                        ctypes.POINTER(mg_stats)]),
     ("mg_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("mg_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("mg_destroy", None, [ctypes.c_void_p]),
@@ -114,10 +119,11 @@ SIGNATURES = [
 ]
 
 MG_PROF_CELL_SMOOTH_FINE, MG_PROF_RESID64, MG_PROF_NODE_SMOOTH_FINE, MG_PROF_CELL_RESTRICT_FINE, \
-    MG_PROF_NODE_RESID64 = range(5)
+    MG_PROF_NODE_RESID64, MG_PROF_CELL_PIPE_DOWN, MG_PROF_CELL_PIPE_UP = range(7)
 PROF_NAMES = {MG_PROF_CELL_SMOOTH_FINE: "cell_smooth_fine", MG_PROF_RESID64: "cell_resid64",
               MG_PROF_NODE_SMOOTH_FINE: "node_smooth_fine", MG_PROF_CELL_RESTRICT_FINE: "cell_restrict_fine",
-              MG_PROF_NODE_RESID64: "node_resid64"}
+              MG_PROF_NODE_RESID64: "node_resid64", MG_PROF_CELL_PIPE_DOWN: "cell_pipe_down",
+              MG_PROF_CELL_PIPE_UP: "cell_pipe_up"}
 # kernel classes bound by the FP64 pipe rather than by HBM
 PROF_FP64_BOUND = {"cell_resid64", "node_resid64"}
 
@@ -230,6 +236,21 @@ def mg_solve_batch(handles, rhs_ptrs, phi_ptrs, tols, allow=(MG_OK,)):
     st = (mg_stats * n)()
     rc = load().mg_solve_batch(H, R, P, T, n, st)
     check(rc, "mg_solve_batch", allow)
+    return list(st)
+
+
+def mg_project_batch(handles, U_ptrs, beta0s, S_ptrs, phi_ptrs, tols, allow=(MG_OK,)):
+    """U_ptrs: per entry a list of 3 device pointers (None for absent components)."""
+    n = len(handles)
+    P = ctypes.c_void_p
+    hs = (P * n)(*[h.value for h in handles])
+    U = (P * (3 * n))(*[u for e in U_ptrs for u in (list(e) + [None] * (3 - len(e)))])
+    b0 = (mg_beta0 * n)(*beta0s)
+    S = (P * n)(*S_ptrs)
+    ph = (P * n)(*phi_ptrs) if phi_ptrs is not None else None
+    tl = (ctypes.c_double * n)(*tols)
+    st = (mg_stats * n)()
+    check(load().mg_project_batch(hs, U, b0, S, ph, tl, n, st), "mg_project_batch", allow)
     return list(st)
 
 

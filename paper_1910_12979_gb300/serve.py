@@ -7,9 +7,12 @@ A request uses an idle slot of its size, or a new slot when the device-memory
 budget still has room for one, or -- when the budget is full -- the space of the
 least recently used idle slot of another size, which is evicted.  Otherwise it
 waits in FIFO order.  Admitted solves run on their slot's stream from a worker
-thread (the library call releases the GIL and synchronises only that stream),
+thread (the library call releases the GIL and synchronises only those streams),
 so requests arriving while others are on the GPU are admitted as slots and
-memory free up, and their kernels overlap on the device.
+memory free up, and their kernels overlap on the device.  Requests admitted
+together (several were waiting when a slot freed up, or arrived together) are
+run as one batch when the backend offers ``run_batch``: on the GPU their
+elliptic solves share one graph launch (mg_project_batch).
 
 The scheduling core (``Scheduler``) holds no CUDA state: it is driven by a
 ``backend`` object that creates slots, reports their size in bytes and runs a
@@ -74,6 +77,7 @@ class Scheduler:
         self.evictions = 0
         self.created = 0
         self.errors = []
+        self.batches = []   # size of every group of requests started together
 
     # -- bookkeeping (called with the lock held) --------------------------------
     def used_bytes(self):
@@ -140,7 +144,35 @@ class Scheduler:
             self.lock.notify_all()
         self._start(started)
 
+    def _batch_worker(self, started):
+        try:
+            outs = self.backend.run_batch([slot.state for slot, _ in started], [req for _, req in started])
+            for (_, req), (res, st) in zip(started, outs):
+                req.result, req.status = res, st
+        except Exception as e:  # the batch fails as a whole; the rest of the stream continues
+            for _, req in started:
+                req.status = e
+                self.errors.append((req.rid, repr(e)))
+        with self.lock:
+            now = self.clock() - self.t0
+            for slot, req in started:
+                req.finished = now
+                slot.busy = False
+                slot.last_used = now
+                self.inflight -= 1
+                self.done.append(req)
+            nxt = self._admit()
+            self.lock.notify_all()
+        self._start(nxt)
+
     def _start(self, started):
+        if not started:
+            return
+        with self.lock:
+            self.batches.append(len(started))
+        if len(started) > 1 and getattr(self.backend, "run_batch", None) is not None:
+            threading.Thread(target=self._batch_worker, args=(started,), daemon=True).start()
+            return
         for slot, req in started:
             threading.Thread(target=self._worker, args=(slot, req), daemon=True).start()
 
@@ -188,16 +220,22 @@ def latency_stats(reqs):
 class GpuBackend:
     """Slots are mixed-precision MAC projection hierarchies on their own streams.
 
-    problems: dict n -> list of device-resident problems (dicts of tensors from
-    ``device_problem``); a request's payload is (n, index into that list).
+    problems: dict n -> list of host-resident problems (pinned tensors, from
+    ``host_problem``); a request's payload is (n, index into that list).  Every
+    request uploads its problem (sigma, beta0 at cells and faces, S, U) from
+    pinned host memory on its slot's stream, rebuilds the hierarchy's
+    coefficients from that sigma, projects, and reads the projected velocity
+    back into the slot's pinned host buffers, so its latency includes both
+    transfers.  ``run_batch`` runs several requests with their solves in one
+    graph launch (mg_project_batch).
     """
 
     def __init__(self, problems, device="cuda:0", tol=1e-10, prec="mixed"):
         import torch
 
         from . import native as N
-        from .solver import ProjectionSolver
-        self.torch, self.N, self.ProjectionSolver = torch, N, ProjectionSolver
+        from .solver import ProjectionSolver, project_batch
+        self.torch, self.N, self.ProjectionSolver, self.project_batch = torch, N, ProjectionSolver, project_batch
         self.problems = problems
         self.device = torch.device(device)
         self.tol = tol
@@ -213,7 +251,8 @@ class GpuBackend:
             opt = N.mg_default_options()
             opt.prec = N.MG_PREC_MIXED if self.prec == "mixed" else N.MG_PREC_FP64
             hier = N.mg_hierarchy_bytes(g, bc, opt)
-            work = 8 * (3 * (n + 1) * n * n + n ** 3)   # U faces and phi of the slot
+            # device inputs (sigma, beta0, S on cells; beta0 and U on faces) and phi
+            work = 8 * (6 * (n + 1) * n * n + 4 * n ** 3)
             self._bytes[n] = hier + work
         return self._bytes[n]
 
@@ -221,37 +260,65 @@ class GpuBackend:
         torch = self.torch
         p0 = self.problems[n][0]
         stream = torch.cuda.Stream(device=self.device)
+        dev = lambda t: torch.empty(t.shape, dtype=t.dtype, device=self.device)
         with torch.cuda.stream(stream):
-            solver = self.ProjectionSolver(p0["geom"], p0["sigma"], loc="cell", prec=self.prec, stream=stream,
+            d = {"sigma": dev(p0["sigma"]), "beta0": dev(p0["beta0"]), "S": dev(p0["S"]),
+                 "beta0_face": [dev(b) for b in p0["beta0_face"]], "U": [dev(u) for u in p0["U"]]}
+            d["sigma"].copy_(p0["sigma"], non_blocking=True)
+            solver = self.ProjectionSolver(p0["geom"], d["sigma"], loc="cell", prec=self.prec, stream=stream,
                                            flags=self.N.MG_FLAG_ZERO_GUESS | self.N.MG_FLAG_AUTOTUNE)
-            U = [torch.empty_like(u) for u in p0["U"]]
-            phi = torch.empty_like(p0["sigma"])
+            phi = torch.empty_like(d["sigma"])
+        host_U = [torch.empty(u.shape, dtype=u.dtype).pin_memory() for u in p0["U"]]
         stream.synchronize()
-        return {"solver": solver, "stream": stream, "U": U, "phi": phi}
+        return {"solver": solver, "stream": stream, "d": d, "phi": phi, "host_U": host_U}
 
     def free_slot(self, state):
         state["solver"].close()
 
-    def run(self, state, req):
+    def _stage(self, state, req):
+        """Upload the request's problem and rebuild the coefficients (asynchronous)."""
         torch = self.torch
         n, k = req.payload
-        p = self.problems[n][k]
-        s = state["solver"]
+        p, d = self.problems[n][k], state["d"]
         with torch.cuda.stream(state["stream"]):
-            s.update_coeff(p["sigma"])
-            for a, b in zip(state["U"], p["U"]):
-                a.copy_(b)
-            st = s.project(state["U"], p["beta0"], p["S"], beta0_face=p["beta0_face"], phi=state["phi"],
-                           tol=self.tol, allow_not_converged=True)
-            out = [u.clone() for u in state["U"]] if req.keep else None
+            for name in ("sigma", "beta0", "S"):
+                d[name].copy_(p[name], non_blocking=True)
+            for a, b in zip(d["beta0_face"] + d["U"], p["beta0_face"] + p["U"]):
+                a.copy_(b, non_blocking=True)
+            state["solver"].update_coeff(d["sigma"])
+
+    def _finish(self, state, req):
+        """Read the projected velocity back to the slot's pinned host buffers."""
+        torch = self.torch
+        with torch.cuda.stream(state["stream"]):
+            for h, u in zip(state["host_U"], state["d"]["U"]):
+                h.copy_(u, non_blocking=True)
         state["stream"].synchronize()
-        return out, st
+        return [h.clone() for h in state["host_U"]] if req.keep else None
+
+    def run(self, state, req):
+        self._stage(state, req)
+        d = state["d"]
+        with self.torch.cuda.stream(state["stream"]):
+            st = state["solver"].project(d["U"], d["beta0"], d["S"], beta0_face=d["beta0_face"], phi=state["phi"],
+                                         tol=self.tol, allow_not_converged=True)
+        return self._finish(state, req), st
+
+    def run_batch(self, states, reqs):
+        for st_, req in zip(states, reqs):
+            self._stage(st_, req)
+        ds = [s["d"] for s in states]
+        sts = self.project_batch([s["solver"] for s in states], [d["U"] for d in ds], [d["beta0"] for d in ds],
+                                 [d["S"] for d in ds], beta0_face=[d["beta0_face"] for d in ds],
+                                 phi=[s["phi"] for s in states], tols=[self.tol] * len(states),
+                                 allow_not_converged=True)
+        return [(self._finish(s, r), st) for s, r, st in zip(states, reqs, sts)]
 
 
-def device_problem(p, device):
-    """Move one generated problem (inputs.polytrope_star / stratified) to the device."""
+def host_problem(p):
+    """One generated problem (inputs.polytrope_star / stratified) in pinned host memory."""
     import torch
-    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     return {"geom": p["geom"], "sigma": T(p["sigma"]), "beta0": T(p["beta0"]), "S": T(p["S"]),
             "beta0_face": [T(b) for b in p["beta0_face"]], "U": [T(u) for u in p["U_mac"]]}
 

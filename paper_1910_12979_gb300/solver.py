@@ -165,6 +165,26 @@ def solve_batch(solvers, rhs, phi, tols, allow_not_converged=False):
     return [s.as_dict() for s in st]
 
 
+def project_batch(solvers, U, beta0_cell, S, beta0_face=None, phi=None, tols=None, allow_not_converged=False):
+    """mg_project_batch: one projection per solver (U[i]: its velocity components,
+    updated in place; beta0_cell[i], S[i]; beta0_face[i] for MAC solvers; phi[i]
+    or None), the solves as one graph launch.  Returns the statistics."""
+    n = len(solvers)
+    faces = beta0_face if beta0_face is not None else [None] * n
+    phis = phi if phi is not None else [None] * n
+    tols = tols if tols is not None else [1e-10] * n
+    Up, b0s, Sp, pp = [], [], [], []
+    for s, u, bc, sv, bf, ph in zip(solvers, U, beta0_cell, S, faces, phis):
+        shp = (lambda d: s.face_shape(d)) if s.loc == "cell" else (lambda d: s.cell_shape)
+        Up.append([_ptr(u[d], f"U[{d}]", shp(d)) for d in range(s.dim)])
+        b0s.append(s._beta0(bc, bf))
+        Sp.append(_ptr(sv, "S", s.cell_shape))
+        pp.append(_ptr(ph, "phi", s.vec_shape) if ph is not None else None)
+    allow = (N.MG_OK, N.MG_ERR_NOT_CONVERGED) if allow_not_converged else (N.MG_OK,)
+    st = N.mg_project_batch([s.handle for s in solvers], Up, b0s, Sp, pp, tols, allow)
+    return [x.as_dict() for x in st]
+
+
 def time_step(mac, nodal, U, Unew, Uadv, beta0_cell, beta0_face, S, dt, omega=None, center=None, centrifugal=False,
               tol=1e-10, allow_not_converged=False):
     """mg_step: face velocities, MAC projection, advection (+ rotation), nodal

@@ -27,7 +27,10 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
     assert d["config"]["workload"].startswith("stratified atmosphere 256^3")
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 2e3 / d["value"]) <= 1e-6 * d["ms_per_step"]
+    # ms_per_step is the measured time of one sample step (what the run spent); value is the
+    # workload-size throughput, the sample scaled by the cell-count ratio 512
+    assert d["value"] > 0 and abs(d["ms_per_step_at_workload_size"] - 2e3 / d["value"]) <= 1e-6 * d["ms_per_step"]
+    assert abs(d["ms_per_step_at_workload_size"] - 512 * d["ms_per_step"]) <= 1e-6 * d["ms_per_step_at_workload_size"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["unit"] == d["unit"]
     assert "32^3" in cb["sample"]

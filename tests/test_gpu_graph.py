@@ -3,7 +3,8 @@
 The graph path makes the convergence decisions on the device with the same
 formulas as the host loop (MG_FLAG_NO_GRAPH), so both must return the same phi
 bit for bit after the same number of iterations.  mg_solve_batch runs every
-solve as a branch of one graph; each branch must equal the solve run alone.
+solve as a branch of one graph, and mg_project_batch every projection's solve;
+each branch must equal the solve (or projection) run alone.
 """
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_1910_12979_gb300 import ProjectionSolver, solve_batch  # noqa: E402
+from paper_1910_12979_gb300 import ProjectionSolver, project_batch, solve_batch  # noqa: E402
 from paper_1910_12979_gb300 import native as N  # noqa: E402
 
 DEV = "cuda:0"
@@ -149,3 +150,46 @@ def test_graph_launch_count_matches_host_loop(loc):
     assert vg == vh and ig == ih
     # a check kernel and two condition kernels per refinement step, a few per solve
     assert abs(g - h) <= 4 * (ih + 1) + 12, (g, h)
+
+
+def test_project_batch_equals_alone(oracle):
+    """mg_project_batch: MAC and nodal projections of uneven sizes and both
+    precisions, their solves as one graph launch, give the same projected
+    velocities and statistics as each projection alone; the 48^3 MAC entry is
+    also checked against the oracle's projection."""
+    specs = [(32, "cell", "mixed"), (48, "cell", "mixed"), (24, "nodal", "mixed"), (32, "cell", "fp64"),
+             (16, "nodal", "fp64")]
+    probs, solvers = [], []
+    for i, (n, loc, prec) in enumerate(specs):
+        p = I.stratified(n, seed=60 + i, contrast=10.0 ** (1 + i % 3))
+        probs.append(p)
+        solvers.append(ProjectionSolver(p["geom"], T(p["sigma"]), loc=loc, prec=prec))
+
+    def inputs(p, loc):
+        U = [T(u) for u in (p["U_mac"] if loc == "cell" else p["U_cell"])]
+        return U, T(p["beta0"]), T(p["S"]), ([T(b) for b in p["beta0_face"]] if loc == "cell" else None)
+
+    alone = []
+    for (n, loc, prec), p, s in zip(specs, probs, solvers):
+        U, b0, S, bf = inputs(p, loc)
+        st = s.project(U, b0, S, beta0_face=bf, tol=1e-11)
+        alone.append((U, st))
+    for _ in range(2):   # the second call replays the cached batch graph
+        ins = [inputs(p, loc) for (n, loc, prec), p in zip(specs, probs)]
+        st = project_batch(solvers, [x[0] for x in ins], [x[1] for x in ins], [x[2] for x in ins],
+                           beta0_face=[x[3] for x in ins], tols=[1e-11] * len(specs))
+        for (Ua, sa), x, sb in zip(alone, ins, st):
+            assert sb["status"] == N.MG_OK and sb["iters"] == sa["iters"]
+            assert sb["rel_constraint"] == sa["rel_constraint"]
+            for a, b in zip(Ua, x[0]):
+                assert torch.equal(a, b)
+    O = oracle
+    p = probs[1]
+    g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+    ref = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=1e-13)
+    U = ins[1][0]
+    num = np.sqrt(sum(np.sum((u.cpu().numpy() - r) ** 2) for u, r in zip(U, ref["U"])))
+    den = np.sqrt(sum(np.sum(r ** 2) for r in ref["U"]))
+    assert num / den <= 1e-8
+    for s in solvers:
+        s.close()

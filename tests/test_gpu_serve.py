@@ -1,11 +1,13 @@
 """Serving on the GPU: every request's result is the same in the mix as alone.
 
-Requests of three grid sizes arrive together and are admitted into resident
-hierarchies that run concurrently on their own streams; the projected
-velocities must equal, bit for bit, those of the same problems each solved
-alone on a fresh solver (the kernels' arithmetic does not depend on what else
-runs on the device).  The post-projection constraint of each request is also
-checked against the oracle's definition of D(beta0 U) - beta0 S.
+Requests of three grid sizes arrive together: their problems are uploaded from
+pinned host memory into resident hierarchies on their own streams, the requests
+admitted together run as one batch (their solves in one graph launch), and the
+projected velocities come back to pinned host memory.  They must equal, bit for
+bit, those of the same problems each projected alone on a fresh solver (the
+kernels' arithmetic does not depend on what else runs on the device).  The
+post-projection constraint of each request is also checked against the
+oracle's definition of D(beta0 U) - beta0 S.
 """
 import numpy as np
 import pytest
@@ -19,13 +21,13 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_1910_12979_gb300 import ProjectionSolver  # noqa: E402
-from paper_1910_12979_gb300.serve import GpuBackend, Request, Scheduler, device_problem, latency_stats  # noqa: E402
+from paper_1910_12979_gb300.serve import GpuBackend, Request, Scheduler, host_problem, latency_stats  # noqa: E402
 
 
 def test_alone_equals_mix(oracle):
     dev = "cuda:0"
     sizes = (32, 48, 64)
-    problems = {n: [device_problem(I.polytrope_star(n, seed=50 + 3 * n + k), dev) for k in range(2)] for n in sizes}
+    problems = {n: [host_problem(I.polytrope_star(n, seed=50 + 3 * n + k)) for k in range(2)] for n in sizes}
     order = [32, 64, 48, 32, 64, 48, 48, 32, 64, 32]
     reqs = [Request(i, n, 0.0, (n, i % 2), keep=True) for i, n in enumerate(order)]
     be = GpuBackend(problems, device=dev, tol=1e-11)
@@ -34,16 +36,18 @@ def test_alone_equals_mix(oracle):
     assert all(not isinstance(r.status, Exception) for r in done)
     st = latency_stats(done)
     assert st["count"] == len(order)
+    assert max(sch.batches) > 1      # requests admitted together ran as a batch
     sch.close()
+    D = lambda t: t.to(dev)
     for r in done:
         n, k = r.payload
         p = problems[n][k]
-        s = ProjectionSolver(p["geom"], p["sigma"], loc="cell", prec="mixed")
-        U = [u.clone() for u in p["U"]]
-        phi = torch.zeros_like(p["sigma"])
-        s.project(U, p["beta0"], p["S"], beta0_face=p["beta0_face"], phi=phi, tol=1e-11)
+        s = ProjectionSolver(p["geom"], D(p["sigma"]), loc="cell", prec="mixed")
+        U = [D(u) for u in p["U"]]
+        phi = torch.zeros(s.vec_shape, dtype=torch.float64, device=dev)
+        s.project(U, D(p["beta0"]), D(p["S"]), beta0_face=[D(b) for b in p["beta0_face"]], phi=phi, tol=1e-11)
         for a, b in zip(U, r.result):
-            assert torch.equal(a, b), (r.rid, n)
+            assert torch.equal(a.cpu(), b), (r.rid, n)
         s.close()
     # one projected field checked with the oracle's own divergence
     O = oracle

@@ -66,7 +66,7 @@ constexpr int kPipeRQ = 128;                           // quads per restriction 
 
 static_assert(kPipeBand == 8, "the item loops below take a band of 8 rows");
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 k_cell_pipe(CellLevel<float> F, float* __restrict__ x, const float* __restrict__ b, CellLevel<float> C,
             float* __restrict__ bc, const float* __restrict__ xc, CellPipe P, PipeSync S)
 {
@@ -168,19 +168,7 @@ k_cell_pipe(CellLevel<float> F, float* __restrict__ x, const float* __restrict__
                             for (int q = lane; q < nq; q += 32) prolong4_quad<true>(F, C, x, xc, q, j, kk);
                             continue;
                         }
-                        // two quads 32 apart per lane: both are loaded before either is
-                        // written (neither reads a cell of the other), so their load
-                        // latencies overlap
-                        for (int q = lane; q < nq; q += 64) {
-                            const bool two = q + 32 < nq;
-                            Gs4 ga, gb;
-                            gs4_load<3, true>(F, x, b, op, q, j, kk, zx, ga);
-                            if (two) gs4_load<3, true>(F, x, b, op, q + 32, j, kk, zx, gb);
-                            *reinterpret_cast<float4*>(quad_ptr(F, x, q, j, kk)) = gs4_value<3>(F, op, q, j, kk, ga);
-                            if (two)
-                                *reinterpret_cast<float4*>(quad_ptr(F, x, q + 32, j, kk)) =
-                                    gs4_value<3>(F, op, q + 32, j, kk, gb);
-                        }
+                        for (int q = lane; q < nq; q += 32) gsrb4_quad<3, true>(F, x, b, op, q, j, kk, zx);
                     }
                 }
             }

@@ -171,9 +171,38 @@ def oracle_cpu_leg(n_full, n_small=48, n_large=128, seed=3, tol=1e-10):
             fn = O.nodal_rhs(g, p["beta0"], p["U_cell"], p["S"])
             phn, _ = O.nodal_solve_mg(g, p["sigma"], fn, tol=1e-13, phi0=b["phi"])
             ref = {"p": p, "g": g, "mac_phi": phm, "nodal_phi": phn, "live": ~g.dirichlet_node_mask()}
+    # the all-core build of the oracle (colour-ordered smoothers, OpenMP loops): its result must
+    # not depend on the thread count (checked at n_small^3), then it is timed at n_large^3
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    par = None
+    try:
+        p = I.stratified(n_small, seed=seed, contrast=1e3)
+        g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+        outs = []
+        for th in (1, cores):
+            with O.all_cores(th):
+                a = O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=tol)
+                b = O.nodal_project(g, p["sigma"], p["beta0"], p["U_cell"], p["S"], tol=tol)
+            outs.append((a["phi"], b["phi"]))
+        same = bool(all((x == y).all() for x, y in zip(outs[0], outs[1])))
+        p = I.stratified(n_large, seed=seed, contrast=1e3)
+        g = O.Grid.make(p["geom"]["n"], p["geom"]["bclo"], p["geom"]["bchi"])
+        with O.all_cores(cores):
+            t0 = time.perf_counter()
+            O.mac_project(g, p["sigma"], p["beta0"], p["beta0_face"], p["U_mac"], p["S"], tol=tol)
+            O.nodal_project(g, p["sigma"], p["beta0"], p["U_cell"], p["S"], tol=tol)
+            tp = time.perf_counter() - t0
+        par = {"value": 2.0 / (tp * (n_full / n_large) ** 3), "unit": UNIT, "cores": cores,
+               "kind": "oracle, all cores (colour-ordered Gauss-Seidel, OpenMP)",
+               "sample": f"one MAC + nodal projection at {n_large}^3 ({tp:.1f} s, measured) scaled by "
+                         f"{(n_full / n_large) ** 3:.0f} to {n_full}^3",
+               "bitwise_equal_1_vs_all_threads": same}
+    except Exception as e:  # no OpenMP toolchain on this host: report why
+        par = {"unavailable": repr(e)[:200]}
     scale = (n_full / n_large) ** 3
     per_cell = {n: times[n] / n ** 3 for n in times}
     base = {"value": 2.0 / (times[n_large] * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "all_cores": par,
             "sample": f"one full MAC + nodal oracle projection of the same recipe at {n_large}^3 "
                       f"({times[n_large]:.1f} s, measured) scaled by the cell-count ratio {scale:.0f} to "
                       f"{n_full}^3; at {n_small}^3 it took {times[n_small]:.2f} s: "

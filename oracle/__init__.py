@@ -3,7 +3,9 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import this package.  It wraps
 ``mg_oracle.c`` (plain C, compiled with gcc) through ctypes and shares no code
-with the CUDA library.
+with the CUDA library.  ``all_cores(threads)`` switches the calls inside it to
+``mg_oracle_omp.c``, the same source built with colour-ordered smoothers and
+OpenMP loops: the benchmark's all-core CPU baseline, never used for parity.
 
 Arrays are numpy float64, C order, always 3-D shaped (nz, ny, nx) with nz = 1
 for 2-D problems:
@@ -35,6 +37,10 @@ _LIB = os.path.join(_HERE, "_build", "liborc.so")
 BC_CODES = {"periodic": 0, "neumann": 1, "dirichlet": 2}
 
 
+_SRC_OMP = os.path.join(_HERE, "mg_oracle_omp.c")
+_LIB_OMP = os.path.join(_HERE, "_build", "liborc_omp.so")
+
+
 def build(force: bool = False) -> str:
     """Compile mg_oracle.c into oracle/_build/liborc.so (plain gcc, no -march)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
@@ -43,6 +49,20 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile the all-core CPU baseline (mg_oracle_omp.c: this oracle with
+    colour-ordered smoothers and OpenMP loops) into oracle/_build/liborc_omp.so.
+    Timing only: the parity tests never use it."""
+    os.makedirs(os.path.dirname(_LIB_OMP), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_OMP))
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < newest:
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC_OMP,
+                               "-lm"])
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
 
 
 class _Grid(ctypes.Structure):
@@ -56,19 +76,49 @@ class _Stats(ctypes.Structure):
 
 
 _lib = None
+_lib_omp = None
+_use_omp = False
 
 
 def _L():
-    global _lib
+    global _lib, _lib_omp
+    if _use_omp:
+        if _lib_omp is None:
+            _lib_omp = _declare(ctypes.CDLL(build_omp()))
+        return _lib_omp
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        for name in ("orc_mac_faces", "orc_mac_apply", "orc_mac_div", "orc_mac_rhs", "orc_mac_grad_update",
-                     "orc_mac_solve_dense", "orc_mac_solve_mg", "orc_mac_project", "orc_nodal_apply",
-                     "orc_nodal_div", "orc_nodal_lump", "orc_nodal_grad", "orc_nodal_rhs",
-                     "orc_nodal_solve_dense", "orc_nodal_solve_mg", "orc_nodal_project", "orc_beta0_eq5",
-                     "orc_map_radial", "orc_rotation_forces", "orc_face_average", "orc_advect"):
-            getattr(_lib, name).restype = ctypes.c_int
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+class all_cores:
+    """Context: the oracle calls inside run on the all-core CPU-baseline build
+    (colour-ordered smoothers, OpenMP loops) with ``threads`` threads.  Timing
+    only; not for parity (another smoother, so other iteration counts)."""
+
+    def __init__(self, threads):
+        self.threads = int(threads)
+
+    def __enter__(self):
+        global _use_omp
+        _use_omp = True
+        _L().orc_omp_set_threads(self.threads)
+        return self
+
+    def __exit__(self, *exc):
+        global _use_omp
+        _use_omp = False
+        return False
+
+
+def _declare(lib):
+    for name in ("orc_mac_faces", "orc_mac_apply", "orc_mac_div", "orc_mac_rhs", "orc_mac_grad_update",
+                 "orc_mac_solve_dense", "orc_mac_solve_mg", "orc_mac_project", "orc_nodal_apply",
+                 "orc_nodal_div", "orc_nodal_lump", "orc_nodal_grad", "orc_nodal_rhs",
+                 "orc_nodal_solve_dense", "orc_nodal_solve_mg", "orc_nodal_project", "orc_beta0_eq5",
+                 "orc_map_radial", "orc_rotation_forces", "orc_face_average", "orc_advect"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
 
 
 @dataclass(frozen=True)

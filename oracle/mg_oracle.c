@@ -51,6 +51,18 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The CPU-baseline build (mg_oracle_omp.c) compiles this file with
+ * ORC_PARALLEL: loops whose iterations write only their own element run on
+ * OpenMP threads, and the multigrid smoothers are replaced by colour-ordered
+ * ones (declared below, defined there).  The oracle itself is built without
+ * it: ORC_PARALLEL_FOR is then empty and the smoothers are the lexicographic
+ * sweeps of this file. */
+#ifdef ORC_PARALLEL
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PARALLEL_FOR
+#endif
+
 enum { BC_PERIODIC = 0, BC_NEUMANN = 1, BC_DIRICHLET = 2 };
 
 typedef struct {
@@ -261,11 +273,13 @@ int orc_mac_apply(const orc_grid* g, const double* bx, const double* by, const d
                   const double* phi, double* out)
 {
     const double* B[3] = { bx, by, bz };
-    int c[3];
-    for (c[2] = 0; c[2] < g->n[2]; ++c[2])
-        for (c[1] = 0; c[1] < g->n[1]; ++c[1])
-            for (c[0] = 0; c[0] < g->n[0]; ++c[0])
+    ORC_PARALLEL_FOR
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                int c[3] = { i, j, k };
                 out[cell_index(g, c)] = mac_row(g, B, phi, c, NULL);
+            }
     return 0;
 }
 
@@ -558,17 +572,19 @@ static void mac_residual(const mac_level* L)
 {
     orc_mac_apply(&L->g, L->B[0], L->B[1], L->B[2], L->x, L->r);
     long N = ncells(&L->g);
+    ORC_PARALLEL_FOR
     for (long i = 0; i < N; ++i) L->r[i] = L->b[i] - L->r[i];
 }
 
 /* coarse b = mean of the 2^dim fine residuals */
 static void mac_restrict(const mac_level* F, mac_level* C)
 {
-    int c[3];
     int nch = 1 << C->g.dim;
-    for (c[2] = 0; c[2] < C->g.n[2]; ++c[2])
-        for (c[1] = 0; c[1] < C->g.n[1]; ++c[1])
-            for (c[0] = 0; c[0] < C->g.n[0]; ++c[0]) {
+    ORC_PARALLEL_FOR
+    for (int k = 0; k < C->g.n[2]; ++k)
+        for (int j = 0; j < C->g.n[1]; ++j)
+            for (int i = 0; i < C->g.n[0]; ++i) {
+                int c[3] = { i, j, k };
                 double s = 0.0;
                 for (int q = 0; q < nch; ++q) {
                     int fc[3] = { 2 * c[0] + (q & 1), 2 * c[1] + ((q >> 1) & 1),
@@ -582,14 +598,22 @@ static void mac_restrict(const mac_level* F, mac_level* C)
 /* fine x += coarse x, piecewise constant */
 static void mac_prolong(const mac_level* C, mac_level* F)
 {
-    int c[3];
-    for (c[2] = 0; c[2] < F->g.n[2]; ++c[2])
-        for (c[1] = 0; c[1] < F->g.n[1]; ++c[1])
-            for (c[0] = 0; c[0] < F->g.n[0]; ++c[0]) {
+    ORC_PARALLEL_FOR
+    for (int k = 0; k < F->g.n[2]; ++k)
+        for (int j = 0; j < F->g.n[1]; ++j)
+            for (int i = 0; i < F->g.n[0]; ++i) {
+                int c[3] = { i, j, k };
                 int cc[3] = { c[0] / 2, c[1] / 2, (F->g.dim == 3) ? c[2] / 2 : 0 };
                 F->x[cell_index(&F->g, c)] += C->x[cell_index(&C->g, cc)];
             }
 }
+
+#ifdef ORC_PARALLEL
+static void mac_gs_colour(const mac_level* L);   /* red-black sweep, mg_oracle_omp.c */
+#define ORC_MAC_SMOOTH mac_gs_colour
+#else
+#define ORC_MAC_SMOOTH mac_gs_lex
+#endif
 
 static void mac_vcycle(mac_mg* mg, int l)
 {
@@ -604,14 +628,14 @@ static void mac_vcycle(mac_mg* mg, int l)
         free(rhs);
         return;
     }
-    for (int s = 0; s < 2; ++s) mac_gs_lex(L);
+    for (int s = 0; s < 2; ++s) ORC_MAC_SMOOTH(L);
     mac_residual(L);
     mac_level* C = &mg->lev[l + 1];
     mac_restrict(L, C);
     memset(C->x, 0, sizeof(double) * ncells(&C->g));
     mac_vcycle(mg, l + 1);
     mac_prolong(C, L);
-    for (int s = 0; s < 2; ++s) mac_gs_lex(L);
+    for (int s = 0; s < 2; ++s) ORC_MAC_SMOOTH(L);
 }
 
 /* Multigrid solve to relative residual <= tol, or until the residual stops
@@ -799,11 +823,13 @@ static double nodal_row(const orc_grid* g, const double* sigma, const double* ph
 
 int orc_nodal_apply(const orc_grid* g, const double* sigma, const double* phi, double* out)
 {
-    int p[3];
-    for (p[2] = 0; p[2] < node_extent(g, 2); ++p[2])
-        for (p[1] = 0; p[1] < node_extent(g, 1); ++p[1])
-            for (p[0] = 0; p[0] < node_extent(g, 0); ++p[0])
+    ORC_PARALLEL_FOR
+    for (int k = 0; k < node_extent(g, 2); ++k)
+        for (int j = 0; j < node_extent(g, 1); ++j)
+            for (int i = 0; i < node_extent(g, 0); ++i) {
+                int p[3] = { i, j, k };
                 out[node_index(g, p)] = node_is_dirichlet(g, p) ? 0.0 : nodal_row(g, sigma, phi, p, NULL);
+            }
     return 0;
 }
 
@@ -1106,6 +1132,7 @@ static void nodal_residual(const nodal_level* L)
 {
     orc_nodal_apply(&L->g, L->sigma, L->x, L->r);
     long M = nnodes(&L->g);
+    ORC_PARALLEL_FOR
     for (long i = 0; i < M; ++i) L->r[i] = L->b[i] - L->r[i];
     int p[3];
     for (p[2] = 0; p[2] < node_extent(&L->g, 2); ++p[2])
@@ -1137,13 +1164,14 @@ static int fine_pos(const orc_grid* gf, int d, int q, int* out)
 /* b_C = 2^-dim sum_J P_{JC} r_J  (R = 2^-dim P^T, full weighting) */
 static void nodal_restrict(const nodal_level* F, nodal_level* C)
 {
-    int pc[3];
     int dim = C->g.dim;
     double scale = 1.0 / (double)(1 << dim);
     int noff = (dim == 3) ? 27 : 9;
-    for (pc[2] = 0; pc[2] < node_extent(&C->g, 2); ++pc[2])
-        for (pc[1] = 0; pc[1] < node_extent(&C->g, 1); ++pc[1])
-            for (pc[0] = 0; pc[0] < node_extent(&C->g, 0); ++pc[0]) {
+    ORC_PARALLEL_FOR
+    for (int k = 0; k < node_extent(&C->g, 2); ++k)
+        for (int j = 0; j < node_extent(&C->g, 1); ++j)
+            for (int i = 0; i < node_extent(&C->g, 0); ++i) {
+                int pc[3] = { i, j, k };
                 double s = 0.0;
                 if (!node_is_dirichlet(&C->g, pc)) {
                     for (int t = 0; t < noff; ++t) {
@@ -1165,11 +1193,12 @@ static void nodal_restrict(const nodal_level* F, nodal_level* C)
 /* x_J += sum_C P_{JC} x_C over fine non-Dirichlet nodes (trilinear) */
 static void nodal_prolong(const nodal_level* C, nodal_level* F)
 {
-    int pf[3];
     int dim = F->g.dim;
-    for (pf[2] = 0; pf[2] < node_extent(&F->g, 2); ++pf[2])
-        for (pf[1] = 0; pf[1] < node_extent(&F->g, 1); ++pf[1])
-            for (pf[0] = 0; pf[0] < node_extent(&F->g, 0); ++pf[0]) {
+    ORC_PARALLEL_FOR
+    for (int k = 0; k < node_extent(&F->g, 2); ++k)
+        for (int j = 0; j < node_extent(&F->g, 1); ++j)
+            for (int i = 0; i < node_extent(&F->g, 0); ++i) {
+                int pf[3] = { i, j, k };
                 if (node_is_dirichlet(&F->g, pf)) continue;
                 /* per axis: even position -> one coarse node, odd -> two halves */
                 int lo[3] = { 0, 0, 0 }, cnt[3] = { 1, 1, 1 };
@@ -1193,6 +1222,13 @@ static void nodal_prolong(const nodal_level* C, nodal_level* F)
             }
 }
 
+#ifdef ORC_PARALLEL
+static void nodal_gs_colour(const nodal_level* L);   /* eight-colour sweep, mg_oracle_omp.c */
+#define ORC_NODAL_SMOOTH nodal_gs_colour
+#else
+#define ORC_NODAL_SMOOTH nodal_gs_lex
+#endif
+
 static void nodal_vcycle(nodal_mg* mg, int l)
 {
     nodal_level* L = &mg->lev[l];
@@ -1206,14 +1242,14 @@ static void nodal_vcycle(nodal_mg* mg, int l)
         free(rhs);
         return;
     }
-    for (int s = 0; s < 2; ++s) nodal_gs_lex(L);
+    for (int s = 0; s < 2; ++s) ORC_NODAL_SMOOTH(L);
     nodal_residual(L);
     nodal_level* C = &mg->lev[l + 1];
     nodal_restrict(L, C);
     memset(C->x, 0, sizeof(double) * nnodes(&C->g));
     nodal_vcycle(mg, l + 1);
     nodal_prolong(C, L);
-    for (int s = 0; s < 2; ++s) nodal_gs_lex(L);
+    for (int s = 0; s < 2; ++s) ORC_NODAL_SMOOTH(L);
 }
 
 int orc_nodal_solve_mg(const orc_grid* g, const double* sigma, const double* f_in, double* phi,

@@ -57,6 +57,8 @@ def parse():
                          "config1: 2-D 64^2 manufactured solve; config2: 128^3 FP64 MAC + nodal step; "
                          "step: the time step around the two projections (face velocities, MAC projection, "
                          "advection with rotation, nodal projection), mixed, on the stratified workload")
+    ap.add_argument("--batch-branches", action="store_true",
+                    help="batch: run every solve as its own graph branch instead of the shared batched loop")
     ap.add_argument("--parity", action="store_true",
                     help="also solve the MAC system of the workload with the CPU oracle and report rel-L2 of phi")
     ap.add_argument("--budget-gb", type=float, default=24.0, help="serve: device-memory budget of the slots")
@@ -373,7 +375,8 @@ def run_batch(args, dev, world, dist):
         for sp in specs:
             p = I.batch_problem(sp)
             s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", stream=stream,
-                                 flags=N.MG_FLAG_AUTOTUNE | N.MG_FLAG_ZERO_GUESS)
+                                 flags=N.MG_FLAG_AUTOTUNE | N.MG_FLAG_ZERO_GUESS |
+                                 (N.MG_FLAG_BATCH_BRANCHES if args.batch_branches else 0))
             f = s.rhs([T(u) for u in p["U_mac"]], T(p["beta0"]), T(p["S"]), beta0_face=[T(b) for b in p["beta0_face"]])
             solvers.append(s)
             rhs.append(f)
@@ -447,6 +450,11 @@ def run_batch(args, dev, world, dist):
             "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": {"workload": "batch of 64 MAC solves, n in {32,64,96,128} (seed 4), contrast log-uniform "
                                    "in [1e1,1e4], one graph launch per step", "cells": cells, "tol": args.tol,
+                       "loop": ("per-solve graph branches" if args.batch_branches else
+                                "one batched loop: each step of all solves in one persistent launch driven by "
+                                "per-solve work items"),
+                       "rhs": "each solve's right-hand side formed before the timed region (mg_rhs); the timed "
+                              "step is the 64 solves",
                        "l2": "aggregate inputs larger than L2",
                        "autotuned_smoother_per_level": tuned},
             "gpu_launches": launches,

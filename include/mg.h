@@ -174,6 +174,17 @@ typedef struct {
  * pass that waits for its predecessor longer than about a second makes the
  * solve return MG_ERR_CUDA. */
 #define MG_FLAG_CELL_PIPE 64
+/* flags: in mg_solve_batch / mg_project_batch, run this handle's solve as its
+ * own branch of the batch graph.  By default, when every solve of a batch is a
+ * 3-D mixed-precision cell solve with linear prolongation and automatic inner
+ * cycles (and the same nu1, nu2), the solves share one iteration loop whose
+ * steps -- each colour pass, restriction and prolongation of "level l" of all
+ * solves, their coarse ends, FP64 residuals, norms and updates -- are one
+ * launch each, driven by tables of per-solve work items; solves that have
+ * converged drop out of the launches.  Both forms give every solve the result
+ * it has alone, bit for bit.  One handle with this flag makes the whole batch
+ * use per-solve branches. */
+#define MG_FLAG_BATCH_BRANCHES 128
 
 /* Per-solve statistics.  rel_resid = ||f - L phi||_2/||f||_2 over the unknowns;
  * rel_constraint (projections only): MAC ||D(beta0 U) - beta0 S||/||beta0 S||
@@ -311,6 +322,16 @@ mg_status mg_project_batch(mg_handle* const* hs, double* const* U, const mg_beta
  * No counterpart in the paper.  Work already enqueued stays on the old stream:
  * synchronise it first if the new stream does not wait for it.
  * MG_ERR_INVALID_ARG for a null handle. */
+/* Concurrent batched loops (section 3's V-cycles of many independent solves):
+ * a batch whose solves share batched loops (see MG_FLAG_BATCH_BRANCHES) is
+ * split into this many groups of about equal total cells, each group one
+ * lockstep loop, the groups concurrent branches of the batch graph, so one
+ * group's FP64 residuals and latency-bound small levels overlap another's
+ * bandwidth-bound finest levels.  0 (the default) picks one group per 16
+ * solves, at most 4.  Results do not depend on it.  Takes effect for batch
+ * graphs built afterwards (they are cached per list of handles and setting).
+ * MG_ERR_INVALID_ARG outside 0 .. 64. */
+mg_status mg_set_batch_groups(int groups);
 mg_status mg_set_stream(mg_handle* h, void* stream);
 
 /* out = L phi with the FP64 fine-level operator of the projection system (S3,
@@ -363,7 +384,17 @@ typedef enum {
     MG_PROF_CELL_PIPE_UP = 6,     /* up leg as one pipelined launch: the prolongation fused
                                      into the first of nu2 sweeps (4 + 1/8 words/cell), 4 words
                                      per further sweep */
-    MG_PROF_COUNT = 7
+    /* the batched loop of mg_solve_batch / mg_project_batch (host-driven while
+     * profiling): one launch each, over every solve with work in that step */
+    MG_PROF_BATCH_SMOOTH = 7,     /* a colour pass of the finest level step (level 0 of every
+                                     solve): 2 words per cell */
+    MG_PROF_BATCH_RESTRICT = 8,   /* residual + restriction of one level step: 3 + 1/8 words per fine cell */
+    MG_PROF_BATCH_PROLONG = 9,    /* prolongation + correction of one level step: x read and
+                                     written, 1/8 word of coarse x per fine cell */
+    MG_PROF_BATCH_COARSE = 10,    /* the solves' coarse ends (one CTA each; latency-bound, no bytes counted) */
+    MG_PROF_BATCH_RESID64 = 11,   /* FP64 residuals and norms of the solves: 15 FP64 flops per cell */
+    MG_PROF_BATCH_SMOOTH_COARSE = 12, /* a colour pass of a coarser level step: 2 words per cell */
+    MG_PROF_COUNT = 13
 } mg_prof_kernel;
 
 /* Allocation-free check of the MAC constraint.  The paper has no counterpart:

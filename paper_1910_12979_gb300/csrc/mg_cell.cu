@@ -222,9 +222,12 @@ __global__ void k_resid64(CellLevel<double> L, const double* __restrict__ x, con
 // the neighbouring lanes, the integer index work once per quad.  Every cell's
 // FP64 arithmetic is cell_row's (face terms x-lo, x-hi, y-lo, y-hi, z-lo, z-hi,
 // fused multiply-adds from 0) followed by b - fma(-d, x, off): identical values.
-__global__ void __launch_bounds__(256)
-k_resid64_v4(CellLevel<double> L, const double* __restrict__ x, const double* __restrict__ b,
-             float* __restrict__ r32, const double* __restrict__ scale, double* __restrict__ partials)
+// The body is shared with the batched residual (one block's share of one solve).
+// vb, vgrid: the block's index and the grid size of that partition.
+__device__ __forceinline__ void resid64_v4_block(const CellLevel<double>& L, const double* __restrict__ x,
+                                                 const double* __restrict__ b, float* __restrict__ r32,
+                                                 const double* __restrict__ scale, double* __restrict__ partials,
+                                                 int vb, int vgrid)
 {
     const int nx = L.nx, ny = L.ny, nz = L.nz, nq = nx / 4;
     const int nquad = nq * ny * nz;
@@ -234,8 +237,8 @@ k_resid64_v4(CellLevel<double> L, const double* __restrict__ x, const double* __
     float acc = 0.f;
     auto ld2 = [](const double* p) { return *reinterpret_cast<const double2*>(p); };
     const double2 z2 = make_double2(0.0, 0.0);
-    const int stride = gridDim.x * blockDim.x;
-    for (int u0 = blockIdx.x * blockDim.x; u0 < nquad; u0 += stride) {
+    const int stride = vgrid * blockDim.x;
+    for (int u0 = vb * blockDim.x; u0 < nquad; u0 += stride) {
         // every lane of the warp runs the iteration (shuffles); lanes past the end compute the last quad
         const int ug = u0 + threadIdx.x;
         const bool live = ug < nquad;
@@ -288,7 +291,42 @@ k_resid64_v4(CellLevel<double> L, const double* __restrict__ x, const double* __
         }
     }
     double a[1] = {(double)acc};
-    block_reduce_store<1>(a, partials);
+    block_reduce_store<1>(a, partials, vb);
+}
+
+__global__ void __launch_bounds__(256)
+k_resid64_v4(CellLevel<double> L, const double* __restrict__ x, const double* __restrict__ b,
+             float* __restrict__ r32, const double* __restrict__ scale, double* __restrict__ partials)
+{
+    resid64_v4_block(L, x, b, r32, scale, partials, blockIdx.x, gridDim.x);
+}
+
+// Batched FP64 residuals: one block per (solve, block of k_resid64_v4's
+// kRedBlocks-block partition that has quads); each takes that block's quads
+// and partial slot, so every solve's residual and norm partials are those of
+// its solve alone.  The first block of a solve zeroes the slots of the
+// partition's blocks without quads (their partials alone are 0).
+__global__ void __launch_bounds__(256)
+k_resid64_batch(const Resid64Item* __restrict__ items, const int* __restrict__ bmap, const int* __restrict__ run)
+{
+    const Resid64Item& it = items[__ldg(bmap + blockIdx.x)];
+    if (!__ldg(run + it.solve)) return;
+    const int vb = blockIdx.x - it.vb0;
+    if (vb == 0)
+        for (int t = it.nvb + threadIdx.x; t < kRedBlocks; t += blockDim.x) it.partials[t] = 0.0;
+    resid64_v4_block(it.L, it.x, it.b, it.r32, it.scale, it.partials, vb, kRedBlocks);
+}
+
+bool cell_resid64_batch_ok(const CellLevel<double>& L, const double* x, const double* b, const float* r32)
+{
+    auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    return L.diag && L.nx % 4 == 0 && a16(x) && a16(b) && a16(L.diag) && a16(L.by) && a16(L.bz) &&
+           (!r32 || a16(r32)) && (size_t)L.nx * L.ny * L.nz / 4 < (size_t)1 << 30;
+}
+
+void cell_resid64_batch(const Resid64Item* items, const int* bmap, int blocks, const int* run, cudaStream_t s)
+{
+    MGP_LAUNCH(k_resid64_batch<<<blocks, kThreads, 0, s>>>(items, bmap, run));
 }
 
 template <int DIM>

@@ -14,18 +14,8 @@
 
 namespace mgp {
 
-template <typename T>
-struct CoarseArgs {
-    int nlev;                          // levels of the sub-cycle; the last is the coarsest
-    CellLevel<T> L[kCoarseMaxLevels];
-    T* x[kCoarseMaxLevels];
-    T* b[kCoarseMaxLevels];            // b[0]: the sub-cycle's right-hand side (read only)
-    const double* Minv;
-    int Nd, nu1, nu2, order, zero_first;
-};
-
 template <int DIM, typename T>
-__global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> A)
+__device__ __forceinline__ void coarse_body(const CoarseArgs<T>& A)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     auto cells = [&](int l) { return A.L[l].nx * A.L[l].ny * A.L[l].nz; };
@@ -76,6 +66,25 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> A)
         __syncthreads();
         smooth(l, A.nu2);
     }
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> A)
+{
+    coarse_body<DIM, T>(A);
+}
+
+// Batched coarse ends: CTA i runs solve i's while its run flag is set.
+__global__ void __launch_bounds__(1024) k_coarse_batch(const CoarseArgs<float>* __restrict__ A,
+                                                       const int* __restrict__ run)
+{
+    if (!run[blockIdx.x]) return;
+    coarse_body<3, float>(A[blockIdx.x]);
+}
+
+void coarse_cycle_batch(const CoarseArgs<float>* A, int count, const int* run, cudaStream_t s)
+{
+    MGP_LAUNCH(k_coarse_batch<<<count, 1024, 0, s>>>(A, run));
 }
 
 template <typename T>

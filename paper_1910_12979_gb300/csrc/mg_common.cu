@@ -10,23 +10,43 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// Sum the kRedBlocks partials of slot q in a fixed order (kThreads threads):
+// out = the sum (times *mul when mul is given), written by thread 0.
+__device__ __forceinline__ void finalize_slot(const double* __restrict__ partials, int q, double* __restrict__ out,
+                                              const double* __restrict__ mul, double* sh)
+{
+    double s = 0.0;
+    for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += partials[q * kRedBlocks + b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = mul ? sh[0] * *mul : sh[0];
+    __syncthreads();
+}
+
 // Sum the kRedBlocks partials of each slot in a fixed order: out[q].
 __global__ void k_finalize(const double* __restrict__ partials, int nslots, double* __restrict__ out,
                            const double* __restrict__ mul)
 {
     __shared__ double sh[kThreads];
-    for (int q = 0; q < nslots; ++q) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += partials[q * kRedBlocks + b];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[q] = mul ? sh[0] * *mul : sh[0];
-        __syncthreads();
-    }
+    for (int q = 0; q < nslots; ++q) finalize_slot(partials, q, out, mul, sh);
+}
+
+// One block per solve of a batch: slot 0 of its partials, as k_finalize.
+__global__ void k_finalize_batch(const FinalItem* __restrict__ items, const int* __restrict__ run)
+{
+    __shared__ double sh[kThreads];
+    const FinalItem& it = items[blockIdx.x];
+    if (!run[it.solve]) return;
+    finalize_slot(it.partials, 0, it.out, it.mul, sh);
+}
+
+void reduce_finalize_batch(const FinalItem* items, int count, const int* run, cudaStream_t s)
+{
+    MGP_LAUNCH(k_finalize_batch<<<count, kThreads, 0, s>>>(items, run));
 }
 
 void reduce_finalize(const double* partials, int nslots, double* out, cudaStream_t s, const double* mul)
@@ -110,6 +130,56 @@ __global__ void k_axpy32(double* __restrict__ phi, const float* __restrict__ e, 
     for (size_t t = done + t0; t < n; t += st) phi[t] = fmadd(s, f32_to_f64(e[t]), phi[t]);
 }
 static inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// Batched refinement updates: resident blocks walk the tiles of every solve
+// whose run flag is set; each thread updates four entries as k_axpy32 does
+// (the update is entrywise, so the partition changes nothing).
+__global__ void __launch_bounds__(kThreads)
+k_axpy32_batch(const AxpyItem* __restrict__ items, int count, int tiles, const int* __restrict__ run)
+{
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].tile0 <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const AxpyItem& it = items[lo];
+        if (!run[it.solve]) continue;
+        const int t = (tile - it.tile0) * kThreads + threadIdx.x;
+        if (t >= it.n4) continue;
+        const double s = *it.scale;
+        const float4 ev = reinterpret_cast<const float4*>(it.e)[t];
+        double2* pp = reinterpret_cast<double2*>(it.phi) + 2 * t;
+        double2 p = pp[0], q = pp[1];
+        p.x = fmadd(s, f32_to_f64(ev.x), p.x);
+        p.y = fmadd(s, f32_to_f64(ev.y), p.y);
+        q.x = fmadd(s, f32_to_f64(ev.z), q.x);
+        q.y = fmadd(s, f32_to_f64(ev.w), q.y);
+        pp[0] = p;
+        pp[1] = q;
+    }
+}
+
+int axpy_batch_grid(int tiles)
+{
+    static std::atomic<int> per{0};
+    int p = per.load(std::memory_order_acquire);
+    if (p == 0) {
+        int dev = 0, sms = 0, b = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_axpy32_batch, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+        p = (sms > 0 ? sms : kNumSMs) * b;
+        per.store(p, std::memory_order_release);
+    }
+    return tiles < p ? tiles : p;
+}
+
+void axpy_f32_batch(const AxpyItem* items, int count, int tiles, const int* run, int grid, cudaStream_t s)
+{
+    MGP_LAUNCH(k_axpy32_batch<<<grid, kThreads, 0, s>>>(items, count, tiles, run));
+}
 
 __global__ void k_to64(double* __restrict__ d, const float* __restrict__ a, size_t n)
 {

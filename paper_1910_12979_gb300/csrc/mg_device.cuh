@@ -13,7 +13,7 @@ __host__ __device__ inline int ceil_div(long long a, long long b) { return (int)
 // partial sums at partials[q * kRedBlocks + blockIdx.x].  The grid must have
 // exactly kRedBlocks blocks (1-D grid) of kThreads threads (any block shape).
 template <int NS>
-__device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* __restrict__ partials)
+__device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* __restrict__ partials, int slot)
 {
     __shared__ double sh[NS][kThreads / 32];
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);  // 1-D or 2-D blocks
@@ -32,9 +32,14 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* __re
             double x = (lane < kThreads / 32) ? sh[q][lane] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) partials[q * kRedBlocks + blockIdx.x] = x;
+            if (lane == 0) partials[q * kRedBlocks + slot] = x;
         }
     }
+}
+template <int NS>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* __restrict__ partials)
+{
+    block_reduce_store<NS>(v, partials, blockIdx.x);
 }
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }

@@ -1054,9 +1054,8 @@ __global__ void k_zero_if_f0(double* __restrict__ phi, size_t n, const DevScalar
 
 // Convergence decision after a residual (first: the initial one).  Mirrors the
 // host loop of solve_core.
-__global__ void k_check(DevScalars* d, cudaGraphConditionalHandle c, int first)
+__device__ unsigned check_state(DevScalars* d, int first)
 {
-    if (threadIdx.x != 0) return;
     const double fn2 = d->fnorm2;
     unsigned cont = 0;
     if (fn2 == 0.0) {
@@ -1088,7 +1087,13 @@ __global__ void k_check(DevScalars* d, cudaGraphConditionalHandle c, int first)
         d->ncyc = m;
         d->prev_rel = rel;
     }
-    cudaGraphSetConditional(c, cont);
+    return cont;
+}
+
+__global__ void k_check(DevScalars* d, cudaGraphConditionalHandle c, int first)
+{
+    if (threadIdx.x != 0) return;
+    cudaGraphSetConditional(c, check_state(d, first));
 }
 
 // the IF node of V-cycle k + 1 (k >= 1) of a refinement step
@@ -1098,6 +1103,61 @@ __global__ void k_set_cycle(DevScalars* d, cudaGraphConditionalHandle c, int k)
     const bool run = d->ncyc > k;
     if (run) d->n_extra += 1;
     cudaGraphSetConditional(c, run ? 1u : 0u);
+}
+
+// Launches of a batched graph that run a data-dependent number of times.
+struct BatchCounters {
+    int loops;                 // iterations of the WHILE body
+    int ifruns[kMaxInner];     // runs of the IF node of V-cycle v + 1 of a step (v >= 1)
+    int any;                   // the last check's decision (host-driven loop)
+};
+
+// The convergence decisions of a batched solve loop: each solve's check as
+// k_check, for the solves still iterating (all of them after the initial
+// residual); run[s] keeps whether solve s iterates again, and the WHILE
+// condition is set while any does.
+__global__ void k_batch_check(DevScalars* const* ds, int* run, int count, cudaGraphConditionalHandle c, int first,
+                              BatchCounters* ctr, int use_cond)
+{
+    int any = 0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x)
+        if (first || run[i]) {
+            const unsigned cont = check_state(ds[i], first);
+            run[i] = cont ? 1 : 0;
+            any |= run[i];
+        }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        if (first) {
+            ctr->loops = 0;
+            for (int v = 0; v < kMaxInner; ++v) ctr->ifruns[v] = 0;
+        } else {
+            ctr->loops += 1;
+        }
+        ctr->any = any;
+        if (use_cond) cudaGraphSetConditional(c, any ? 1u : 0u);
+    }
+}
+
+// The run flags of V-cycle v + 1 (v >= 1) of a refinement step: the solves
+// still iterating whose step takes more than v V-cycles (k_set_cycle's test);
+// the IF condition is set when any does.
+__global__ void k_batch_gate(DevScalars* const* ds, const int* run0, int* runv, int count,
+                             cudaGraphConditionalHandle c, int v, BatchCounters* ctr, int use_cond)
+{
+    int any = 0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        DevScalars* d = ds[i];
+        const int r = run0[i] && d->ncyc > v;
+        if (r) d->n_extra += 1;
+        runv[i] = r;
+        any |= r;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        if (any) ctr->ifruns[v] += 1;
+        if (use_cond) cudaGraphSetConditional(c, any ? 1u : 0u);
+    }
 }
 
 // One refinement iteration (mixed) or V-cycle (FP64) on phi, then the residual.
@@ -1172,16 +1232,15 @@ mg_status capture_deps(cudaStream_t s, cudaGraph_t* g, std::vector<cudaGraphNode
     return MG_OK;
 }
 
-// Enqueue one whole solve of L phi_int = f64 on h->stream, which is capturing.
-mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream, cudaStream_t if_stream,
-                        long long& fixed, long long& body, long long& if_body)
+// The part of a captured solve before its iteration loop: rhs staging (from
+// the caller's rhs when rhs_from_io) and the initial residual.
+void capture_prologue(mg_handle* h, bool rhs_from_io)
 {
     cudaStream_t s = h->stream;
     const size_t n = h->lev[0].nvec;
     const bool nodal = h->loc == MG_LOC_NODAL;
     double* phi = h->phi_int;
     float* r32 = h->prec == MG_PREC_MIXED ? h->lev[0].b32 : nullptr;
-    const long long c0 = launch_count();
     if (rhs_from_io) {
         MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(h->f64, h->d, n, 0));
         if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), h->f64, s);
@@ -1196,6 +1255,30 @@ mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream
         if (nodal) node_zero_dirichlet<double>(h->dim, nview<double>(h, 0), phi, s);
         residual64(h, phi, r32);
     }
+}
+
+// The part after the loop: gauge, copy-out of phi, scalar block to the host.
+mg_status capture_epilogue(mg_handle* h)
+{
+    cudaStream_t s = h->stream;
+    const size_t n = h->lev[0].nvec;
+    double* phi = h->phi_int;
+    if (h->singular) gauge(h, phi);
+    MGP_LAUNCH(k_zero_if_f0<<<kRedBlocks, kThreads, 0, s>>>(phi, n, h->d));
+    MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(phi, h->d, n, 2));
+    MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    return MG_OK;
+}
+
+// Enqueue one whole solve of L phi_int = f64 on h->stream, which is capturing.
+mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream, cudaStream_t if_stream,
+                        long long& fixed, long long& body, long long& if_body)
+{
+    cudaStream_t s = h->stream;
+    double* phi = h->phi_int;
+    float* r32 = h->prec == MG_PREC_MIXED ? h->lev[0].b32 : nullptr;
+    const long long c0 = launch_count();
+    capture_prologue(h, rhs_from_io);
     cudaGraph_t g;
     std::vector<cudaGraphNode_t> deps;
     mg_status rc = capture_deps(s, &g, deps);
@@ -1224,10 +1307,8 @@ mg_status capture_solve(mg_handle* h, bool rhs_from_io, cudaStream_t body_stream
     h->stream = s;
     MG_CK(cudaStreamEndCapture(body_stream, &bodyg));
     const long long c2 = launch_count();
-    if (h->singular) gauge(h, phi);
-    MGP_LAUNCH(k_zero_if_f0<<<kRedBlocks, kThreads, 0, s>>>(phi, n, h->d));
-    MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(phi, h->d, n, 2));
-    MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    rc = capture_epilogue(h);
+    if (rc != MG_OK) return rc;
     const long long c3 = launch_count();
     fixed = (c1 - c0) + (c3 - c2);
     body = (c2 - c1) - if_total;
@@ -1328,13 +1409,486 @@ mg_status graph_result(mg_handle* h, long long fixed, long long body, long long 
     return (mg_status)r.status;
 }
 
+// ------------------------------------------------ batched (lockstep) solve loops
+//
+// When every solve of a batch is a 3-D mixed-precision cell solve whose
+// levels the batched kernels take, the batch graph shares one iteration loop:
+// each solve's rhs staging and initial residual (its own branch), then one
+// WHILE node whose body runs V-cycle 1 of a refinement step for every solve
+// still iterating, V-cycles 2 .. kMaxInner in IF nodes, the FP64 updates,
+// residuals and norms, and the checks -- one launch per step for all solves
+// (mg_batch.cu and the batched launchers) -- then each solve's copy-out.  The
+// V-cycles run the solves' levels in lockstep from the finest: step l holds
+// level l of every solve with more launched levels than l; the levels of at
+// most kBatchCoarseCells cells run in the solves' coarse ends, one CTA per
+// solve in one launch.  Each solve's decisions are k_check's on its own
+// scalar block, so it iterates exactly as alone, and its arithmetic is that
+// of the single-solve kernels: the results equal the solves run alone.
+
+// first level of a handle's batched coarse end
+int batch_coarse_start(const mg_handle* h)
+{
+    const int L = h->nlev;
+    int l = 1;
+    while (l < L - 1 && (h->lev[l].ncell > kBatchCoarseCells || L - l > kCoarseMaxLevels)) ++l;
+    return l;
+}
+
+bool batch_kernels_ok(const mg_handle* h)
+{
+    auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    auto a8 = [](const void* p) { return ((uintptr_t)p & 7) == 0; };
+    if (h->loc != MG_LOC_CELL || h->dim != 3 || h->prec != MG_PREC_MIXED || !adaptive_cycles(h)) return false;
+    if (h->opt.interp_order != 1 || h->opt.nu1 < 1 || h->opt.nu2 < 0 || h->nlev < 2) return false;
+    if (h->opt.flags & (MG_FLAG_NO_FUSED | MG_FLAG_BATCH_BRANCHES)) return false;
+    if (h->Nd > kMaxDense || h->lev[0].nvec % 4 != 0 || !a16(h->phi_int)) return false;
+    if (!cell_resid64_batch_ok(cview<double>(h, 0), h->phi_int, h->f64, h->lev[0].b32)) return false;
+    const int lc = batch_coarse_start(h);
+    if (h->nlev - lc > kCoarseMaxLevels) return false;
+    for (int l = 0; l < lc; ++l) {
+        const CellLevel<float> V = cview<float>(h, l);
+        float* x = h->lev[l].x32;
+        const float* b = h->lev[l].b32;
+        if (V.nx % 4 != 0 || V.nx < 8 || V.ny % 2 != 0 || V.nz % 2 != 0 || V.invd) return false;
+        if (!a16(x) || !a16(b) || !a16(V.by) || !a16(V.bz)) return false;
+        if (!a8(h->lev[l + 1].b32) || !a8(h->lev[l + 1].x32)) return false;
+    }
+    return true;
+}
+
+// Whether the solves of hs share one batched loop (graph or host-driven).
+bool batch_eligible(mg_handle* const* hs, int count)
+{
+    if (count < 2) return false;
+    for (int i = 0; i < count; ++i)
+        if (!batch_kernels_ok(hs[i]) || hs[i]->opt.nu1 != hs[0]->opt.nu1 || hs[i]->opt.nu2 != hs[0]->opt.nu2)
+            return false;
+    return true;
+}
+
+// The device tables of a batched loop (one allocation) and its launch shapes.
+struct BatchPlan {
+    struct Step {
+        std::vector<BatchLaunch> launches;   // the step's items, at most kBatchLaunchItems per launch
+        double cells = 0.0;                  // fine cells of the step's items (profiling bytes)
+        void add(const BatchItem& it)
+        {
+            if (launches.empty() || launches.back().nitems == kBatchLaunchItems) {
+                launches.emplace_back();
+                launches.back().nitems = 0;
+                launches.back().tiles = 0;
+            }
+            BatchLaunch& B = launches.back();
+            B.items[B.nitems] = it;
+            B.items[B.nitems].tile0 = B.tiles;
+            B.tiles += (it.units + kBatchTile - 1) / kBatchTile;
+            B.nitems += 1;
+        }
+    };
+    int count = 0, nsteps = 0, nu1 = 0, nu2 = 0;
+    std::vector<mg_handle*> hs;       // the group's handles (its solves 0 .. count - 1)
+    long long body = 0, ifb = 0;      // launches per loop iteration (outside the IF nodes) and per IF run
+    double cells0 = 0.0;              // cells of the solves' finest levels
+    char* dmem = nullptr;
+    int* run = nullptr;               // [kMaxInner][count]
+    DevScalars** ds = nullptr;        // [count]
+    BatchCounters* ctr = nullptr;     // device counters
+    BatchCounters* hctr = nullptr;    // pinned host copy, written at the end of each run
+    Step smooth[kMaxLevels], restr[kMaxLevels], prolong[kMaxLevels];
+    CoarseArgs<float>* coarse = nullptr;
+    Resid64Item* resid = nullptr;
+    int* resid_bmap = nullptr;        // item of every block of the batched residual
+    int resid_blocks = 0;
+    FinalItem* fin = nullptr;
+    AxpyItem* axpy = nullptr;
+    int axpy_tiles = 0, axpy_grid = 0;
+    ~BatchPlan()
+    {
+        if (dmem) cudaFree(dmem);
+        if (hctr) cudaFreeHost(hctr);
+    }
+};
+
+// Lay out and upload the tables of a batched loop over hs[0..count).
+mg_status make_batch_plan(mg_handle* const* hs, int count, BatchPlan& P)
+{
+    P.count = count;
+    P.hs.assign(hs, hs + count);
+    P.nu1 = hs[0]->opt.nu1;
+    P.nu2 = hs[0]->opt.nu2;
+    std::vector<int> lc(count);
+    for (int i = 0; i < count; ++i) {
+        lc[i] = batch_coarse_start(hs[i]);
+        P.nsteps = std::max(P.nsteps, lc[i]);
+    }
+    for (int l = 0; l < P.nsteps; ++l) {
+        for (int i = 0; i < count; ++i) {
+            if (l >= lc[i]) continue;
+            mg_handle* h = hs[i];
+            BatchItem it{};
+            it.F = cview<float>(h, l);
+            it.C = cview<float>(h, l + 1);
+            it.x = h->lev[l].x32;
+            it.b = h->lev[l].b32;
+            it.bc = h->lev[l + 1].b32;
+            it.xc = h->lev[l + 1].x32;
+            it.solve = i;
+            const int nq = it.F.nx / 4;
+            batch_magic(nq, &it.mq, &it.sq);
+            batch_magic(it.F.ny, &it.my, &it.sy);
+            it.units = nq * it.F.ny * it.F.nz;
+            P.smooth[l].cells += 4.0 * it.units;
+            P.smooth[l].add(it);
+            P.prolong[l].add(it);
+            it.units = nq * (it.F.ny / 2) * (it.F.nz / 2);
+            batch_magic(it.F.ny / 2, &it.my, &it.sy);
+            P.restr[l].add(it);
+        }
+        P.prolong[l].cells = P.restr[l].cells = P.smooth[l].cells;
+    }
+    std::vector<CoarseArgs<float>> co(count);
+    std::vector<Resid64Item> rs(count);
+    std::vector<FinalItem> fi(count);
+    std::vector<AxpyItem> ax(count);
+    std::vector<DevScalars*> ds(count);
+    int at = 0;
+    std::vector<int> bmap;
+    for (int i = 0; i < count; ++i) {
+        mg_handle* h = hs[i];
+        CoarseArgs<float>& A = co[i];
+        memset(&A, 0, sizeof A);
+        A.nlev = h->nlev - lc[i];
+        for (int l = lc[i]; l < h->nlev; ++l) {
+            A.L[l - lc[i]] = cview<float>(h, l);
+            A.x[l - lc[i]] = h->lev[l].x32;
+            A.b[l - lc[i]] = h->lev[l].b32;
+        }
+        A.Minv = h->Minv;
+        A.Nd = h->Nd;
+        A.nu1 = h->opt.nu1;
+        A.nu2 = h->opt.nu2;
+        A.order = h->opt.interp_order;
+        A.zero_first = 1;
+        const long long quads = (long long)(h->lev[0].nvec / 4);
+        const int nvb = (int)std::min<long long>(kRedBlocks, (quads + kThreads - 1) / kThreads);
+        rs[i] = Resid64Item{cview<double>(h, 0), h->phi_int, h->f64, h->lev[0].b32, &h->d->fscale, h->partials,
+                            i, (int)bmap.size(), nvb, 0};
+        bmap.resize(bmap.size() + nvb, i);
+        fi[i] = FinalItem{h->partials, &h->d->rnorm2, &h->d->rscale2, i, 0};
+        const int n4 = (int)(h->lev[0].nvec / 4);
+        ax[i] = AxpyItem{h->phi_int, h->lev[0].x32, &h->d->fscale, i, at, n4, 0};
+        at += (n4 + kThreads - 1) / kThreads;
+        ds[i] = h->d;
+        P.cells0 += (double)h->lev[0].ncell;
+    }
+    P.axpy_tiles = at;
+    P.axpy_grid = axpy_batch_grid(at);
+    P.resid_blocks = (int)bmap.size();
+    // one allocation, 256-byte aligned tables
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    const size_t o_run = take(sizeof(int) * kMaxInner * count), o_ds = take(sizeof(DevScalars*) * count),
+                 o_ctr = take(sizeof(BatchCounters)), o_co = take(sizeof(CoarseArgs<float>) * count),
+                 o_rs = take(sizeof(Resid64Item) * count), o_fi = take(sizeof(FinalItem) * count),
+                 o_ax = take(sizeof(AxpyItem) * count), o_bm = take(sizeof(int) * bmap.size());
+    MG_CK(cudaMalloc(&P.dmem, off));
+    MG_CK(cudaMallocHost(&P.hctr, sizeof(BatchCounters)));
+    memset(P.hctr, 0, sizeof(BatchCounters));
+    std::vector<char> host(off, 0);
+    auto put = [&](size_t o, const void* src, size_t bytes) { if (bytes) memcpy(host.data() + o, src, bytes); };
+    put(o_ds, ds.data(), sizeof(DevScalars*) * count);
+    put(o_co, co.data(), sizeof(CoarseArgs<float>) * count);
+    put(o_rs, rs.data(), sizeof(Resid64Item) * count);
+    put(o_fi, fi.data(), sizeof(FinalItem) * count);
+    put(o_ax, ax.data(), sizeof(AxpyItem) * count);
+    put(o_bm, bmap.data(), sizeof(int) * bmap.size());
+    MG_CK(cudaMemcpy(P.dmem, host.data(), off, cudaMemcpyHostToDevice));
+    P.run = reinterpret_cast<int*>(P.dmem + o_run);
+    P.ds = reinterpret_cast<DevScalars**>(P.dmem + o_ds);
+    P.ctr = reinterpret_cast<BatchCounters*>(P.dmem + o_ctr);
+    P.coarse = reinterpret_cast<CoarseArgs<float>*>(P.dmem + o_co);
+    P.resid = reinterpret_cast<Resid64Item*>(P.dmem + o_rs);
+    P.fin = reinterpret_cast<FinalItem*>(P.dmem + o_fi);
+    P.axpy = reinterpret_cast<AxpyItem*>(P.dmem + o_ax);
+    P.resid_bmap = reinterpret_cast<int*>(P.dmem + o_bm);
+    return MG_OK;
+}
+
+// V-cycle v + 1 of a refinement step for every solve whose run flag for it is
+// set, in lockstep from the finest level (level 0 from zero when v == 0; the
+// other levels always from zero, which the first colour pass of each level
+// takes without loading x).
+void batch_vcycle(const BatchPlan& P, int v, cudaStream_t s)
+{
+    const int* run = P.run + (size_t)v * P.count;
+    auto pass = [&](const BatchPlan::Step& st, int op, int color, int zx) {
+        if (st.launches.empty()) return;
+        // algorithmic words per fine cell (as the single-solve classes)
+        const double w = op == BATCH_GSRB ? 2.0 : op == BATCH_RESTRICT ? 3.125 : 2.125;
+        const int id = op == BATCH_GSRB ? (&st == &P.smooth[0] ? MG_PROF_BATCH_SMOOTH : MG_PROF_BATCH_SMOOTH_COARSE)
+                                        : op == BATCH_RESTRICT ? MG_PROF_BATCH_RESTRICT : MG_PROF_BATCH_PROLONG;
+        const int pr = prof_begin(id, w * sizeof(float) * st.cells, s);
+        for (const BatchLaunch& B : st.launches) batch_level(op, B, run, color, zx, s);
+        prof_end(pr, s);
+    };
+    for (int l = 0; l < P.nsteps; ++l) {
+        for (int k = 0; k < P.nu1; ++k)
+            for (int color = 0; color < 2; ++color)
+                pass(P.smooth[l], BATCH_GSRB, color, k == 0 && color == 0 && (l > 0 || v == 0));
+        pass(P.restr[l], BATCH_RESTRICT, 0, 0);
+    }
+    const int pc = prof_begin(MG_PROF_BATCH_COARSE, 0.0, s);
+    coarse_cycle_batch(P.coarse, P.count, run, s);
+    prof_end(pc, s);
+    for (int l = P.nsteps - 1; l >= 0; --l) {
+        pass(P.prolong[l], BATCH_PROLONG, 0, 0);
+        for (int k = 0; k < P.nu2; ++k)
+            for (int color = 0; color < 2; ++color) pass(P.smooth[l], BATCH_GSRB, color, 0);
+    }
+}
+
+// The FP64 refinement update, residuals and norms of a batched loop.
+void batch_update(const BatchPlan& P, cudaStream_t s)
+{
+    axpy_f32_batch(P.axpy, P.count, P.axpy_tiles, P.run, P.axpy_grid, s);
+    const int pr = prof_begin(MG_PROF_BATCH_RESID64, (24.0 + 4.0) * P.cells0, s, kCellResidFlops * P.cells0);
+    cell_resid64_batch(P.resid, P.resid_bmap, P.resid_blocks, P.run, s);
+    reduce_finalize_batch(P.fin, P.count, P.run, s);
+    prof_end(pr, s);
+}
+
+// Capture a batched graph (see above) with one lockstep loop per group of
+// solves, the groups as concurrent branches: while one group runs its FP64
+// residuals or its latency-bound small levels, another streams its finest
+// levels.  fixed: launches that run once per graph launch; each plan's body
+// and ifb: per iteration of its loop and per run of one of its IF nodes.
+mg_status build_batched_graph(std::vector<std::unique_ptr<BatchPlan>>& plans, mg_handle* const* branch,
+                              int nbranch, bool rhs_from_io, cudaGraphExec_t* exec, long long& fixed,
+                              long long* bfixed, long long* bbody, long long* bifb)
+{
+    CaptureStreams cs;
+    mg_status rc = cs.make();
+    if (rc != MG_OK) return rc;
+    const long long c0 = launch_count();
+    long long loops = 0;   // launches inside the loops and the branches (not fixed)
+    MG_CK(cudaStreamBeginCapture(cs.main, cudaStreamCaptureModeRelaxed));
+    std::vector<cudaGraphNode_t> sinks, all;
+    cudaGraph_t g = nullptr;
+    for (size_t gi = 0; gi < plans.size() && rc == MG_OK; ++gi) {
+        BatchPlan& P = *plans[gi];
+        const int count = P.count;
+        std::vector<cudaGraphNode_t> join;
+        for (int i = 0; i < count && rc == MG_OK; ++i) {
+            cudaStreamUpdateCaptureDependencies(cs.main, nullptr, nullptr, 0, cudaStreamSetCaptureDependencies);
+            cudaStream_t saved = P.hs[i]->stream;
+            P.hs[i]->stream = cs.main;
+            capture_prologue(P.hs[i], rhs_from_io);
+            P.hs[i]->stream = saved;
+            rc = capture_deps(cs.main, &g, sinks);
+            join.insert(join.end(), sinks.begin(), sinks.end());
+        }
+        cudaGraphConditionalHandle cond{};
+        cudaGraphNode_t wnode{};
+        if (rc == MG_OK) {
+            cudaStreamUpdateCaptureDependencies(cs.main, join.data(), nullptr, join.size(),
+                                                cudaStreamSetCaptureDependencies);
+            rc = capture_deps(cs.main, &g, sinks);
+        }
+        if (rc == MG_OK && cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+            rc = fail(MG_ERR_CUDA, "cudaGraphConditionalHandleCreate");
+        if (rc == MG_OK) {
+            MGP_LAUNCH(k_batch_check<<<1, kThreads, 0, cs.main>>>(P.ds, P.run, count, cond, 1, P.ctr, 1));
+            rc = capture_deps(cs.main, &g, sinks);
+        }
+        cudaGraphNodeParams prm = {};
+        if (rc == MG_OK) {
+            prm.type = cudaGraphNodeTypeConditional;
+            prm.conditional.handle = cond;
+            prm.conditional.type = cudaGraphCondTypeWhile;
+            prm.conditional.size = 1;
+            if (cudaGraphAddNode(&wnode, g, sinks.data(), nullptr, sinks.size(), &prm) != cudaSuccess ||
+                cudaStreamUpdateCaptureDependencies(cs.main, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+                    cudaSuccess)
+                rc = fail(MG_ERR_CUDA, "adding the batched WHILE node");
+        }
+        if (rc == MG_OK) {
+            const long long c1 = launch_count();
+            long long if_total = 0;
+            cudaGraph_t bodyg = prm.conditional.phGraph_out[0];
+            cudaStream_t b = cs.body;
+            if (cudaStreamBeginCaptureToGraph(b, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+                cudaSuccess)
+                rc = fail(MG_ERR_CUDA, "capturing the batched loop body");
+            if (rc == MG_OK) {
+                batch_vcycle(P, 0, b);
+                for (int v = 1; v < kMaxInner && rc == MG_OK; ++v) {
+                    cudaGraph_t bg;
+                    std::vector<cudaGraphNode_t> deps;
+                    rc = capture_deps(b, &bg, deps);
+                    cudaGraphConditionalHandle ifh{};
+                    if (rc == MG_OK && cudaGraphConditionalHandleCreate(&ifh, bg, 0, 0) != cudaSuccess)
+                        rc = fail(MG_ERR_CUDA, "cudaGraphConditionalHandleCreate");
+                    if (rc != MG_OK) break;
+                    MGP_LAUNCH(k_batch_gate<<<1, kThreads, 0, b>>>(P.ds, P.run, P.run + (size_t)v * count, count, ifh,
+                                                                   v, P.ctr, 1));
+                    rc = capture_deps(b, &bg, deps);
+                    if (rc != MG_OK) break;
+                    cudaGraphNodeParams ip = {};
+                    ip.type = cudaGraphNodeTypeConditional;
+                    ip.conditional.handle = ifh;
+                    ip.conditional.type = cudaGraphCondTypeIf;
+                    ip.conditional.size = 1;
+                    cudaGraphNode_t ifnode;
+                    if (cudaGraphAddNode(&ifnode, bg, deps.data(), nullptr, deps.size(), &ip) != cudaSuccess ||
+                        cudaStreamUpdateCaptureDependencies(b, &ifnode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+                            cudaSuccess) {
+                        rc = fail(MG_ERR_CUDA, "adding a batched IF node");
+                        break;
+                    }
+                    cudaGraph_t ifg = ip.conditional.phGraph_out[0];
+                    if (cudaStreamBeginCaptureToGraph(cs.inner, ifg, nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                        rc = fail(MG_ERR_CUDA, "capturing a batched IF body");
+                        break;
+                    }
+                    const long long i0 = launch_count();
+                    batch_vcycle(P, v, cs.inner);
+                    P.ifb = launch_count() - i0;
+                    if_total += P.ifb;
+                    if (cudaStreamEndCapture(cs.inner, &ifg) != cudaSuccess) rc = fail(MG_ERR_CUDA, "end of IF capture");
+                }
+                if (rc == MG_OK) {
+                    batch_update(P, b);
+                    MGP_LAUNCH(k_batch_check<<<1, kThreads, 0, b>>>(P.ds, P.run, count, cond, 0, P.ctr, 1));
+                }
+                cudaGraph_t tmp = bodyg;
+                if (cudaStreamEndCapture(b, &tmp) != cudaSuccess && rc == MG_OK)
+                    rc = fail(MG_ERR_CUDA, "end of body capture");
+            }
+            const long long c2 = launch_count();
+            P.body = (c2 - c1) - if_total;
+            loops += c2 - c1;
+        }
+        for (int i = 0; i < count && rc == MG_OK; ++i) {
+            cudaStreamUpdateCaptureDependencies(cs.main, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+            cudaStream_t saved = P.hs[i]->stream;
+            P.hs[i]->stream = cs.main;
+            rc = capture_epilogue(P.hs[i]);
+            P.hs[i]->stream = saved;
+            if (rc == MG_OK) rc = capture_deps(cs.main, &g, sinks);
+            all.insert(all.end(), sinks.begin(), sinks.end());
+        }
+    }
+    // the solves that run as their own branches (each its own loop, as build_graph)
+    for (int i = 0; i < nbranch && rc == MG_OK; ++i) {
+        cudaStreamUpdateCaptureDependencies(cs.main, nullptr, nullptr, 0, cudaStreamSetCaptureDependencies);
+        const long long b0 = launch_count();
+        cudaStream_t saved = branch[i]->stream;
+        branch[i]->stream = cs.main;
+        rc = capture_solve(branch[i], rhs_from_io, cs.body, cs.inner, bfixed[i], bbody[i], bifb[i]);
+        branch[i]->stream = saved;
+        loops += launch_count() - b0;
+        if (rc == MG_OK) rc = capture_deps(cs.main, &g, sinks);
+        all.insert(all.end(), sinks.begin(), sinks.end());
+    }
+    if (rc == MG_OK) {
+        cudaStreamUpdateCaptureDependencies(cs.main, all.data(), nullptr, all.size(), cudaStreamSetCaptureDependencies);
+        for (auto& P : plans)
+            if (cudaMemcpyAsync(P->hctr, P->ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, cs.main) != cudaSuccess)
+                rc = fail(MG_ERR_CUDA, "counter copy");
+    }
+    const long long c3 = launch_count();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs.main, &graph);
+    add_launches(-(c3 - c0));   // capture enqueues nothing; replays are counted after each run
+    if (rc != MG_OK) { if (graph) cudaGraphDestroy(graph); cudaGetLastError(); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    fixed = (c3 - c0) - loops;
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return MG_OK;
+}
+
+// The batched loop driven from the host (graphs off, or profiling): the
+// launches of the graph's body, with V-cycles 2 .. kMaxInner of a step always
+// launched (a solve that does not take one has its run flag clear) and one
+// read-back of the check per iteration.  Same decisions, same results.
+mg_status batch_host_loop(mg_handle* const* hs, int count, bool rhs_from_io, cudaStream_t s)
+{
+    BatchPlan P;
+    mg_status rc = make_batch_plan(hs, count, P);
+    if (rc != MG_OK) return rc;
+    for (int i = 0; i < count; ++i) {
+        cudaStream_t saved = hs[i]->stream;
+        hs[i]->stream = s;
+        capture_prologue(hs[i], rhs_from_io);
+        hs[i]->stream = saved;
+    }
+    MGP_LAUNCH(k_batch_check<<<1, kThreads, 0, s>>>(P.ds, P.run, count, 0, 1, P.ctr, 0));
+    for (;;) {
+        MG_CK(cudaMemcpyAsync(P.hctr, P.ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, s));
+        MG_CK(cudaStreamSynchronize(s));
+        if (!P.hctr->any) break;
+        batch_vcycle(P, 0, s);
+        for (int v = 1; v < kMaxInner; ++v) {
+            MGP_LAUNCH(k_batch_gate<<<1, kThreads, 0, s>>>(P.ds, P.run, P.run + (size_t)v * count, count, 0, v,
+                                                           P.ctr, 0));
+            batch_vcycle(P, v, s);
+        }
+        batch_update(P, s);
+        MGP_LAUNCH(k_batch_check<<<1, kThreads, 0, s>>>(P.ds, P.run, count, 0, 0, P.ctr, 0));
+    }
+    for (int i = 0; i < count && rc == MG_OK; ++i) {
+        cudaStream_t saved = hs[i]->stream;
+        hs[i]->stream = s;
+        rc = capture_epilogue(hs[i]);
+        hs[i]->stream = saved;
+    }
+    MG_CK(cudaStreamSynchronize(s));
+    return rc;
+}
+
+// Solves of at most this many fine cells share the batched loops; larger ones
+// run as their own branches of the batch graph.  Measured on one GB300 (64
+// solves of 32^3: the loop 2.8x faster than branches; 64^3: 1.35x; 16 of
+// 96^3: even; 16 of 128^3: 12 % slower): a large solve keeps its own working
+// set in L2 from one pass to the next when it runs as a branch, which a step
+// over the finest levels of all solves at once cannot.
+constexpr size_t kBatchLockstepCells = (size_t)1 << 18;
+
+// Concurrent batched loops a batch of count solves is split into
+// (mg_set_batch_groups; 0: automatic, one loop per 16 solves, at most 4).
+std::atomic<int> g_batch_groups{0};
+int batch_groups(int count)
+{
+    const int g = g_batch_groups.load(std::memory_order_relaxed);
+    if (g > 0) return g;
+    return std::max(1, std::min(4, count / 16));
+}
+
 // Batch graphs, cached by the exact ordered list of handles.
 struct BatchGraph {
     std::vector<mg_handle*> hs;
     bool rhs_io = true;   // right-hand sides from the callers (solves) or already in f64 (projections)
+    int groups = 1;       // concurrent batched loops asked for when the graph was built
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> fixed, body, ifb;
+    std::vector<std::unique_ptr<BatchPlan>> plans;   // set when the solves share batched loops
+    long long b_fixed = 0;
+    // launches of the last run (batched loops), from the device counters
+    long long launches() const
+    {
+        if (plans.empty()) return 0;
+        long long n = b_fixed;
+        for (const auto& P : plans) {
+            n += P->body * P->hctr->loops;
+            for (int v = 1; v < kMaxInner; ++v) n += P->ifb * P->hctr->ifruns[v];
+        }
+        return n;
+    }
 };
+
 constexpr size_t kMaxBatchGraphs = 64;   // cached batch graphs; the least recently used goes first
 std::mutex g_batch_mu;
 std::vector<BatchGraph*> g_batches;
@@ -1365,7 +1919,8 @@ mg_status batch_graph(mg_handle* const* hs, int count, bool rhs_io, BatchGraph**
         std::lock_guard<std::mutex> lk(g_batch_mu);
         for (size_t i = 0; i < g_batches.size(); ++i) {
             BatchGraph* b = g_batches[i];
-            if (b->rhs_io == rhs_io && (int)b->hs.size() == count && std::equal(b->hs.begin(), b->hs.end(), hs)) {
+            if (b->rhs_io == rhs_io && b->groups == batch_groups(count) && (int)b->hs.size() == count &&
+                std::equal(b->hs.begin(), b->hs.end(), hs)) {
                 g_batches.erase(g_batches.begin() + i);
                 g_batches.push_back(b);
                 *out = b;
@@ -1376,7 +1931,65 @@ mg_status batch_graph(mg_handle* const* hs, int count, bool rhs_io, BatchGraph**
     std::unique_ptr<BatchGraph> nb(new BatchGraph());
     nb->hs.assign(hs, hs + count);
     nb->rhs_io = rhs_io;
-    mg_status rc = build_graph(hs, count, rhs_io, &nb->exec, nb->fixed, nb->body, nb->ifb);
+    nb->groups = batch_groups(count);
+    // solves of at most kBatchLockstepCells fine cells share batched loops
+    // (when at least two do); the others run as their own branches
+    std::vector<mg_handle*> lock, branch;
+    std::vector<int> branch_at;
+    for (int i = 0; i < count; ++i) {
+        if (batch_kernels_ok(hs[i]) && hs[i]->lev[0].ncell <= kBatchLockstepCells &&
+            hs[i]->opt.nu1 == hs[0]->opt.nu1 && hs[i]->opt.nu2 == hs[0]->opt.nu2) {
+            lock.push_back(hs[i]);
+        } else {
+            branch.push_back(hs[i]);
+            branch_at.push_back(i);
+        }
+    }
+    if (lock.size() < 2) {
+        lock.clear();
+        branch.assign(hs, hs + count);
+        branch_at.resize(count);
+        for (int i = 0; i < count; ++i) branch_at[i] = i;
+    }
+    mg_status rc = MG_OK;
+    if (!lock.empty()) {
+        // groups balanced by cells: the largest solves first, each to the lightest group
+        const int nl = (int)lock.size();
+        const int G = std::max(1, std::min(batch_groups(nl), nl));
+        std::vector<int> order(nl);
+        for (int i = 0; i < nl; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return lock[a]->lev[0].ncell > lock[b]->lev[0].ncell; });
+        std::vector<std::vector<mg_handle*>> members(G);
+        std::vector<double> load(G, 0.0);
+        for (int i : order) {
+            const int gi = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            members[gi].push_back(lock[i]);
+            load[gi] += (double)lock[i]->lev[0].ncell;
+        }
+        for (int gi = 0; gi < G && rc == MG_OK; ++gi) {
+            if (members[gi].empty()) continue;
+            nb->plans.emplace_back(new BatchPlan());
+            rc = make_batch_plan(members[gi].data(), (int)members[gi].size(), *nb->plans.back());
+        }
+        const int nbr = (int)branch.size();
+        std::vector<long long> bf(nbr, 0), bb(nbr, 0), bi(nbr, 0);
+        if (rc == MG_OK)
+            rc = build_batched_graph(nb->plans, branch.data(), nbr, rhs_io, &nb->exec, nb->b_fixed, bf.data(),
+                                     bb.data(), bi.data());
+        if (rc == MG_OK) {
+            nb->fixed.assign(count, 0);
+            nb->body.assign(count, 0);
+            nb->ifb.assign(count, 0);
+            for (int k = 0; k < nbr; ++k) {
+                nb->fixed[branch_at[k]] = bf[k];
+                nb->body[branch_at[k]] = bb[k];
+                nb->ifb[branch_at[k]] = bi[k];
+            }
+        }
+    } else {
+        rc = build_graph(hs, count, rhs_io, &nb->exec, nb->fixed, nb->body, nb->ifb);
+    }
     if (rc != MG_OK) return rc;
     std::lock_guard<std::mutex> lk(g_batch_mu);
     // evict from the least recently used end, skipping graphs whose handles are
@@ -1764,7 +2377,8 @@ mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double*
         graph = graph && use_graph(hs[i]);
     }
     mg_status worst = MG_OK;
-    if (!graph) {
+    const bool host_batched = !graph && batch_eligible(hs, count);
+    if (!graph && !host_batched) {
         for (int i = 0; i < count; ++i) {
             mg_status rc = mg_solve(hs[i], rhs[i], phi[i], tol[i], st ? &st[i] : nullptr);
             if (rc != MG_OK && worst == MG_OK) worst = rc;
@@ -1778,18 +2392,27 @@ mg_status mg_solve_batch(mg_handle* const* hs, const double* const* rhs, double*
     }
     const double t0 = now_ms();
     BatchGraph* bg = nullptr;
-    mg_status brc = batch_graph(hs, count, true, &bg);
-    if (brc != MG_OK) return brc;
+    if (!host_batched) {
+        mg_status brc = batch_graph(hs, count, true, &bg);
+        if (brc != MG_OK) return brc;
+    }
     cudaStream_t s = hs[0]->stream;
     for (int i = 0; i < count; ++i)
         MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(hs[i]->d, rhs[i], phi[i], tol[i], hs[i]->opt.max_iters));
-    MG_CK(cudaGraphLaunch(bg->exec, s));
-    MG_CK(cudaStreamSynchronize(s));
+    if (host_batched) {
+        mg_status hrc = batch_host_loop(hs, count, true, s);
+        if (hrc != MG_OK) return hrc;
+    } else {
+        MG_CK(cudaGraphLaunch(bg->exec, s));
+        MG_CK(cudaStreamSynchronize(s));
+        add_launches(bg->launches());
+    }
     const double ms = now_ms() - t0;
     for (int i = 0; i < count; ++i) {
         mg_stats local;
         memset(&local, 0, sizeof local);
-        mg_status rc = graph_result(hs[i], bg->fixed[i], bg->body[i], bg->ifb[i], &local);
+        mg_status rc = bg ? graph_result(hs[i], bg->fixed[i], bg->body[i], bg->ifb[i], &local)
+                          : graph_result(hs[i], 0, 0, 0, &local);
         local.ms = ms;
         local.status = rc;
         if (st) st[i] = local;
@@ -1816,7 +2439,8 @@ mg_status mg_project_batch(mg_handle* const* hs, double* const* U, const mg_beta
         graph = graph && use_graph(h);
     }
     mg_status worst = MG_OK;
-    if (!graph) {
+    const bool host_batched = !graph && batch_eligible(hs, count);
+    if (!graph && !host_batched) {
         for (int i = 0; i < count; ++i) {
             mg_status rc = mg_project(hs[i], U + 3 * i, &b0[i], S[i], phi ? phi[i] : nullptr, tol[i], st ? &st[i] : nullptr);
             if (rc != MG_OK && worst == MG_OK) worst = rc;
@@ -1830,8 +2454,10 @@ mg_status mg_project_batch(mg_handle* const* hs, double* const* U, const mg_beta
     }
     const double t0 = now_ms();
     BatchGraph* bg = nullptr;
-    mg_status rc = batch_graph(hs, count, false, &bg);
-    if (rc != MG_OK) return rc;
+    if (!host_batched) {
+        mg_status rc = batch_graph(hs, count, false, &bg);
+        if (rc != MG_OK) return rc;
+    }
     cudaStream_t s = hs[0]->stream;
     std::vector<double*> ph(count);
     // a2 on each handle's own stream (after whatever the caller queued there:
@@ -1860,15 +2486,22 @@ mg_status mg_project_batch(mg_handle* const* hs, double* const* U, const mg_beta
         MGP_LAUNCH(k_set_io<<<1, 1, 0, s>>>(hs[i]->d, nullptr, ph[i], tol[i], hs[i]->opt.max_iters));
         if (hs[i]->loc == MG_LOC_CELL) MGP_LAUNCH(k_constraint_tol<<<1, 1, 0, s>>>(hs[i]->d));
     }
-    MG_CK(cudaGraphLaunch(bg->exec, s));
-    MG_CK(cudaStreamSynchronize(s));
+    if (host_batched) {
+        mg_status hrc = batch_host_loop(hs, count, false, s);
+        if (hrc != MG_OK) return hrc;
+    } else {
+        MG_CK(cudaGraphLaunch(bg->exec, s));
+        MG_CK(cudaStreamSynchronize(s));
+        add_launches(bg->launches());
+    }
     // a9-a10 on each handle's stream (concurrently), then the read-backs
     std::vector<mg_stats> local(count);
     std::vector<mg_status> rcs(count);
     for (int i = 0; i < count; ++i) {
         mg_handle* h = hs[i];
         memset(&local[i], 0, sizeof(mg_stats));
-        rcs[i] = graph_result(h, bg->fixed[i], bg->body[i], bg->ifb[i], &local[i]);
+        rcs[i] = bg ? graph_result(h, bg->fixed[i], bg->body[i], bg->ifb[i], &local[i])
+                    : graph_result(h, 0, 0, 0, &local[i]);
         if (rcs[i] != MG_OK && rcs[i] != MG_ERR_NOT_CONVERGED) continue;
         cudaStream_t hsx = h->stream;
         const Level& v0 = h->lev[0];
@@ -1914,6 +2547,13 @@ mg_status mg_apply(mg_handle* h, const double* phi, double* out)
     else node_apply64(h->dim, nview<double>(h, 0), phi, out, h->stream);
     MG_CK(cudaGetLastError());
     MG_CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+mg_status mg_set_batch_groups(int groups)
+{
+    if (groups < 0 || groups > 64) return fail(MG_ERR_INVALID_ARG, "batch groups must be in 0 .. 64");
+    g_batch_groups.store(groups, std::memory_order_relaxed);
     return MG_OK;
 }
 

@@ -182,6 +182,89 @@ constexpr int kCoarseMaxLevels = 8;
 template <typename T>
 void coarse_cycle(int dim, int nlev, const CellLevel<T>* L, T* const* x, T* const* b, const double* Minv, int Nd,
                   int nu1, int nu2, int order, bool zero_first, cudaStream_t s);
+// The arguments of one coarse end (levels of the sub-cycle, coarsest last).
+template <typename T>
+struct CoarseArgs {
+    int nlev;                          // levels of the sub-cycle; the last is the coarsest
+    CellLevel<T> L[kCoarseMaxLevels];
+    T* x[kCoarseMaxLevels];
+    T* b[kCoarseMaxLevels];            // b[0]: the sub-cycle's right-hand side (read only)
+    const double* Minv;
+    int Nd, nu1, nu2, order, zero_first;
+};
+
+// ---- batched solves: the same steps of many independent cell solves (3-D,
+// FP32 V-cycles in FP64 refinement) share one launch per step.  Each launch
+// reads a table of work items in device memory -- one per solve that has work
+// in that step -- and its CTAs stay resident and walk the items' tiles; a
+// solve's items run while its run flag (run[solve]) is set, so solves that
+// have converged drop out without the launch sequence changing.  Every item
+// computes with the per-quad, per-cell and per-block functions of the
+// single-solve kernels, over the same partition where a reduction is formed,
+// so each solve's result equals its result alone bit for bit.
+enum { BATCH_GSRB = 0, BATCH_RESTRICT = 1, BATCH_PROLONG = 2 };
+constexpr int kBatchTile = 32;               // work units per (warp) tile
+constexpr size_t kBatchCoarseCells = 4096;   // batched coarse ends start at the first level this small
+// One solve's share of a batched level launch: a colour pass, the residual +
+// restriction to C, or the linear prolongation from C, on level F (3-D FP32,
+// nx % 4 == 0, ny and nz even).  units: quads (colour pass, prolongation) or
+// quad columns of 2 x 2 rows and planes (restriction); tile0: first tile.  A
+// launch also takes the item index of each of its tiles (tmap).
+struct BatchItem {
+    CellLevel<float> F, C;
+    float* x;
+    const float* b;
+    float* bc;
+    const float* xc;
+    int solve, tile0, units;
+    int sq, sy;        // multiply-shift divisors (batch_magic): nx / 4, and ny (ny / 2 for the restriction)
+    unsigned mq, my;
+};
+// (m, s) with floor(n / d) = (n m) >> s for 0 <= n < 2^31
+void batch_magic(int d, unsigned* m, int* s);
+// The parameter of one batched level launch: its items (sorted by first tile)
+// and its warp tiles; it fits the 32 KB kernel-parameter space.
+constexpr int kBatchLaunchItems = 96;
+struct BatchLaunch {
+    int nitems, tiles;
+    BatchItem items[kBatchLaunchItems];
+};
+void batch_level(int op, const BatchLaunch& B, const int* run, int color, int zx, cudaStream_t s);
+// the coarse ends of count solves, one 1024-thread CTA each (A[i] belongs to solve i)
+void coarse_cycle_batch(const CoarseArgs<float>* A, int count, const int* run, cudaStream_t s);
+// FP64 residual, FP32 copy and norm partials of many cell solves (the
+// four-cells-per-thread kernel's traversal and block partition per solve):
+// blocks vb0 .. vb0 + nvb - 1 of the launch are a solve's blocks with quads
+// (nvb = min(kRedBlocks, quads / kThreads rounded up)); bmap gives the item of
+// each block.
+struct Resid64Item {
+    CellLevel<double> L;
+    const double* x;
+    const double* b;
+    float* r32;
+    const double* scale;
+    double* partials;
+    int solve, vb0, nvb, pad;
+};
+bool cell_resid64_batch_ok(const CellLevel<double>& L, const double* x, const double* b, const float* r32);
+void cell_resid64_batch(const Resid64Item* items, const int* bmap, int blocks, const int* run, cudaStream_t s);
+// *out = (sum of the partials of slot 0) * *mul per solve, in reduce_finalize's order
+struct FinalItem {
+    const double* partials;
+    double* out;
+    const double* mul;
+    int solve, pad;
+};
+void reduce_finalize_batch(const FinalItem* items, int count, const int* run, cudaStream_t s);
+// phi += (*scale) e per solve; n4: groups of four entries (n % 4 == 0, 16-byte aligned)
+struct AxpyItem {
+    double* phi;
+    const float* e;
+    const double* scale;
+    int solve, tile0, n4, pad;
+};
+int axpy_batch_grid(int tiles);
+void axpy_f32_batch(const AxpyItem* items, int count, int tiles, const int* run, int grid, cudaStream_t s);
 // The coarse end of a nodal V-cycle in one CTA (levels of at most kCoarseNodes
 // stored nodes): zero, nu1 Jacobi sweeps (ping-pong with t), residual into r,
 // restriction, dense bottom solve, prolongation, nu2 sweeps; same arithmetic

@@ -24,6 +24,7 @@ MG_FLAG_AUTOTUNE = 8
 MG_FLAG_ZERO_GUESS = 16
 MG_FLAG_SWEEP_TMA = 32
 MG_FLAG_CELL_PIPE = 64
+MG_FLAG_BATCH_BRANCHES = 128
 
 BC = {"periodic": MG_BC_PERIODIC, "neumann": MG_BC_NEUMANN, "dirichlet": MG_BC_DIRICHLET}
 
@@ -114,18 +115,24 @@ SIGNATURES = [
     ("mg_smoother_kind", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mg_prof_enable", None, [ctypes.c_int]),
     ("mg_launch_count", ctypes.c_longlong, []),
+    ("mg_set_batch_groups", ctypes.c_int, [ctypes.c_int]),
     ("mg_prof_query", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 ]
 
 MG_PROF_CELL_SMOOTH_FINE, MG_PROF_RESID64, MG_PROF_NODE_SMOOTH_FINE, MG_PROF_CELL_RESTRICT_FINE, \
-    MG_PROF_NODE_RESID64, MG_PROF_CELL_PIPE_DOWN, MG_PROF_CELL_PIPE_UP = range(7)
+    MG_PROF_NODE_RESID64, MG_PROF_CELL_PIPE_DOWN, MG_PROF_CELL_PIPE_UP, MG_PROF_BATCH_SMOOTH, \
+    MG_PROF_BATCH_RESTRICT, MG_PROF_BATCH_PROLONG, MG_PROF_BATCH_COARSE, MG_PROF_BATCH_RESID64, \
+    MG_PROF_BATCH_SMOOTH_COARSE = range(13)
 PROF_NAMES = {MG_PROF_CELL_SMOOTH_FINE: "cell_smooth_fine", MG_PROF_RESID64: "cell_resid64",
               MG_PROF_NODE_SMOOTH_FINE: "node_smooth_fine", MG_PROF_CELL_RESTRICT_FINE: "cell_restrict_fine",
               MG_PROF_NODE_RESID64: "node_resid64", MG_PROF_CELL_PIPE_DOWN: "cell_pipe_down",
-              MG_PROF_CELL_PIPE_UP: "cell_pipe_up"}
+              MG_PROF_CELL_PIPE_UP: "cell_pipe_up", MG_PROF_BATCH_SMOOTH: "batch_smooth",
+              MG_PROF_BATCH_RESTRICT: "batch_restrict", MG_PROF_BATCH_PROLONG: "batch_prolong",
+              MG_PROF_BATCH_COARSE: "batch_coarse", MG_PROF_BATCH_RESID64: "batch_resid64",
+              MG_PROF_BATCH_SMOOTH_COARSE: "batch_smooth_coarse"}
 # kernel classes bound by the FP64 pipe rather than by HBM
-PROF_FP64_BOUND = {"cell_resid64", "node_resid64"}
+PROF_FP64_BOUND = {"cell_resid64", "node_resid64", "batch_resid64"}
 
 _lib = None
 _lib_gil = None   # the same library through ctypes.PyDLL: calls keep the GIL
@@ -332,6 +339,11 @@ def mg_launch_count():
 
 def mg_prof_enable(on):
     load().mg_prof_enable(1 if on else 0)
+
+
+def mg_set_batch_groups(groups):
+    """Concurrent batched loops a batch is split into (0: automatic)."""
+    return check(load().mg_set_batch_groups(int(groups)), "mg_set_batch_groups")
 
 
 def mg_prof_query(kernel):

@@ -451,8 +451,9 @@ def run_batch(args, dev, world, dist):
             "config": {"workload": "batch of 64 MAC solves, n in {32,64,96,128} (seed 4), contrast log-uniform "
                                    "in [1e1,1e4], one graph launch per step", "cells": cells, "tol": args.tol,
                        "loop": ("per-solve graph branches" if args.batch_branches else
-                                "one batched loop: each step of all solves in one persistent launch driven by "
-                                "per-solve work items"),
+                                "the solves of at most 64^3 cells (32 of 64) in one batched loop -- each step of all "
+                                "of them one launch driven by per-solve work items -- the larger ones as concurrent "
+                                "graph branches"),
                        "rhs": "each solve's right-hand side formed before the timed region (mg_rhs); the timed "
                               "step is the 64 solves",
                        "l2": "aggregate inputs larger than L2",
@@ -462,7 +463,49 @@ def run_batch(args, dev, world, dist):
             "worst_rel_resid": max(x["rel_resid"] for x in st),
             "sequential": {"value": len(solvers) / (t_seq / 1e3), "unit": "solves/s",
                            "note": "the same 64 solves issued one mg_solve at a time"},
-            "rel_l2_vs_oracle": errs}
+            "rel_l2_vs_oracle": errs,
+            "small_batch": small_batch_compare(dev, stream, args.tol)}
+
+
+def small_batch_compare(dev, stream, tol, n=32, count=64):
+    """count solves of n^3 (the batch recipe at one size): the batched loop
+    against per-solve graph branches, CUDA events over 5 launches after 3."""
+    import numpy as np
+    import torch
+
+    import inputs as I
+    from paper_1910_12979_gb300 import ProjectionSolver, solve_batch
+    from paper_1910_12979_gb300 import native as N
+
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    specs = I.batch_specs(count, seed=4, sizes=(n,))
+    out = {"workload": f"{count} MAC solves of {n}^3 (batch recipe, seed 4)", "unit": "solves/s"}
+    for name, extra in (("batched_loop", 0), ("graph_branches", N.MG_FLAG_BATCH_BRANCHES)):
+        solvers, rhs = [], []
+        with torch.cuda.stream(stream):
+            for sp in specs:
+                p = I.batch_problem(sp)
+                s = ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", stream=stream,
+                                     flags=N.MG_FLAG_ZERO_GUESS | extra)
+                rhs.append(s.rhs([T(u) for u in p["U_mac"]], T(p["beta0"]), T(p["S"]),
+                                 beta0_face=[T(b) for b in p["beta0_face"]]))
+                solvers.append(s)
+        phis = [torch.zeros_like(f) for f in rhs]
+        for _ in range(3):
+            solve_batch(solvers, rhs, phis, [tol] * count, allow_not_converged=True)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = N.mg_launch_count()
+        e0.record(stream)
+        for _ in range(5):
+            solve_batch(solvers, rhs, phis, [tol] * count, allow_not_converged=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out[name] = {"value": count / (ms / 1e3), "ms_per_batch": ms, "gpu_launches_per_batch": (N.mg_launch_count() - l0) / 5}
+        for s in solvers:
+            s.close()
+    return out
 
 
 def run_serve(args, dev, rank, world, dist):

@@ -988,7 +988,6 @@ def main():
         with torch.cuda.stream(stream):
             d_sets = [[torch.empty(nr, dtype=torch.float64, device=dev) for _ in range(2)] + [torch.empty_like(sigma)] +
                       [torch.empty_like(u) for u in U0m] + [torch.empty_like(u) for u in U0c] for _ in range(2)]
-            w_sets = [[torch.empty_like(u) for u in Um + Uc] for _ in range(2)]
             m_sig, m_b0 = torch.empty_like(sigma), torch.empty_like(sigma)
             m_b0f = [torch.empty_like(b) for b in b0f]
         h_out = [[torch.empty_like(u, device="cpu").pin_memory() for u in Um + Uc] for _ in range(2)]
@@ -997,19 +996,22 @@ def main():
         comp_done = [torch.cuda.Event() for _ in range(2)]
         d2h_done = [torch.cuda.Event() for _ in range(2)]
 
+        issue_ms = {"upload": 0.0, "download": 0.0, "calls": 0}   # host time spent issuing the copies
+
         def upload(i):
+            t_issue = time.perf_counter()
             with torch.cuda.stream(ustream):
-                ustream.wait_event(comp_done[i])   # the solves that read input set i are done
+                ustream.wait_event(comp_done[i])   # the solves that used set i are done
+                ustream.wait_event(d2h_done[i])    # and its projected velocities have been read back
                 for d, hsrc in zip(d_sets[i], h_in):
                     d.copy_(hsrc, non_blocking=True)
                 h2d_done[i].record(ustream)
+            issue_ms["upload"] = max(issue_ms["upload"], (time.perf_counter() - t_issue) * 1e3)
 
         def compute(i):
             br, rr, Sv = d_sets[i][0], d_sets[i][1], d_sets[i][2]
-            u0m, u0c = d_sets[i][3:6], d_sets[i][6:9]
-            um, uc = w_sets[i][:3], w_sets[i][3:]
+            um, uc = d_sets[i][3:6], d_sets[i][6:9]   # projected in place
             stream.wait_event(h2d_done[i])
-            stream.wait_event(d2h_done[i])   # output set i has been read back
             with torch.cuda.stream(stream):
                 N.mg_base_state_map(geo, 0, (0.5, 0.5, 0.5), 0.0, 0.5 * hz, nr, br.data_ptr(), rr.data_ptr(),
                                     m_sig.data_ptr(), m_b0.data_ptr(), [b.data_ptr() for b in m_b0f],
@@ -1017,18 +1019,18 @@ def main():
                 sg, b0, bf = m_sig, m_b0, m_b0f
                 mac.update_coeff(sg)
                 nod.update_coeff(sg)
-                for a_, b_ in zip(um + uc, u0m + u0c):
-                    a_.copy_(b_)
                 mac.project(um, b0, Sv, beta0_face=bf, phi=phim, tol=args.tol, allow_not_converged=True)
                 nod.project(uc, b0, Sv, phi=phin, tol=args.tol, allow_not_converged=True)
                 comp_done[i].record(stream)
 
         def download(i):
+            t_issue = time.perf_counter()
             with torch.cuda.stream(dstream):
                 dstream.wait_event(comp_done[i])
-                for hd, d in zip(h_out[i], w_sets[i]):
+                for hd, d in zip(h_out[i], d_sets[i][3:9]):
                     hd.copy_(d, non_blocking=True)
                 d2h_done[i].record(dstream)
+            issue_ms["download"] = max(issue_ms["download"], (time.perf_counter() - t_issue) * 1e3)
 
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -1064,8 +1066,55 @@ def main():
             t = torch.tensor([mse], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             mse = float(t.item())
+        # the parts of a step timed one at a time (after the pipelined run; inputs resident):
+        # the upload alone, the read-back alone, and the device work of one step alone
+        def alone(st_, fn, reps=3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(st_)
+            for _ in range(reps):
+                fn()
+            b.record(st_)
+            b.synchronize()
+            return a.elapsed_time(b) / reps
+
+        def up_only():
+            with torch.cuda.stream(ustream):
+                for d, hsrc in zip(d_sets[0], h_in):
+                    d.copy_(hsrc, non_blocking=True)
+
+        def down_only():
+            with torch.cuda.stream(dstream):
+                for hd, d in zip(h_out[0], d_sets[0][3:9]):
+                    hd.copy_(d, non_blocking=True)
+
+        def compute_only(reps=3):
+            # each projection starts from the step's inputs again (restored outside the timed part)
+            tot = 0.0
+            for _ in range(reps):
+                with torch.cuda.stream(stream):
+                    for d, u in zip(d_sets[0][3:9], U0m + U0c):
+                        d.copy_(u)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                compute(0)
+                b.record(stream)
+                b.synchronize()
+                tot += a.elapsed_time(b)
+            return tot / reps
+
+        t_up, t_down, t_comp = alone(ustream, up_only), alone(dstream, down_only), compute_only()
+        torch.cuda.synchronize(dev)
+        breakdown = {"h2d_ms": t_up, "h2d_gbs": h2d / (t_up * 1e6), "d2h_ms": t_down, "d2h_gbs": d2h / (t_down * 1e6),
+                     "device_ms": t_comp, "pipelined_ms_per_step": mse / Ke,
+                     "hidden_copy_ms": t_up + t_down + t_comp - mse / Ke,
+                     "host_buffers_pinned": all(t.is_pinned() for t in h_in + h_out[0] + h_out[1]),
+                     "max_host_issue_ms": {"upload": issue_ms["upload"], "download": issue_ms["download"]},
+                     "note": "each part timed alone with CUDA events on its own stream (the device part: the "
+                             "base-state expansion, both coefficient rebuilds and both projections of one "
+                             "step); hidden_copy_ms = the parts' sum minus the pipelined step time"}
         line["e2e"] = {"value": 2.0 * Ke * world / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": mse / Ke,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": mse / Ke, "breakdown": breakdown,
                        "note": "pinned host inputs copied and results read back every step on an upload and "
                                "a read-back stream, overlapping the solves of the neighbouring steps "
                                "(double-buffered device inputs and outputs). The height-dependent base state "

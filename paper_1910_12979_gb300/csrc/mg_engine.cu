@@ -147,6 +147,7 @@ struct mg_handle {
     double* partials;
     DevScalars* d;
     DevScalars* hs;  // pinned host copy
+    DevScalars* hs_dev;  // the same pinned block as the device addresses it (written by k_put_words)
     cudaStream_t stream;
     void* ws;
     size_t ws_bytes;
@@ -402,9 +403,23 @@ mg_status build_coefficients(mg_handle* h, const mg_coeff* c)
     return MG_OK;
 }
 
+// Small device-to-host results (the scalar block, batch counters) are written
+// into mapped pinned memory by a one-block kernel instead of a copy: a copy
+// would queue on a copy engine behind whatever large transfer the caller has in
+// flight on another stream (a step's uploads or read-backs), a kernel does not.
+__global__ void k_put_words(int* __restrict__ dst, const int* __restrict__ src, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+void put_host(void* dst_dev, const void* src, size_t bytes, cudaStream_t s)
+{
+    MGP_LAUNCH(k_put_words<<<1, 64, 0, s>>>((int*)dst_dev, (const int*)src, (int)(bytes / sizeof(int))));
+}
+static_assert(sizeof(DevScalars) % sizeof(int) == 0, "scalar block copied as words");
+
 mg_status readback(mg_handle* h)
 {
-    MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+    put_host(h->hs_dev, h->d, sizeof(DevScalars), h->stream);
     MG_CK(cudaStreamSynchronize(h->stream));
     if (h->hs->async_err) return fail(MG_ERR_CUDA, "a bounded wait inside a kernel (an asynchronous copy or a pipelined pass) gave up");
     return MG_OK;
@@ -1266,7 +1281,7 @@ mg_status capture_epilogue(mg_handle* h)
     if (h->singular) gauge(h, phi);
     MGP_LAUNCH(k_zero_if_f0<<<kRedBlocks, kThreads, 0, s>>>(phi, n, h->d));
     MGP_LAUNCH(k_copy_io<<<kRedBlocks, kThreads, 0, s>>>(phi, h->d, n, 2));
-    MG_CK(cudaMemcpyAsync(h->hs, h->d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    put_host(h->hs_dev, h->d, sizeof(DevScalars), s);
     return MG_OK;
 }
 
@@ -1494,6 +1509,7 @@ struct BatchPlan {
     DevScalars** ds = nullptr;        // [count]
     BatchCounters* ctr = nullptr;     // device counters
     BatchCounters* hctr = nullptr;    // pinned host copy, written at the end of each run
+    BatchCounters* hctr_dev = nullptr;   // its device address
     Step smooth[kMaxLevels], restr[kMaxLevels], prolong[kMaxLevels];
     CoarseArgs<float>* coarse = nullptr;
     Resid64Item* resid = nullptr;
@@ -1592,7 +1608,8 @@ mg_status make_batch_plan(mg_handle* const* hs, int count, BatchPlan& P)
                  o_rs = take(sizeof(Resid64Item) * count), o_fi = take(sizeof(FinalItem) * count),
                  o_ax = take(sizeof(AxpyItem) * count), o_bm = take(sizeof(int) * bmap.size());
     MG_CK(cudaMalloc(&P.dmem, off));
-    MG_CK(cudaMallocHost(&P.hctr, sizeof(BatchCounters)));
+    MG_CK(cudaHostAlloc(&P.hctr, sizeof(BatchCounters), cudaHostAllocMapped));
+    MG_CK(cudaHostGetDevicePointer((void**)&P.hctr_dev, P.hctr, 0));
     memset(P.hctr, 0, sizeof(BatchCounters));
     std::vector<char> host(off, 0);
     auto put = [&](size_t o, const void* src, size_t bytes) { if (bytes) memcpy(host.data() + o, src, bytes); };
@@ -1793,9 +1810,7 @@ mg_status build_batched_graph(std::vector<std::unique_ptr<BatchPlan>>& plans, mg
     }
     if (rc == MG_OK) {
         cudaStreamUpdateCaptureDependencies(cs.main, all.data(), nullptr, all.size(), cudaStreamSetCaptureDependencies);
-        for (auto& P : plans)
-            if (cudaMemcpyAsync(P->hctr, P->ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, cs.main) != cudaSuccess)
-                rc = fail(MG_ERR_CUDA, "counter copy");
+        for (auto& P : plans) put_host(P->hctr_dev, P->ctr, sizeof(BatchCounters), cs.main);
     }
     const long long c3 = launch_count();
     cudaGraph_t graph = nullptr;
@@ -1827,7 +1842,7 @@ mg_status batch_host_loop(mg_handle* const* hs, int count, bool rhs_from_io, cud
     }
     MGP_LAUNCH(k_batch_check<<<1, kThreads, 0, s>>>(P.ds, P.run, count, 0, 1, P.ctr, 0));
     for (;;) {
-        MG_CK(cudaMemcpyAsync(P.hctr, P.ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, s));
+        put_host(P.hctr_dev, P.ctr, sizeof(BatchCounters), s);
         MG_CK(cudaStreamSynchronize(s));
         if (!P.hctr->any) break;
         batch_vcycle(P, 0, s);
@@ -2201,7 +2216,9 @@ mg_status mg_setup(const mg_coeff* c, const mg_geometry* g, const mg_bc* bc, con
         h->own_ws = true;
     }
     h->ws_bytes = need;
-    if (cudaMallocHost((void**)&h->hs, sizeof(DevScalars)) != cudaSuccess) {
+    if (cudaHostAlloc((void**)&h->hs, sizeof(DevScalars), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&h->hs_dev, h->hs, 0) != cudaSuccess) {
+        if (h->hs) cudaFreeHost(h->hs);
         if (h->own_ws) cudaFree(h->ws);
         delete h;
         return fail(MG_ERR_OOM, "pinned host allocation failed");

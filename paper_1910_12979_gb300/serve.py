@@ -178,8 +178,14 @@ class Scheduler:
 
     # -- driving ------------------------------------------------------------------
     def run_stream(self, requests, timeout=600.0):
-        """Feed requests at their arrival times; return them when all are done."""
+        """Feed requests at their arrival times; return them when all are done.
+        The slots (resident hierarchies) stay from one stream to the next; the
+        per-stream counters (done, batches, evictions) start again."""
         reqs = sorted(requests, key=lambda r: r.arrival)
+        with self.lock:
+            self.done = []
+            self.batches = []
+            self.evictions = 0
         self.t0 = self.clock()
         i = 0
         deadline = self.t0 + timeout

@@ -322,17 +322,18 @@ mg_status mg_project_batch(mg_handle* const* hs, double* const* U, const mg_beta
  * No counterpart in the paper.  Work already enqueued stays on the old stream:
  * synchronise it first if the new stream does not wait for it.
  * MG_ERR_INVALID_ARG for a null handle. */
+mg_status mg_set_stream(mg_handle* h, void* stream);
+
 /* Concurrent batched loops (section 3's V-cycles of many independent solves):
  * a batch whose solves share batched loops (see MG_FLAG_BATCH_BRANCHES) is
  * split into this many groups of about equal total cells, each group one
  * lockstep loop, the groups concurrent branches of the batch graph, so one
  * group's FP64 residuals and latency-bound small levels overlap another's
- * bandwidth-bound finest levels.  0 (the default) picks one group per 16
- * solves, at most 4.  Results do not depend on it.  Takes effect for batch
+ * bandwidth-bound finest levels.  0 (the default) means one group, which
+ * measured fastest.  Results do not depend on it.  Takes effect for batch
  * graphs built afterwards (they are cached per list of handles and setting).
  * MG_ERR_INVALID_ARG outside 0 .. 64. */
 mg_status mg_set_batch_groups(int groups);
-mg_status mg_set_stream(mg_handle* h, void* stream);
 
 /* out = L phi with the FP64 fine-level operator of the projection system (S3,
  * Eq. 6's elliptic operator; diagnostics and tests).  Device arrays in the

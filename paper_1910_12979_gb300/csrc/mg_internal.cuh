@@ -204,7 +204,7 @@ struct CoarseArgs {
 // so each solve's result equals its result alone bit for bit.
 enum { BATCH_GSRB = 0, BATCH_RESTRICT = 1, BATCH_PROLONG = 2 };
 constexpr int kBatchTile = 32;               // work units per (warp) tile
-constexpr size_t kBatchCoarseCells = 4096;   // batched coarse ends start at the first level this small
+constexpr size_t kBatchCoarseCells = 512;    // batched coarse ends start at the first level this small
 // One solve's share of a batched level launch: a colour pass, the residual +
 // restriction to C, or the linear prolongation from C, on level F (3-D FP32,
 // nx % 4 == 0, ny and nz even).  units: quads (colour pass, prolongation) or

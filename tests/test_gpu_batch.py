@@ -203,3 +203,50 @@ def test_mixed_batch_falls_back_to_branches():
         assert torch.equal(pa, pb)
     for s in solvers:
         s.close()
+
+
+def test_batched_loop_over_96_solves():
+    """More solves than one launch's parameter table holds (96 items): every
+    step is split over several launches; each result is its result alone."""
+    specs = [((16, 16, 16), P_N, P_D), ((24, 24, 24), D3, D3), ((32, 16, 16), N3, N3)] * 34   # 102 solves
+    solvers = make(specs)
+    rhs = rhs_of(solvers)
+    alone = []
+    for s, f in zip(solvers, rhs):
+        phi = torch.zeros_like(f)
+        alone.append((phi, s.solve(f, phi, tol=1e-10)))
+    phis = [torch.zeros_like(f) for f in rhs]
+    st = solve_batch(solvers, rhs, phis, [1e-10] * len(rhs))
+    for (pa, sa), pb, sb in zip(alone, phis, st):
+        assert sb["status"] == sa["status"] and sb["iters"] == sa["iters"]
+        assert torch.equal(pa, pb)
+    for s in solvers:
+        s.close()
+
+
+def test_host_driven_projection_batch_equals_alone():
+    """mg_project_batch with graphs off runs the batched loop from the host
+    (one read-back per iteration): the same velocities as each projection alone."""
+    sizes = (32, 24, 48)
+    probs = [I.stratified(n, seed=90 + n, contrast=10.0 ** (1 + k), mac=True, nodal=False)
+             for k, n in enumerate(sizes)]
+    alone_s = [ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed") for p in probs]
+    host_s = [ProjectionSolver(p["geom"], T(p["sigma"]), loc="cell", prec="mixed", flags=N.MG_FLAG_NO_GRAPH)
+              for p in probs]
+
+    def inputs(p):
+        return [T(u) for u in p["U_mac"]], T(p["beta0"]), T(p["S"]), [T(b) for b in p["beta0_face"]]
+
+    alone = []
+    for p, s in zip(probs, alone_s):
+        U, b0, S, bf = inputs(p)
+        alone.append((U, s.project(U, b0, S, beta0_face=bf, tol=1e-11)))
+    ins = [inputs(p) for p in probs]
+    st = project_batch(host_s, [x[0] for x in ins], [x[1] for x in ins], [x[2] for x in ins],
+                       beta0_face=[x[3] for x in ins], tols=[1e-11] * len(sizes))
+    for (Ua, sa), x, sb in zip(alone, ins, st):
+        assert sb["status"] == N.MG_OK and sb["iters"] == sa["iters"]
+        for a, b in zip(Ua, x[0]):
+            assert torch.equal(a, b)
+    for s in alone_s + host_s:
+        s.close()

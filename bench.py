@@ -932,10 +932,17 @@ def main():
                     "hbm_GBps": k["bytes"] / n / t / 1e9, "avg_launch_ms": t * 1e3, "launches": k["launches"],
                     "share_of_step": k["ms"] / ms if ms > 0 else None}
         ach = k["bytes"] / n / t / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": ncu_traffic(name), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": k["bytes"] / n, "avg_launch_ms": t * 1e3,
-                "launches": k["launches"], "share_of_step": k["ms"] / ms if ms > 0 else None}
+        tr = ncu_traffic(name)
+        out = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+               "traffic": tr, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+               "algorithmic_bytes_per_launch": k["bytes"] / n, "avg_launch_ms": t * 1e3,
+               "launches": k["launches"], "share_of_step": k["ms"] / ms if ms > 0 else None}
+        if tr:
+            # the DRAM bytes the kernel actually moves (ncu, per launch) over this run's event-timed
+            # launch duration: the kernel's fraction of the HBM peak on its own traffic
+            out["dram_GBps"] = tr / t / 1e9
+            out["dram_frac"] = tr / t / 1e9 / hbm
+        return out
 
     live = [k for k in prof if prof[k]["launches"] > 0]
     dom = max(live, key=lambda k: prof[k]["ms"])

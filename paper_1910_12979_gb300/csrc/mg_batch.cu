@@ -1,4 +1,4 @@
-// mg_batch.cu -- the FP32 level passes of many solves in one persistent launch.
+// mg_batch.cu -- the FP32 level passes of many solves, one launch per step for all of them.
 //
 // A batch of independent cell solves of uneven sizes runs its V-cycles in
 // lockstep: one launch per step (a colour pass, the residual + restriction or

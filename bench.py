@@ -1014,21 +1014,31 @@ def main():
         d2h_done = [torch.cuda.Event() for _ in range(2)]
 
         issue_ms = {"upload": 0.0, "download": 0.0, "calls": 0}   # host time spent issuing the copies
+        tl = []   # (stage, event) of the first timed steps: where the device spends each step
+
+        def mark(st_, name):
+            if tl is not None and len(tl) < 36:
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(st_)
+                tl.append((name, ev))
 
         def upload(i):
             t_issue = time.perf_counter()
             with torch.cuda.stream(ustream):
                 ustream.wait_event(comp_done[i])   # the solves that used set i are done
                 ustream.wait_event(d2h_done[i])    # and its projected velocities have been read back
+                mark(ustream, f"upload{i}-start")
                 for d, hsrc in zip(d_sets[i], h_in):
                     d.copy_(hsrc, non_blocking=True)
                 h2d_done[i].record(ustream)
+                mark(ustream, f"upload{i}-end")
             issue_ms["upload"] = max(issue_ms["upload"], (time.perf_counter() - t_issue) * 1e3)
 
         def compute(i):
             br, rr, Sv = d_sets[i][0], d_sets[i][1], d_sets[i][2]
             um, uc = d_sets[i][3:6], d_sets[i][6:9]   # projected in place
             stream.wait_event(h2d_done[i])
+            mark(stream, f"step{i}-start")
             with torch.cuda.stream(stream):
                 N.mg_base_state_map(geo, 0, (0.5, 0.5, 0.5), 0.0, 0.5 * hz, nr, br.data_ptr(), rr.data_ptr(),
                                     m_sig.data_ptr(), m_b0.data_ptr(), [b.data_ptr() for b in m_b0f],
@@ -1039,14 +1049,17 @@ def main():
                 mac.project(um, b0, Sv, beta0_face=bf, phi=phim, tol=args.tol, allow_not_converged=True)
                 nod.project(uc, b0, Sv, phi=phin, tol=args.tol, allow_not_converged=True)
                 comp_done[i].record(stream)
+                mark(stream, f"step{i}-end")
 
         def download(i):
             t_issue = time.perf_counter()
             with torch.cuda.stream(dstream):
                 dstream.wait_event(comp_done[i])
+                mark(dstream, f"readback{i}-start")
                 for hd, d in zip(h_out[i], d_sets[i][3:9]):
                     hd.copy_(d, non_blocking=True)
                 d2h_done[i].record(dstream)
+                mark(dstream, f"readback{i}-end")
             issue_ms["download"] = max(issue_ms["download"], (time.perf_counter() - t_issue) * 1e3)
 
         e0 = torch.cuda.Event(enable_timing=True)
@@ -1073,12 +1086,16 @@ def main():
                 e1.record(stream)
             torch.cuda.synchronize(dev)
 
+        tl = None
         run(2)
         Ke = max(2, args.steps)
         if dist is not None:
             dist.barrier()
+        tl = []
         run(Ke, timed=True)
         mse = e0.elapsed_time(e1)
+        timeline = [(name, round(e0.elapsed_time(ev), 3)) for name, ev in tl]
+        tl = None
         if dist is not None:
             t = torch.tensor([mse], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -1127,6 +1144,7 @@ def main():
                      "hidden_copy_ms": t_up + t_down + t_comp - mse / Ke,
                      "host_buffers_pinned": all(t.is_pinned() for t in h_in + h_out[0] + h_out[1]),
                      "max_host_issue_ms": {"upload": issue_ms["upload"], "download": issue_ms["download"]},
+                     "timeline_ms": timeline,
                      "note": "each part timed alone with CUDA events on its own stream (the device part: the "
                              "base-state expansion, both coefficient rebuilds and both projections of one "
                              "step); hidden_copy_ms = the parts' sum minus the pipelined step time"}

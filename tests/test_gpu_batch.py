@@ -250,3 +250,28 @@ def test_host_driven_projection_batch_equals_alone():
             assert torch.equal(a, b)
     for s in alone_s + host_s:
         s.close()
+
+
+def test_ineligible_solves_run_as_branches_beside_the_loop():
+    """A batch mixing solves the batched kernels take (16^3, 24^3, 32x40x32)
+    with cell solves they do not (40^3: its 10^3 level has nx % 4 != 0; a 2-D
+    grid): the first share the loop, the others run as branches of the same
+    graph; every result equals the solve alone."""
+    specs = [((16, 16, 16), P_N, P_D), ((40, 40, 40), D3, D3), ((24, 24, 24), N3, N3), ((32, 40, 32), P_N, P_D)]
+    solvers = make(specs)
+    rng = np.random.default_rng(3)
+    g2 = I.geometry((64, 48), ("periodic", "neumann"), ("periodic", "dirichlet"))
+    solvers.append(ProjectionSolver(g2, T(np.exp(rng.random((1, 48, 64)))), loc="cell", prec="mixed"))
+    rhs = rhs_of(solvers)
+    alone = []
+    for s, f in zip(solvers, rhs):
+        phi = torch.zeros_like(f)
+        alone.append((phi, s.solve(f, phi, tol=1e-10)))
+    for rep in range(2):
+        phis = [torch.zeros_like(f) for f in rhs]
+        st = solve_batch(solvers, rhs, phis, [1e-10] * len(rhs))
+        for (pa, sa), pb, sb in zip(alone, phis, st):
+            assert sb["status"] == N.MG_OK and sb["iters"] == sa["iters"]
+            assert torch.equal(pa, pb)
+    for s in solvers:
+        s.close()
